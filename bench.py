@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark: batched exp(A) by parallel shifted solves (Blanes, arXiv:2210.03714).
+
+Workload (one step): 4096 real dense matrices, d drawn uniformly from
+{16, 32, ..., 256}, entries N(0,1)/sqrt(d), each scaled to ||A||_1 ~ U[0.5, 8];
+the R8 set (8 shifted solves, Sec. 4.2) with scaling and squaring.  A step is
+one fm_expm_batched call over the whole batch (norm, s, scaling, 8 factor +
+solve + refinement + combination per matrix, s squarings).
+
+Printed: one JSON line (rank 0).  value = matrices per second of the mixed
+precision form (single-precision factorizations + refinement to double
+accuracy); the plain double form is timed in the same run (fp64_value) and the
+largest relative difference between the two over the batch is reported.
+Inputs (784 MB) are larger than L2 (129 MB), so no flush is needed between steps.
+
+--impl reference times the CPU oracle (oracle/, plain C, FP64) on a bounded
+sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched f(A)/f(A)V evals/sec at ≤1e-12 rel err, mixed vs FP64 GPU; % roofline"
+WORKLOAD = ("batched expm: 4096 real dense matrices, d uniform in {16,32,...,256}, "
+            "entries N(0,1)/sqrt(d), ||A||_1 ~ U[0.5,8], R8 coefficient set (k=8 shifted solves)")
+BATCH = 4096
+SEED = 1000
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# FP64 FMA peak of this GPU: 152 SMs x 64 FP64 flop/clk... is not what GB300
+# has; its FP64 rate is 1.25 TFLOP/s nominal (about 2 DFMA per SM per clock).
+FP64_NOMINAL_TFLOPS = 1.25
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def make_batch():
+    import numpy as np
+    from paper_2210_03714_gb300 import workloads as wl
+    dims = wl.batch_dims(BATCH, SEED)
+    norms = np.random.default_rng(SEED + 7919).uniform(0.5, 8.0, size=BATCH)
+    flat = wl.batch_flat(dims, norms, SEED)
+    return dims, norms, flat
+
+
+def method_flops(dims, s):
+    """Algorithmic flops of one evaluation (per matrix): k = 8 shifted LU + d-RHS
+    solves at 8/3 d^3 each (Sec. 1: "8/3 d^3 flops") and s squarings at 2 d^3."""
+    import numpy as np
+    d3 = np.asarray(dims, dtype=np.float64) ** 3
+    return float(np.sum(8 * (8.0 / 3.0) * d3 + 2.0 * np.asarray(s, dtype=np.float64) * d3))
+
+
+def cpu_baseline(dims, norms, sample, gpu_F=None, P=None):
+    """The oracle (plain C, FP64, OpenMP over matrices) on a bounded sample."""
+    import numpy as np
+    import oracle
+    from paper_2210_03714_gb300 import workloads as wl
+    rng = np.random.default_rng(99)
+    idx = np.sort(rng.choice(BATCH, sample, replace=False))
+    mats = [wl.dense_scaled(int(dims[b]), float(norms[b]), SEED + 1 + int(b), scale_sqrt=True)
+            for b in idx]
+    oracle.lib()
+    t0 = time.perf_counter()
+    outs, s, info = oracle.expm_batched(mats, np.ones(len(mats)), "R8")
+    dt = time.perf_counter() - t0
+    errs = None
+    if gpu_F is not None:
+        errs = []
+        for j, b in enumerate(idx[:64]):
+            got = P.get(gpu_F, int(b)).cpu().numpy()
+            errs.append(float(np.linalg.norm(got - outs[j]) / np.linalg.norm(outs[j])))
+    return dict(value=len(mats) / dt, unit="evals/s", cores=oracle.num_threads(), kind="oracle",
+                sample="%d matrices drawn uniformly from the 4096-matrix batch (same d and norm "
+                       "distribution), R8, one pass" % len(mats),
+                seconds=dt), errs
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    dims, norms, _ = make_batch()
+    vals = []
+    cb = None
+    for it in range(args.warmup + args.steps):
+        cb, _ = cpu_baseline(dims, norms, args.ref_sample)
+        if it >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * args.ref_sample / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": BATCH, "sample": args.ref_sample},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2210_03714_gb300 as fm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    fm.lib()
+    dims, norms, flat = make_batch()
+    P = fm.Packed(dims=[int(d) for d in dims], flat=torch.from_numpy(flat).to(dev))
+    F = torch.empty_like(P.flat)
+    t_dev = torch.ones(BATCH, dtype=torch.float64, device=dev)
+    cs = fm.Coeffs("R8")
+    stream = torch.cuda.current_stream()
+
+    def step(prec, out):
+        return fm.expm_batched(P, t_dev, cs, precision=prec, out=out)
+
+    def timed(prec, out, steps, warmup):
+        for _ in range(warmup):
+            step(prec, out)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for k in range(steps):
+            _, info, s = step(prec, out)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        barrier()
+        return per, info, s
+
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    per, info, s = timed(args.precision, F, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(per) / len(per))
+    bad = int((info != 0).sum().item())
+    s_host = s.cpu().numpy()
+    value = world * BATCH / (ms / 1000.0)
+
+    # the plain double form on the same GPU, same batch
+    F64 = torch.empty_like(P.flat)
+    fp64_ms = None
+    maxdiff = None
+    if not args.no_fp64:
+        per64, info64, _ = timed("fp64", F64, max(1, min(args.steps, 2)), 1)
+        fp64_ms = max_over_ranks(sum(per64) / len(per64))
+        # largest relative Frobenius difference, mixed vs double, over the batch
+        diffs = []
+        for b in range(BATCH):
+            x, y = P.get(F, b), P.get(F64, b)
+            diffs.append((x - y).norm() / y.norm())
+        maxdiff = float(torch.stack(diffs).max().item())
+
+    # end to end through the public API: pinned host input, H2D, call, D2H
+    A_host = torch.from_numpy(flat).pin_memory()
+    F_host = torch.empty_like(A_host).pin_memory()
+    A_dev = torch.empty_like(P.flat)
+    Pe = fm.Packed(dims=[int(d) for d in dims], flat=A_dev)
+    t_host = torch.ones(BATCH, dtype=torch.float64).pin_memory()
+    info_host = torch.empty(BATCH, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    for k in range(e2e_steps + 1):
+        if k == 1:
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        A_dev.copy_(A_host, non_blocking=True)
+        t_dev.copy_(t_host, non_blocking=True)
+        Fo, inf, _ = fm.expm_batched(Pe, t_dev, cs, precision=args.precision)
+        F_host.copy_(Fo, non_blocking=True)
+        info_host.copy_(inf, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
+    h2d = A_host.numel() * 8 + t_host.numel() * 8
+    d2h = F_host.numel() * 8 + info_host.numel() * 4
+
+    # roofline of the dominant kernel (the persistent per-matrix kernel)
+    flops = method_flops(dims, s_host)
+    peaks = load_peaks()
+    achieved = flops / (ms / 1000.0) / 1e12
+    fp64_peak = peaks.get("fp64_tflops", FP64_NOMINAL_TFLOPS)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "note": "method flops (8 x 8/3 d^3 + 2 s d^3 per matrix) per launch / call time; "
+                        "peak = FP64 FMA rate (nominal 1.25 TFLOP/s)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": BATCH, "precision": args.precision,
+                       "coeffs": "R8", "l2": "inputs (784 MB) larger than L2, no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline,
+            "e2e": {"value": world * BATCH / (e2e_ms / 1000.0), "unit": "evals/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "status_nonzero": bad,
+            "fp64_value": (world * BATCH / (fp64_ms / 1000.0)) if fp64_ms else None,
+            "fp64_ms_per_step": fp64_ms,
+            "speedup_vs_fp64": (fp64_ms / ms) if fp64_ms else None,
+            "max_rel_diff_vs_fp64": maxdiff,
+            "method_tflops": achieved,
+            "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, errs = cpu_baseline(dims, norms, args.cpu_sample, F, P)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        if errs:
+            line["max_rel_err_vs_oracle_sample"] = max(errs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,237 @@
+/*
+ * fm.h -- C ABI of libfm: functions of matrices, and their action on blocks of
+ * vectors, as a fixed linear combination of k independent shifted solves.
+ *
+ * Method: S. Blanes, "Parallel computation of functions of matrices and their
+ * action on vectors", arXiv:2210.03714.
+ *   r(x) = a0 + d1 x + d2 x^2 + sum_i b_i c_i x / (1 - c_i x)      (Eq. ParallRoundOff,
+ *                                                                 Eq. Frac10R)
+ *   r(x) = d0 + d1 x + d2 x^2 + sum_i b_i / (1 - c_i x)           (Eq. rat1, ParallHybrid)
+ * with d0 = a0 - sum_i b_i; each term needs one solve with M_i = I - c_i B
+ * (Sec. 2: the "processors" F_i = (I - c_i B)^{-1}).  f(tA) is r(B)^(2^s) with
+ * B = tA/2^s (Sec. 1, scaling and squaring); f(tA)V is N steps V <- r(B)V with
+ * B = tA/N and each factorization done once (Sec. 1; Sec. 5.1 remarks);
+ * phi_1 uses the doubling phi1(2X) = (e^X + I) phi1(X) / 2 (Sec. 1).
+ * s (or N) is the smallest value with ||B||_1 <= theta, theta from the forward
+ * error bound of Sec. 3.
+ *
+ * Conventions for every entry point below:
+ *  - Matrices are dense, row-major, with a leading dimension (elements between
+ *    consecutive rows, >= number of columns).  Real data is double; complex data
+ *    ("z" functions) is interleaved (re, im) double pairs.
+ *  - A, V, F, W, Phi, E, t_dev, d_dev, off_dev, info_dev are DEVICE pointers owned
+ *    by the caller; the library never frees or retains them.  fm_coeffs arrays
+ *    are HOST pointers, read during the call only.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are stream-ordered and asynchronous: the return status reports
+ *    argument, configuration and launch errors only.  Per-matrix numerical
+ *    status goes to info (device int per matrix, or the optional info_host of the
+ *    single-matrix calls after a synchronize):
+ *        0       success
+ *        > 0     exactly zero pivot: (term index i) * d + (1-based column)
+ *        -1      mixed precision: iterative refinement did not reach opts.ir_tol
+ *        -2      non-finite entry in A (or V, or t)
+ *  - Outputs must not alias inputs.
+ *  - Scratch: opts.workspace (device, opts.workspace_bytes >= fm_workspace_size)
+ *    or, when NULL, a buffer the library allocates once per device and reuses
+ *    (grown when a larger problem arrives; released at process exit).
+ *  - Errors: FM_EINVAL (bad pointer, value or coefficient set), FM_ESHAPE (bad
+ *    dimension or leading dimension, or d beyond what the kernels support),
+ *    FM_ENOMEM, FM_ECUDA (launch or runtime failure).  fm_last_error() returns
+ *    a message for the calling thread's last failure.
+ */
+#ifndef FM_H_
+#define FM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FM_OK = 0,
+  FM_EINVAL = 1,
+  FM_ESHAPE = 2,
+  FM_ENOMEM = 3,
+  FM_ECUDA = 4,
+  FM_ESINGULAR = 5,
+  FM_ENOCONV = 6,
+  FM_ETIMEOUT = 7
+} fm_status;
+
+/* A coefficient set (Sec. 2 and 4).  k terms with nodes c_i and weights b_i
+ * (c_i = 0 terms allowed: they cost no solve).  conj_pair = 1 means each term
+ * stands for 2 Re(b_i / (1 - c_i x)) with complex c_i, b_i (Eq. Pade4, Pade4phi1;
+ * real matrices only).  a0 = r(0); d1, d2 = hybrid polynomial part (Eq. Frac10).
+ * order = s of Eq. (approx1); theta = ||B|| threshold for the target tolerance
+ * (Sec. 3).  Arrays are host memory of length k; c_im / b_im may be NULL for
+ * real sets.  k <= FM_MAX_TERMS. */
+#define FM_MAX_TERMS 16
+typedef struct {
+  int k;
+  const double* c_re;
+  const double* c_im;
+  const double* b_re;
+  const double* b_im;
+  int conj_pair;
+  double a0, d1, d2;
+  int order;
+  double theta;
+} fm_coeffs;
+
+/* Built-in sets.  The b_i are those printed in the paper, or (FM_R8_PHI1,
+ * FM_R4_PHI1_A5) the solution of Eq. (LinearEqsbi) with the printed c_i and
+ * a_k = 1/(k+1)!.  theta is computed for the double-precision unit roundoff
+ * 2^-53 from the forward bound of Sec. 3. */
+enum {
+  FM_R4 = 0,         /* Eq. Frac4ci/Frac4bi, alpha = 5, exp, 4 solves          */
+  FM_R4_PHI1 = 1,    /* Sec. 4.1, alpha = 6, phi_1, 4 solves                   */
+  FM_R4_PHI1_A5 = 2, /* alpha = 5 nodes, phi_1 weights (shares R4's solves)    */
+  FM_R8 = 3,         /* Eq. Frac8ci/Frac8bi, alpha = 5, exp, 8 solves           */
+  FM_R8_PHI1 = 4,    /* R8 nodes, phi_1 weights (shares R8's solves)            */
+  FM_R5 = 5,         /* Eq. Frac5bi0, exp, 5 solves                             */
+  FM_R10 = 6,        /* Eq. Frac10ci/Frac10bi, hybrid, 10 solves + B^2          */
+  FM_R10_STAR = 7,   /* Eq. Frac10ciNO/Frac10biNO, hybrid, 10 solves + B^2      */
+  FM_PADE22 = 8,     /* Eq. Pade4, one conjugate pair                           */
+  FM_PADE22_PHI1 = 9 /* Eq. Pade4phi1, one conjugate pair                       */
+};
+#define FM_NUM_BUILTIN 10
+
+/* Fill *out with built-in set id.  The arrays point to static storage that
+ * stays valid for the life of the process.  Returns FM_EINVAL for a bad id. */
+fm_status fm_coeffs_builtin(int id, fm_coeffs* out);
+
+/* Forward bound eps(x) = sum_{k>order} |a_k - alpha_k| x^k (Sec. 3) of a set
+ * against target function func (0 = exp, 1 = phi_1), and the x at which it
+ * reaches tol.  Host computation in extended precision.  Returns FM_EINVAL on
+ * bad arguments. */
+fm_status fm_theta(const fm_coeffs* cs, int func, double tol, double* theta_out);
+
+enum { FM_FP64 = 0, FM_FP32_IR = 1 };   /* precision of the shifted solves      */
+enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       */
+
+typedef struct {
+  int precision;      /* FM_FP64: every step in double.  FM_FP32_IR: factor and
+                         solve in single, then max_ir_iters steps of iterative
+                         refinement with double-accurate residuals.            */
+  int form;           /* FM_ROUNDOFF (default) or FM_PLAIN                      */
+  int max_ir_iters;   /* refinement steps for FM_FP32_IR (default 2)            */
+  double ir_tol;      /* info = -1 when the last correction exceeds ir_tol times
+                         the solution (max norms); 0 disables (default 1e-8)    */
+  double anorm;       /* > 0: use anorm*|t| in place of ||tA||_1 to pick s / N  */
+  int s_fixed;        /* >= 0: force s for matrix functions (default -1)        */
+  long nsteps;        /* > 0: force N for actions (default 0)                   */
+  void* workspace;    /* device scratch or NULL                                 */
+  size_t workspace_bytes;
+} fm_opts;
+
+/* Defaults: FM_FP32_IR, FM_ROUNDOFF, 2 refinement steps, ir_tol 1e-8, automatic
+ * s and N, library-managed workspace. */
+void fm_opts_default(fm_opts* o);
+
+/* Job kinds for fm_workspace_size. */
+enum { FM_JOB_EXPM = 0, FM_JOB_PHI1 = 1, FM_JOB_EXPMV = 2, FM_JOB_PHI1MV = 3,
+       FM_JOB_ZEXPM = 4, FM_JOB_ZEXPMV = 5, FM_JOB_EXPMV_ADJ = 6 };
+
+/* Bytes of device scratch a call of that job needs for matrices up to dmax, m
+ * vectors, k terms, on the current device. */
+size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_opts* opts);
+
+/* Largest d the kernels accept (same for every job). */
+int fm_max_dim(void);
+
+/* ---- single matrix ------------------------------------------------------ */
+
+/* F = exp(tA) ~ r(B)^(2^s), B = tA/2^s (Sec. 1, Eq. ParallRoundOff).
+ * A: d x d (lda), F: d x d (ldf).  info_host (nullable, host): per-matrix status,
+ * valid after the stream is synchronized; s_host (nullable, host): chosen s. */
+fm_status fm_expm(const fm_coeffs* cs, int d, const double* A, int lda, double t, double* F,
+                  int ldf, const fm_opts* opts, void* stream, int* info_host, int* s_host);
+
+/* Phi = phi_1(tA) and (if E != NULL) E = exp(tA), both from the same resolvents
+ * (Sec. 2: one set of solves, two sets of weights), then s doublings
+ * (Phi, E) <- ((E + I) Phi / 2, E^2) (Sec. 1).  theta = min of the two sets. */
+fm_status fm_phi1(const fm_coeffs* ce, const fm_coeffs* cphi, int d, const double* A, int lda,
+                  double t, double* Phi, int ldp, double* E, int lde, const fm_opts* opts,
+                  void* stream, int* info_host, int* s_host);
+
+/* W = exp(tA) V by N steps W <- r(B) W, B = tA/N, with one factorization per
+ * term reused by all steps and all m columns (Sec. 1, 2; Eq. Frac10R: one
+ * product B W per step).  V, W: d x m (ldv, ldw). */
+fm_status fm_expmv(const fm_coeffs* cs, int d, const double* A, int lda, double t, int m,
+                   const double* V, int ldv, double* W, int ldw, const fm_opts* opts,
+                   void* stream, int* info_host, long* nsteps_host);
+
+/* W = phi_1(tA) V: phi_1(tA) by fm_phi1's doubling, then one product. */
+fm_status fm_phi1mv(const fm_coeffs* ce, const fm_coeffs* cphi, int d, const double* A, int lda,
+                    double t, int m, const double* V, int ldv, double* W, int ldw,
+                    const fm_opts* opts, void* stream, int* info_host, int* s_host);
+
+/* Complex variants: A, V, F, W interleaved complex double; c_i, b_i complex
+ * (conj_pair must be 0). */
+fm_status fm_zexpm(const fm_coeffs* cs, int d, const double* A, int lda, double t, double* F,
+                   int ldf, const fm_opts* opts, void* stream, int* info_host, int* s_host);
+fm_status fm_zexpmv(const fm_coeffs* cs, int d, const double* A, int lda, double t, int m,
+                    const double* V, int ldv, double* W, int ldw, const fm_opts* opts,
+                    void* stream, int* info_host, long* nsteps_host);
+
+/* ---- batches of independent matrices (one launch) ------------------------ */
+/* Matrix b has order d_dev[b] <= dmax and is stored densely (leading dimension
+ * d_dev[b]) at A + off_dev[b] (elements; complex: complex elements); its result
+ * goes to the same offset of F (or Phi/E/W; for actions V and W use voff_dev
+ * with leading dimension m).  t_dev[b] is its time.  info_dev[b] receives its
+ * status and s_dev[b] (nullable) its s or N.  Work is ordered largest d first
+ * and spread over persistent CTAs, one matrix per CTA at a time. */
+fm_status fm_expm_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                          const int64_t* off_dev, const double* A, const double* t_dev,
+                          double* F, int* info_dev, int* s_dev, const fm_opts* opts,
+                          void* stream);
+fm_status fm_phi1_batched(const fm_coeffs* ce, const fm_coeffs* cphi, int batch, int dmax,
+                          const int* d_dev, const int64_t* off_dev, const double* A,
+                          const double* t_dev, double* Phi, double* E, int* info_dev,
+                          int* s_dev, const fm_opts* opts, void* stream);
+fm_status fm_expmv_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                           const int64_t* off_dev, const double* A, const double* t_dev, int m,
+                           const int64_t* voff_dev, const double* V, double* W, int* info_dev,
+                           int* s_dev, const fm_opts* opts, void* stream);
+fm_status fm_phi1mv_batched(const fm_coeffs* ce, const fm_coeffs* cphi, int batch, int dmax,
+                            const int* d_dev, const int64_t* off_dev, const double* A,
+                            const double* t_dev, int m, const int64_t* voff_dev,
+                            const double* V, double* W, int* info_dev, int* s_dev,
+                            const fm_opts* opts, void* stream);
+fm_status fm_zexpm_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                           const int64_t* off_dev, const double* A, const double* t_dev,
+                           double* F, int* info_dev, int* s_dev, const fm_opts* opts,
+                           void* stream);
+fm_status fm_zexpmv_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                            const int64_t* off_dev, const double* A, const double* t_dev, int m,
+                            const int64_t* voff_dev, const double* V, double* W, int* info_dev,
+                            int* s_dev, const fm_opts* opts, void* stream);
+
+/* ---- adjoint of the action (real, roundoff form, one vector) ----------- */
+/* For each matrix of the batch: the forward map w_0 = v, w_q = r(B) w_{q-1}
+ * (q = 1..N, B = tA/N with N = nsteps_dev[b] fixed, as fm_expmv computes it),
+ * and given wbar = dL/dw_N, the gradients Abar = dL/dA (d x d at off_dev[b]) and
+ * vbar = dL/dv (d at voff_dev[b]).  The reverse sweep reuses the forward
+ * factorizations: lambda = M_i^{-T} (b_i wbar_q), Bbar += c_i lambda Y_iq^T,
+ * ubar = sum c_i lambda, Bbar += ubar w_{q-1}^T, wbar_{q-1} = a0 wbar_q + B^T ubar.
+ * W receives w_N.  Always double precision. */
+fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                                   const int64_t* off_dev, const double* A, const double* t_dev,
+                                   const long* nsteps_dev, const int64_t* voff_dev,
+                                   const double* v, const double* wbar, double* W,
+                                   double* Abar, double* vbar, int* info_dev,
+                                   const fm_opts* opts, void* stream);
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char* fm_last_error(void);
+
+/* Library version string. */
+const char* fm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FM_H_ */

@@ -1,0 +1,460 @@
+// cta_la.cuh -- dense linear algebra executed by ONE thread block (CTA) on
+// matrices that live in global memory (L2-resident working sets), with shared
+// memory staging.  Used by the persistent kernels: each CTA owns one matrix
+// of the batch at a time and runs every step of the method on it.
+//
+// Routines (all called by all NT threads of the CTA, with matching arguments):
+//   cta_gemm     C = alpha A B + beta C        (64x64 tiles, 4x4 per thread)
+//   cta_getrf    blocked right-looking LU with partial pivoting (LAPACK order:
+//                piv[k] = row exchanged with row k at step k)
+//   cta_getrs    solve (P^T L U) X = X, m right-hand sides, blocked
+//   cta_getrs_t  solve (P^T L U)^T x = x, one right-hand side
+// The factorization is the "LU decomposition and triangular solves" route the
+// paper takes for each (I - c_i B)^{-1} (Sec. 1, first bullet of the dense case).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fmk {
+
+constexpr int NT = 256;  // threads per CTA for every routine here
+
+struct zd { double x, y; };
+struct zf { float x, y; };
+
+// ---------------------------------------------------------------------------
+// scalar traits
+// ---------------------------------------------------------------------------
+template <class T> struct Tr;
+
+template <> struct Tr<double> {
+  using R = double;
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double one() { return 1.0; }
+  static __device__ __forceinline__ double mag(double a) { return fabs(a); }
+  static __device__ __forceinline__ void mac(double& c, double a, double b) { c = fma(a, b, c); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double rscale(double a, double s) { return __dmul_rn(a, s); }
+  static __device__ __forceinline__ bool is_zero(double a) { return a == 0.0; }
+  static __device__ __forceinline__ bool finite(double a) { return isfinite(a); }
+};
+
+template <> struct Tr<float> {
+  using R = float;
+  static __device__ __forceinline__ float zero() { return 0.0f; }
+  static __device__ __forceinline__ float one() { return 1.0f; }
+  static __device__ __forceinline__ float mag(float a) { return fabsf(a); }
+  static __device__ __forceinline__ void mac(float& c, float a, float b) { c = fmaf(a, b, c); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return a / b; }
+  static __device__ __forceinline__ float rscale(float a, float s) { return __fmul_rn(a, s); }
+  static __device__ __forceinline__ bool is_zero(float a) { return a == 0.0f; }
+  static __device__ __forceinline__ bool finite(float a) { return isfinite(a); }
+};
+
+template <> struct Tr<zd> {
+  using R = double;
+  static __device__ __forceinline__ zd zero() { return {0.0, 0.0}; }
+  static __device__ __forceinline__ zd one() { return {1.0, 0.0}; }
+  static __device__ __forceinline__ double mag(zd a) { return hypot(a.x, a.y); }
+  static __device__ __forceinline__ void mac(zd& c, zd a, zd b) {
+    c.x = fma(a.x, b.x, c.x);
+    c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y);
+    c.y = fma(a.y, b.x, c.y);
+  }
+  static __device__ __forceinline__ zd mul(zd a, zd b) {
+    return {__dsub_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)),
+            __dadd_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x))};
+  }
+  static __device__ __forceinline__ zd add(zd a, zd b) { return {__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)}; }
+  static __device__ __forceinline__ zd sub(zd a, zd b) { return {__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)}; }
+  static __device__ __forceinline__ zd div(zd a, zd b) {
+    // scaled division (Smith): avoids overflow of |b|^2
+    if (fabs(b.x) >= fabs(b.y)) {
+      double r = b.y / b.x, den = b.x + b.y * r;
+      return {(a.x + a.y * r) / den, (a.y - a.x * r) / den};
+    } else {
+      double r = b.x / b.y, den = b.x * r + b.y;
+      return {(a.x * r + a.y) / den, (a.y * r - a.x) / den};
+    }
+  }
+  static __device__ __forceinline__ zd rscale(zd a, double s) { return {__dmul_rn(a.x, s), __dmul_rn(a.y, s)}; }
+  static __device__ __forceinline__ bool is_zero(zd a) { return a.x == 0.0 && a.y == 0.0; }
+  static __device__ __forceinline__ bool finite(zd a) { return isfinite(a.x) && isfinite(a.y); }
+};
+
+template <> struct Tr<zf> {
+  using R = float;
+  static __device__ __forceinline__ zf zero() { return {0.0f, 0.0f}; }
+  static __device__ __forceinline__ zf one() { return {1.0f, 0.0f}; }
+  static __device__ __forceinline__ float mag(zf a) { return hypotf(a.x, a.y); }
+  static __device__ __forceinline__ void mac(zf& c, zf a, zf b) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+  }
+  static __device__ __forceinline__ zf mul(zf a, zf b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+  }
+  static __device__ __forceinline__ zf add(zf a, zf b) { return {a.x + b.x, a.y + b.y}; }
+  static __device__ __forceinline__ zf sub(zf a, zf b) { return {a.x - b.x, a.y - b.y}; }
+  static __device__ __forceinline__ zf div(zf a, zf b) {
+    if (fabsf(b.x) >= fabsf(b.y)) {
+      float r = b.y / b.x, den = b.x + b.y * r;
+      return {(a.x + a.y * r) / den, (a.y - a.x * r) / den};
+    } else {
+      float r = b.x / b.y, den = b.x * r + b.y;
+      return {(a.x * r + a.y) / den, (a.y * r - a.x) / den};
+    }
+  }
+  static __device__ __forceinline__ zf rscale(zf a, float s) { return {a.x * s, a.y * s}; }
+  static __device__ __forceinline__ bool is_zero(zf a) { return a.x == 0.0f && a.y == 0.0f; }
+  static __device__ __forceinline__ bool finite(zf a) { return isfinite(a.x) && isfinite(a.y); }
+};
+
+// conversions between the working (high) and factorization (low) types
+template <class D, class S> __device__ __forceinline__ D cvt(S a);
+template <> __device__ __forceinline__ double cvt<double, double>(double a) { return a; }
+template <> __device__ __forceinline__ float cvt<float, double>(double a) { return __double2float_rn(a); }
+template <> __device__ __forceinline__ double cvt<double, float>(float a) { return (double)a; }
+template <> __device__ __forceinline__ float cvt<float, float>(float a) { return a; }
+template <> __device__ __forceinline__ zd cvt<zd, zd>(zd a) { return a; }
+template <> __device__ __forceinline__ zf cvt<zf, zd>(zd a) { return {__double2float_rn(a.x), __double2float_rn(a.y)}; }
+template <> __device__ __forceinline__ zd cvt<zd, zf>(zf a) { return {(double)a.x, (double)a.y}; }
+template <> __device__ __forceinline__ zf cvt<zf, zf>(zf a) { return a; }
+
+// ---------------------------------------------------------------------------
+// block reductions
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R cta_max(R v, R* red) {
+  for (int o = 16; o; o >>= 1) {
+    R w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (w > v || isnan(w)) ? w : v;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R m = red[0];
+    for (int w = 1; w < NT / 32; ++w) m = (red[w] > m || isnan(red[w])) ? red[w] : m;
+    red[0] = m;
+  }
+  __syncthreads();
+  R r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int cta_or(int v, int* red) {
+  v = __any_sync(0xffffffffu, v) ? 1 : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  int r = 0;
+  for (int w = 0; w < NT / 32; ++w) r |= red[w];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// GEMM: C[M x N] = alpha * A[M x K] * B[K x N] + beta * C  (row-major, ld*)
+// beta == 0 means C is not read.  smem: 2 * 16 * 68 elements of T.
+// ---------------------------------------------------------------------------
+constexpr int GT = 64, GK = 16, GLD = 68;
+
+template <class T>
+__device__ __noinline__ void cta_gemm(int M, int N, int K, typename Tr<T>::R alpha, const T* __restrict__ A,
+                         int lda, const T* __restrict__ B, int ldb, typename Tr<T>::R beta,
+                         T* C, int ldc, T* smem) {
+  using TT = Tr<T>;
+  T* sA = smem;             // [GK][GLD]  sA[k][m]
+  T* sB = smem + GK * GLD;  // [GK][GLD]  sB[k][n]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += GT)
+    for (int n0 = 0; n0 < N; n0 += GT) {
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = TT::zero();
+      for (int k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+        for (int e0 = 0; e0 < GT * GK; e0 += NT) {
+          int e = e0 + tid;
+          int r = e >> 4, kk = e & 15;
+          int gr = m0 + r, gk = k0 + kk;
+          sA[kk * GLD + r] = (gr < M && gk < K) ? A[(size_t)gr * lda + gk] : TT::zero();
+          int kb = e >> 6, c = e & 63;
+          int gkb = k0 + kb, gc = n0 + c;
+          sB[kb * GLD + c] = (gkb < K && gc < N) ? B[(size_t)gkb * ldb + gc] : TT::zero();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+          T a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = sA[kk * GLD + ty * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = sB[kk * GLD + tx * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) TT::mac(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int r = m0 + ty * 4 + i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int c = n0 + tx * 4 + j;
+          if (c >= N) continue;
+          T v = TT::rscale(acc[i][j], alpha);
+          if (beta != 0) v = TT::add(TT::rscale(C[(size_t)r * ldc + c], beta), v);
+          C[(size_t)r * ldc + c] = v;
+        }
+      }
+    }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// LU with partial pivoting, blocked right-looking, panel width NB.
+// A: n x n (lda) in global memory, overwritten by L (unit, below) and U.
+// piv: n ints (global).  Returns 0 or (first column with an exactly zero
+// pivot) + 1.  smem: n*NB panel + GEMM tiles + reduction scratch.
+// ---------------------------------------------------------------------------
+template <class T, int NB>
+__device__ __noinline__ int cta_getrf(int n, T* A, int lda, int* piv, T* smem) {
+  using TT = Tr<T>;
+  using R = typename TT::R;
+  T* P = smem;                              // panel [n][NB]
+  T* gsm = smem + (size_t)n * NB;           // GEMM tiles
+  R* red = (R*)(gsm + 2 * GK * GLD);        // reduction scratch (8 R + 8 int)
+  int* redi = (int*)(red + 8);
+  __shared__ int s_piv, s_info;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_info = 0;
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int jb = min(NB, n - j0);
+    const int rows = n - j0;
+    // 1. load the panel
+    for (int e = tid; e < rows * NB; e += NT) {
+      int r = e / NB, c = e % NB;
+      P[e] = (c < jb) ? A[(size_t)(j0 + r) * lda + j0 + c] : TT::zero();
+    }
+    __syncthreads();
+    // 2. unblocked GEPP inside the panel
+    for (int jj = 0; jj < jb; ++jj) {
+      R best = -1;
+      int bi = 0x7fffffff;
+      for (int r = jj + tid; r < rows; r += NT) {
+        R v = TT::mag(P[r * NB + jj]);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o; o >>= 1) {
+        R ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if ((tid & 31) == 0) { red[tid >> 5] = best; redi[tid >> 5] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        R bb = red[0];
+        int ii = redi[0];
+        for (int w = 1; w < NT / 32; ++w)
+          if (red[w] > bb || (red[w] == bb && redi[w] < ii)) { bb = red[w]; ii = redi[w]; }
+        if (ii == 0x7fffffff) ii = jj;  // all NaN: keep the diagonal
+        s_piv = ii;
+        piv[j0 + jj] = j0 + ii;
+      }
+      __syncthreads();
+      const int p = s_piv;
+      if (p != jj && tid < NB) {
+        T t = P[jj * NB + tid];
+        P[jj * NB + tid] = P[p * NB + tid];
+        P[p * NB + tid] = t;
+      }
+      __syncthreads();
+      const T pv = P[jj * NB + jj];
+      const bool zero = TT::is_zero(pv);
+      if (zero && tid == 0 && s_info == 0) s_info = j0 + jj + 1;
+      for (int r = jj + 1 + tid; r < rows; r += NT) {
+        T l = P[r * NB + jj];
+        if (!zero) l = TT::div(l, pv);
+        P[r * NB + jj] = l;
+        for (int c = jj + 1; c < jb; ++c) {
+          T v = P[r * NB + c];
+          T u = P[jj * NB + c];
+          v = TT::sub(v, TT::mul(l, u));
+          P[r * NB + c] = v;
+        }
+      }
+      __syncthreads();
+    }
+    // 3. write the panel back
+    for (int e = tid; e < rows * jb; e += NT) {
+      int r = e / jb, c = e % jb;
+      A[(size_t)(j0 + r) * lda + j0 + c] = P[r * NB + c];
+    }
+    // 4. apply the panel's row exchanges to the other columns (thread owns columns)
+    for (int c = tid; c < n - jb; c += NT) {
+      int col = c < j0 ? c : c + jb;
+      for (int jj = 0; jj < jb; ++jj) {
+        int p = piv[j0 + jj];
+        if (p != j0 + jj) {
+          T t = A[(size_t)(j0 + jj) * lda + col];
+          A[(size_t)(j0 + jj) * lda + col] = A[(size_t)p * lda + col];
+          A[(size_t)p * lda + col] = t;
+        }
+      }
+    }
+    __syncthreads();
+    // 5. U12 = L11^{-1} A12 (rows j0..j0+jb, columns j0+jb..n)
+    for (int c = j0 + jb + tid; c < n; c += NT) {
+      T x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = (r < jb) ? A[(size_t)(j0 + r) * lda + c] : TT::zero();
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+#pragma unroll
+        for (int l = 0; l < r; ++l) x[r] = TT::sub(x[r], TT::mul(P[r * NB + l], x[l]));
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < jb) A[(size_t)(j0 + r) * lda + c] = x[r];
+    }
+    __syncthreads();
+    // 6. trailing update A22 -= L21 U12
+    if (j0 + jb < n)
+      cta_gemm<T>(n - j0 - jb, n - j0 - jb, jb, (R)-1, A + (size_t)(j0 + jb) * lda + j0, lda,
+                  A + (size_t)j0 * lda + j0 + jb, lda, (R)1, A + (size_t)(j0 + jb) * lda + j0 + jb,
+                  lda, gsm);
+    __syncthreads();
+  }
+  __syncthreads();
+  int info = s_info;
+  __syncthreads();
+  return info;
+}
+
+// ---------------------------------------------------------------------------
+// Solve (P^T L U) X = X for X: n x m (ldx), LU from cta_getrf.
+// ---------------------------------------------------------------------------
+template <class T, int NB>
+__device__ __noinline__ void cta_getrs(int n, const T* LU, int lda, const int* piv, int m, T* X, int ldx,
+                          T* smem) {
+  using TT = Tr<T>;
+  using R = typename TT::R;
+  T* Lb = smem;                 // NB x NB diagonal block
+  T* gsm = smem + NB * NB;      // GEMM tiles
+  const int tid = threadIdx.x;
+  // row exchanges, in order (thread owns columns)
+  for (int c = tid; c < m; c += NT)
+    for (int k = 0; k < n; ++k) {
+      int p = piv[k];
+      if (p != k) {
+        T t = X[(size_t)k * ldx + c];
+        X[(size_t)k * ldx + c] = X[(size_t)p * ldx + c];
+        X[(size_t)p * ldx + c] = t;
+      }
+    }
+  __syncthreads();
+  // forward: unit lower
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int jb = min(NB, n - j0);
+    for (int e = tid; e < NB * NB; e += NT) {
+      int r = e / NB, c = e % NB;
+      Lb[e] = (r < jb && c < jb) ? LU[(size_t)(j0 + r) * lda + j0 + c] : TT::zero();
+    }
+    __syncthreads();
+    for (int c = tid; c < m; c += NT) {
+      T x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = (r < jb) ? X[(size_t)(j0 + r) * ldx + c] : TT::zero();
+#pragma unroll
+      for (int r = 1; r < NB; ++r) {
+#pragma unroll
+        for (int l = 0; l < r; ++l) x[r] = TT::sub(x[r], TT::mul(Lb[r * NB + l], x[l]));
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < jb) X[(size_t)(j0 + r) * ldx + c] = x[r];
+    }
+    __syncthreads();
+    if (j0 + jb < n)
+      cta_gemm<T>(n - j0 - jb, m, jb, (R)-1, LU + (size_t)(j0 + jb) * lda + j0, lda,
+                  X + (size_t)j0 * ldx, ldx, (R)1, X + (size_t)(j0 + jb) * ldx, ldx, gsm);
+    __syncthreads();
+  }
+  // backward: upper
+  for (int j0 = ((n - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
+    const int jb = min(NB, n - j0);
+    for (int e = tid; e < NB * NB; e += NT) {
+      int r = e / NB, c = e % NB;
+      Lb[e] = (r < jb && c < jb) ? LU[(size_t)(j0 + r) * lda + j0 + c] : TT::one();
+    }
+    __syncthreads();
+    for (int c = tid; c < m; c += NT) {
+      T x[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) x[r] = (r < jb) ? X[(size_t)(j0 + r) * ldx + c] : TT::zero();
+#pragma unroll
+      for (int r = NB - 1; r >= 0; --r) {
+#pragma unroll
+        for (int l = r + 1; l < NB; ++l) x[r] = TT::sub(x[r], TT::mul(Lb[r * NB + l], x[l]));
+        x[r] = TT::div(x[r], Lb[r * NB + r]);
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < jb) X[(size_t)(j0 + r) * ldx + c] = x[r];
+    }
+    __syncthreads();
+    if (j0 > 0)
+      cta_gemm<T>(j0, m, jb, (R)-1, LU + j0, lda, X + (size_t)j0 * ldx, ldx, (R)1, X, ldx, gsm);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Solve (P^T L U)^T x = x for one vector x (length n, global), real types.
+// U^T z = x (forward), L^T w = z (backward), then the exchanges in reverse.
+// Column-oriented: after x_i is final, every later entry is updated.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __noinline__ void cta_getrs_t(int n, const T* LU, int lda, const int* piv, T* x) {
+  using TT = Tr<T>;
+  const int tid = threadIdx.x;
+  for (int i = 0; i < n; ++i) {
+    if (tid == 0) x[i] = TT::div(x[i], LU[(size_t)i * lda + i]);
+    __syncthreads();
+    T xi = x[i];
+    for (int l = i + 1 + tid; l < n; l += NT) x[l] = TT::sub(x[l], TT::mul(LU[(size_t)i * lda + l], xi));
+    __syncthreads();
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    T xi = x[i];
+    for (int l = tid; l < i; l += NT) x[l] = TT::sub(x[l], TT::mul(LU[(size_t)i * lda + l], xi));
+    __syncthreads();
+  }
+  if (tid == 0)
+    for (int k = n - 1; k >= 0; --k) {
+      int p = piv[k];
+      if (p != k) { T t = x[k]; x[k] = x[p]; x[p] = t; }
+    }
+  __syncthreads();
+}
+
+}  // namespace fmk

@@ -1,0 +1,594 @@
+// fm_api.cu -- the C ABI (include/fm.h): argument checks, coefficient packing,
+// scratch management and kernel launches.  Every numerical step runs in the
+// kernels of fm_kernels.cuh; this file only marshals.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/fm.h"
+#include "fm_job.h"
+#include "fm_launch.h"
+
+using namespace fmk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+fm_status fail(fm_status s, const char* msg) {
+  snprintf(g_err, sizeof g_err, "%s", msg);
+  return s;
+}
+
+fm_status cuda_fail(cudaError_t e, const char* where) {
+  snprintf(g_err, sizeof g_err, "%s: %s", where, cudaGetErrorString(e));
+  return FM_ECUDA;
+}
+
+// ---- library-managed scratch (one buffer per device, grown on demand) -----
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_mu;
+std::vector<DevBuf> g_bufs;
+
+fm_status get_scratch(size_t need, const fm_opts* o, void** out, cudaStream_t st) {
+  if (o && o->workspace) {
+    if (o->workspace_bytes < need) return fail(FM_ENOMEM, "opts.workspace is smaller than fm_workspace_size()");
+    *out = o->workspace;
+    return FM_OK;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if ((int)g_bufs.size() <= dev) g_bufs.resize(dev + 1);
+  DevBuf& b = g_bufs[dev];
+  if (b.bytes < need) {
+    if (b.p) {
+      // the previous buffer may still be in use by earlier work on any stream
+      cudaDeviceSynchronize();
+      cudaFree(b.p);
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    size_t sz = need + need / 4;
+    e = cudaMalloc(&b.p, sz);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FM_ENOMEM, "cudaMalloc of the library scratch failed");
+    }
+    b.bytes = sz;
+  }
+  (void)st;
+  *out = b.p;
+  return FM_OK;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+int pick_nb(int dmax) { return dmax <= 512 ? 16 : 8; }
+
+// ---- coefficient packing ----------------------------------------------------
+fm_status pack_one(const fm_coeffs* cs, int f, bool complex_ok, FmCoef& cf) {
+  if (!cs) return fail(FM_EINVAL, "coefficient set is NULL");
+  if (cs->k < 1 || cs->k > FM_MAX_TERMS) return fail(FM_EINVAL, "coefficient set: k must be in [1, 16]");
+  if (!cs->c_re || !cs->b_re) return fail(FM_EINVAL, "coefficient set: c_re and b_re are required");
+  if (cs->conj_pair) return fail(FM_EINVAL, "conjugate-pair sets are not supported by the CUDA kernels");
+  for (int i = 0; i < cs->k; ++i) {
+    double ci = cs->c_im ? cs->c_im[i] : 0.0, bi = cs->b_im ? cs->b_im[i] : 0.0;
+    if (!isfinite(cs->c_re[i]) || !isfinite(ci) || !isfinite(cs->b_re[i]) || !isfinite(bi))
+      return fail(FM_EINVAL, "coefficient set: non-finite value");
+    if (!complex_ok && (ci != 0.0 || bi != 0.0))
+      return fail(FM_EINVAL, "complex c_i or b_i need the complex (z) entry points");
+    if (f == 0) {
+      cf.c_re[i] = cs->c_re[i];
+      cf.c_im[i] = ci;
+    } else if (cf.c_re[i] != cs->c_re[i] || cf.c_im[i] != ci) {
+      return fail(FM_EINVAL, "the two coefficient sets must share the same nodes c_i");
+    }
+    cf.b_re[f][i] = cs->b_re[i];
+    cf.b_im[f][i] = bi;
+  }
+  if (f == 1 && cs->k != cf.k) return fail(FM_EINVAL, "the two coefficient sets must have the same k");
+  cf.k = cs->k;
+  cf.a0[f] = cs->a0;
+  cf.d1[f] = cs->d1;
+  cf.d2[f] = cs->d2;
+  if (!isfinite(cs->a0) || !isfinite(cs->d1) || !isfinite(cs->d2))
+    return fail(FM_EINVAL, "coefficient set: non-finite a0/d1/d2");
+  double th = cs->theta;
+  if (!(th > 0) || !isfinite(th)) {
+    if (fm_theta(cs, f, ldexp(1.0, -53), &th) != FM_OK || !(th > 0))
+      return fail(FM_EINVAL, "coefficient set: theta must be positive");
+  }
+  cf.theta = (f == 0) ? th : fmin(cf.theta, th);
+  return FM_OK;
+}
+
+fm_status pack(const fm_coeffs* ce, const fm_coeffs* cp, bool complex_ok, int form, FmCoef& cf) {
+  memset(&cf, 0, sizeof cf);
+  fm_status s = pack_one(ce, 0, complex_ok, cf);
+  if (s) return s;
+  cf.nfun = 1;
+  if (cp) {
+    s = pack_one(cp, 1, complex_ok, cf);
+    if (s) return s;
+    cf.nfun = 2;
+  }
+  if (form == FM_PLAIN)
+    for (int f = 0; f < cf.nfun; ++f)
+      for (int i = 0; i < cf.k; ++i)
+        if (cf.b_im[f][i] != 0.0) return fail(FM_EINVAL, "the plain form needs real weights b_i");
+  return FM_OK;
+}
+
+fm_opts resolve_opts(const fm_opts* o) {
+  fm_opts r;
+  fm_opts_default(&r);
+  if (o) r = *o;
+  return r;
+}
+
+fm_status check_opts(const fm_opts& o) {
+  if (o.precision != FM_FP64 && o.precision != FM_FP32_IR) return fail(FM_EINVAL, "opts.precision");
+  if (o.form != FM_ROUNDOFF && o.form != FM_PLAIN) return fail(FM_EINVAL, "opts.form");
+  if (o.max_ir_iters < 0 || o.max_ir_iters > 20) return fail(FM_EINVAL, "opts.max_ir_iters must be in [0, 20]");
+  if (!(o.ir_tol >= 0) || !isfinite(o.anorm) || o.anorm < 0) return fail(FM_EINVAL, "opts.ir_tol / opts.anorm");
+  if (o.s_fixed > 1000) return fail(FM_EINVAL, "opts.s_fixed");
+  if (o.nsteps < 0) return fail(FM_EINVAL, "opts.nsteps");
+  return FM_OK;
+}
+
+// element sizes of the working and factorization types
+void type_sizes(bool cplx, int precision, size_t& elt, size_t& lelt) {
+  elt = cplx ? 16 : 8;
+  lelt = precision == FM_FP64 ? elt : elt / 2;
+}
+
+size_t smem_for(bool cplx, int nb, int dmax) { return launch_smem(cplx, nb, dmax); }
+
+struct Plan {
+  int grid;
+  int nb;
+  size_t smem;
+  size_t per_cta;
+  size_t header;
+  size_t total;
+};
+
+Plan make_plan(int kind, bool cplx, int precision, int batch, int dmax, int m, int k, long long nmax) {
+  Plan p;
+  p.nb = pick_nb(dmax);
+  p.smem = smem_for(cplx, p.nb, dmax);
+  size_t elt, lelt;
+  type_sizes(cplx, precision, elt, lelt);
+  int lk = kind == JOB_PHI1MV ? JOB_PHI1 : kind;
+  p.per_cta = fm_align(ws_layout(lk, dmax, m, k, elt, lelt, nmax).total);
+  int occ = launch_occupancy(cplx, precision, p.nb, p.smem);
+  if (occ < 1) occ = 1;
+  long long g = (long long)num_sms() * occ;
+  if (g > batch) g = batch;
+  if (g < 1) g = 1;
+  p.grid = (int)g;
+  p.header = 256 + fm_align((size_t)batch * 4);
+  p.total = p.header + (size_t)p.grid * p.per_cta;
+  return p;
+}
+
+struct Call {
+  int kind;
+  bool cplx;
+  const fm_coeffs* ce;
+  const fm_coeffs* cp;
+  int batch, dmax, m;
+  const int* d_dev;
+  const int64_t* off;
+  const int64_t* voff;
+  int d1, lda, ldf, lde, ldv, ldw;
+  const double* t_dev;
+  double t1;
+  const void* A;
+  void* F;
+  void* E;
+  const void* V;
+  void* W;
+  int* info_dev;
+  int* s_dev;
+  const long* nsteps_dev;
+  long long nsteps_max;
+  const double* wbar;
+  double* Abar;
+  double* vbar;
+  int* info_host;
+  int* s_host;
+  long* n_host;
+};
+
+fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
+  fm_opts o = resolve_opts(optsp);
+  fm_status s = check_opts(o);
+  if (s) return s;
+  if (c.kind == JOB_ADJ) o.precision = FM_FP64;
+  if (c.batch < 1) return fail(FM_ESHAPE, "batch must be >= 1");
+  if (c.dmax < 1 || c.dmax > fm_max_dim()) return fail(FM_ESHAPE, "d (or dmax) must be in [1, fm_max_dim()]");
+  if ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV) && c.m < 1) return fail(FM_ESHAPE, "m must be >= 1");
+  if (!c.A) return fail(FM_EINVAL, "A is NULL");
+  if ((c.kind == JOB_EXPM || c.kind == JOB_PHI1) && !c.F) return fail(FM_EINVAL, "output is NULL");
+  if ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV || c.kind == JOB_ADJ) && (!c.V || !c.W))
+    return fail(FM_EINVAL, "V / W is NULL");
+  if (c.d_dev) {
+    if (!c.off || !c.t_dev) return fail(FM_EINVAL, "batched calls need off_dev and t_dev");
+    if ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV || c.kind == JOB_ADJ) && !c.voff)
+      return fail(FM_EINVAL, "batched actions need voff_dev");
+  } else {
+    const int n = c.d1;
+    if (c.lda < n || ((c.kind == JOB_EXPM || c.kind == JOB_PHI1) && c.ldf < n) ||
+        (c.E && c.lde < n) ||
+        ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV) && (c.ldv < c.m || c.ldw < c.m)))
+      return fail(FM_ESHAPE, "leading dimension smaller than the row length");
+    if (!isfinite(c.t1)) {
+      // reported per matrix (info = -2) like a non-finite entry
+    }
+  }
+  FmCoef cf;
+  s = pack(c.ce, c.cp, c.cplx, o.form, cf);
+  if (s) return s;
+
+  Plan p = make_plan(c.kind, c.cplx, o.precision, c.batch, c.dmax, c.m, cf.k, c.nsteps_max);
+  void* ws = nullptr;
+  s = get_scratch(p.total, &o, &ws, st);
+  if (s) return s;
+
+  FmJob J;
+  memset(&J, 0, sizeof J);
+  J.kind = c.kind;
+  J.precision = o.precision;
+  J.form = o.form;
+  J.max_ir = o.max_ir_iters;
+  J.ir_tol = o.ir_tol;
+  J.anorm = o.anorm;
+  J.s_fixed = o.s_fixed;
+  J.nsteps = o.nsteps;
+  J.nsteps_max = c.nsteps_max;
+  J.batch = c.batch;
+  J.dmax = c.dmax;
+  J.m = c.m;
+  J.d = c.d_dev;
+  J.off = c.off;
+  J.voff = c.voff;
+  J.d1 = c.d1;
+  J.lda = c.lda;
+  J.ldf = c.ldf;
+  J.lde = c.lde;
+  J.ldv = c.ldv;
+  J.ldw = c.ldw;
+  J.t = c.t_dev;
+  J.t1 = c.t1;
+  J.A = c.A;
+  J.F = c.F;
+  J.E = c.E;
+  J.V = c.V;
+  J.W = c.W;
+  J.nsteps_dev = (const long long*)c.nsteps_dev;
+  J.wbar = c.wbar;
+  J.Abar = c.Abar;
+  J.vbar = c.vbar;
+  char* base = (char*)ws;
+  J.counter = (int*)base;                       // [0] queue head, [1] items, [2] info (single)
+  J.order = c.d_dev ? (int*)(base + 256) : nullptr;
+  J.ws = base + p.header;
+  J.ws_stride = p.per_cta;
+  J.info = c.d_dev ? c.info_dev : (int*)(base + 8);
+  J.sN = c.d_dev ? c.s_dev : (int*)(base + 12);
+
+  cudaError_t e;
+  if (c.d_dev) {
+    e = launch_order(c.d_dev, c.batch, c.dmax, (int*)J.order, J.counter, c.info_dev, st);
+    if (e != cudaSuccess) return cuda_fail(e, "order kernel launch");
+  } else {
+    int hdr[4] = {0, 1, 0, 0};
+    e = cudaMemcpyAsync(base, hdr, sizeof hdr, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (queue reset)");
+  }
+  e = launch_persistent(c.cplx, o.precision, p.nb, J, cf, p.grid, p.smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  if (!c.d_dev && (c.info_host || c.s_host || c.n_host)) {
+    int hdr[4];
+    e = cudaMemcpyAsync(hdr, base, sizeof hdr, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status");
+    if (c.info_host) *c.info_host = hdr[2];
+    if (c.s_host) *c.s_host = hdr[3];
+    if (c.n_host) *c.n_host = hdr[3];
+  }
+  return FM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fm_opts_default(fm_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->precision = FM_FP32_IR;
+  o->form = FM_ROUNDOFF;
+  o->max_ir_iters = 2;
+  o->ir_tol = 1e-8;
+  o->anorm = 0.0;
+  o->s_fixed = -1;
+  o->nsteps = 0;
+}
+
+int fm_max_dim(void) { return 1024; }
+
+size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_opts* opts) {
+  fm_opts o = resolve_opts(opts);
+  bool cplx = job == FM_JOB_ZEXPM || job == FM_JOB_ZEXPMV;
+  int kind = JOB_EXPM;
+  long long nmax = 0;
+  switch (job) {
+    case FM_JOB_EXPM: case FM_JOB_ZEXPM: kind = JOB_EXPM; break;
+    case FM_JOB_PHI1: kind = JOB_PHI1; break;
+    case FM_JOB_EXPMV: case FM_JOB_ZEXPMV: kind = JOB_EXPMV; break;
+    case FM_JOB_PHI1MV: kind = JOB_PHI1MV; break;
+    case FM_JOB_EXPMV_ADJ: kind = JOB_ADJ; nmax = o.nsteps > 0 ? o.nsteps : 1; o.precision = FM_FP64; break;
+    default: return 0;
+  }
+  if (batch < 1 || dmax < 1 || dmax > fm_max_dim() || k < 1 || k > FM_MAX_TERMS) return 0;
+  return make_plan(kind, cplx, o.precision, batch, dmax, m, k, nmax).total;
+}
+
+fm_status fm_expm(const fm_coeffs* cs, int d, const double* A, int lda, double t, double* F,
+                  int ldf, const fm_opts* opts, void* stream, int* info_host, int* s_host) {
+  Call c = {};
+  c.kind = JOB_EXPM;
+  c.ce = cs;
+  c.batch = 1;
+  c.dmax = d;
+  c.d1 = d;
+  c.lda = lda;
+  c.ldf = ldf;
+  c.t1 = t;
+  c.A = A;
+  c.F = F;
+  c.info_host = info_host;
+  c.s_host = s_host;
+  return run(c, opts, (cudaStream_t)stream);
+}
+
+fm_status fm_zexpm(const fm_coeffs* cs, int d, const double* A, int lda, double t, double* F,
+                   int ldf, const fm_opts* opts, void* stream, int* info_host, int* s_host) {
+  Call c = {};
+  c.kind = JOB_EXPM;
+  c.cplx = true;
+  c.ce = cs;
+  c.batch = 1;
+  c.dmax = d;
+  c.d1 = d;
+  c.lda = lda;
+  c.ldf = ldf;
+  c.t1 = t;
+  c.A = A;
+  c.F = F;
+  c.info_host = info_host;
+  c.s_host = s_host;
+  return run(c, opts, (cudaStream_t)stream);
+}
+
+fm_status fm_phi1(const fm_coeffs* ce, const fm_coeffs* cphi, int d, const double* A, int lda,
+                  double t, double* Phi, int ldp, double* E, int lde, const fm_opts* opts,
+                  void* stream, int* info_host, int* s_host) {
+  Call c = {};
+  c.kind = JOB_PHI1;
+  c.ce = ce;
+  c.cp = cphi;
+  if (!cphi) return fail(FM_EINVAL, "phi_1 needs both coefficient sets");
+  c.batch = 1;
+  c.dmax = d;
+  c.d1 = d;
+  c.lda = lda;
+  c.ldf = ldp;
+  c.lde = lde;
+  c.t1 = t;
+  c.A = A;
+  c.F = Phi;
+  c.E = E;
+  c.info_host = info_host;
+  c.s_host = s_host;
+  return run(c, opts, (cudaStream_t)stream);
+}
+
+static fm_status action1(bool cplx, const fm_coeffs* cs, int d, const double* A, int lda, double t,
+                         int m, const double* V, int ldv, double* W, int ldw, const fm_opts* opts,
+                         void* stream, int* info_host, long* n_host) {
+  Call c = {};
+  c.kind = JOB_EXPMV;
+  c.cplx = cplx;
+  c.ce = cs;
+  c.batch = 1;
+  c.dmax = d;
+  c.m = m;
+  c.d1 = d;
+  c.lda = lda;
+  c.ldv = ldv;
+  c.ldw = ldw;
+  c.t1 = t;
+  c.A = A;
+  c.V = V;
+  c.W = W;
+  c.info_host = info_host;
+  c.n_host = n_host;
+  return run(c, opts, (cudaStream_t)stream);
+}
+
+fm_status fm_expmv(const fm_coeffs* cs, int d, const double* A, int lda, double t, int m,
+                   const double* V, int ldv, double* W, int ldw, const fm_opts* opts,
+                   void* stream, int* info_host, long* nsteps_host) {
+  return action1(false, cs, d, A, lda, t, m, V, ldv, W, ldw, opts, stream, info_host, nsteps_host);
+}
+
+fm_status fm_zexpmv(const fm_coeffs* cs, int d, const double* A, int lda, double t, int m,
+                    const double* V, int ldv, double* W, int ldw, const fm_opts* opts,
+                    void* stream, int* info_host, long* nsteps_host) {
+  return action1(true, cs, d, A, lda, t, m, V, ldv, W, ldw, opts, stream, info_host, nsteps_host);
+}
+
+fm_status fm_phi1mv(const fm_coeffs* ce, const fm_coeffs* cphi, int d, const double* A, int lda,
+                    double t, int m, const double* V, int ldv, double* W, int ldw,
+                    const fm_opts* opts, void* stream, int* info_host, int* s_host) {
+  if (!cphi) return fail(FM_EINVAL, "phi_1 needs both coefficient sets");
+  Call c = {};
+  c.kind = JOB_PHI1MV;
+  c.ce = ce;
+  c.cp = cphi;
+  c.batch = 1;
+  c.dmax = d;
+  c.m = m;
+  c.d1 = d;
+  c.lda = lda;
+  c.ldv = ldv;
+  c.ldw = ldw;
+  c.t1 = t;
+  c.A = A;
+  c.V = V;
+  c.W = W;
+  c.info_host = info_host;
+  c.s_host = s_host;
+  return run(c, opts, (cudaStream_t)stream);
+}
+
+static fm_status batched(int kind, bool cplx, const fm_coeffs* ce, const fm_coeffs* cp, int batch,
+                         int dmax, const int* d_dev, const int64_t* off_dev, const double* A,
+                         const double* t_dev, int m, const int64_t* voff_dev, const double* V,
+                         double* F, double* E, double* W, int* info_dev, int* s_dev,
+                         const fm_opts* opts, void* stream) {
+  if (!d_dev || !info_dev) return fail(FM_EINVAL, "batched calls need d_dev and info_dev");
+  Call c = {};
+  c.kind = kind;
+  c.cplx = cplx;
+  c.ce = ce;
+  c.cp = cp;
+  c.batch = batch;
+  c.dmax = dmax;
+  c.m = m;
+  c.d_dev = d_dev;
+  c.off = off_dev;
+  c.voff = voff_dev;
+  c.t_dev = t_dev;
+  c.A = A;
+  c.F = F;
+  c.E = E;
+  c.V = V;
+  c.W = W;
+  c.info_dev = info_dev;
+  c.s_dev = s_dev;
+  return run(c, opts, (cudaStream_t)stream);
+}
+
+fm_status fm_expm_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                          const int64_t* off_dev, const double* A, const double* t_dev,
+                          double* F, int* info_dev, int* s_dev, const fm_opts* opts,
+                          void* stream) {
+  return batched(JOB_EXPM, false, cs, nullptr, batch, dmax, d_dev, off_dev, A, t_dev, 0, nullptr,
+                 nullptr, F, nullptr, nullptr, info_dev, s_dev, opts, stream);
+}
+
+fm_status fm_zexpm_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                           const int64_t* off_dev, const double* A, const double* t_dev,
+                           double* F, int* info_dev, int* s_dev, const fm_opts* opts,
+                           void* stream) {
+  return batched(JOB_EXPM, true, cs, nullptr, batch, dmax, d_dev, off_dev, A, t_dev, 0, nullptr,
+                 nullptr, F, nullptr, nullptr, info_dev, s_dev, opts, stream);
+}
+
+fm_status fm_phi1_batched(const fm_coeffs* ce, const fm_coeffs* cphi, int batch, int dmax,
+                          const int* d_dev, const int64_t* off_dev, const double* A,
+                          const double* t_dev, double* Phi, double* E, int* info_dev,
+                          int* s_dev, const fm_opts* opts, void* stream) {
+  if (!cphi) return fail(FM_EINVAL, "phi_1 needs both coefficient sets");
+  return batched(JOB_PHI1, false, ce, cphi, batch, dmax, d_dev, off_dev, A, t_dev, 0, nullptr,
+                 nullptr, Phi, E, nullptr, info_dev, s_dev, opts, stream);
+}
+
+fm_status fm_expmv_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                           const int64_t* off_dev, const double* A, const double* t_dev, int m,
+                           const int64_t* voff_dev, const double* V, double* W, int* info_dev,
+                           int* s_dev, const fm_opts* opts, void* stream) {
+  return batched(JOB_EXPMV, false, cs, nullptr, batch, dmax, d_dev, off_dev, A, t_dev, m, voff_dev,
+                 V, nullptr, nullptr, W, info_dev, s_dev, opts, stream);
+}
+
+fm_status fm_zexpmv_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                            const int64_t* off_dev, const double* A, const double* t_dev, int m,
+                            const int64_t* voff_dev, const double* V, double* W, int* info_dev,
+                            int* s_dev, const fm_opts* opts, void* stream) {
+  return batched(JOB_EXPMV, true, cs, nullptr, batch, dmax, d_dev, off_dev, A, t_dev, m, voff_dev,
+                 V, nullptr, nullptr, W, info_dev, s_dev, opts, stream);
+}
+
+fm_status fm_phi1mv_batched(const fm_coeffs* ce, const fm_coeffs* cphi, int batch, int dmax,
+                            const int* d_dev, const int64_t* off_dev, const double* A,
+                            const double* t_dev, int m, const int64_t* voff_dev,
+                            const double* V, double* W, int* info_dev, int* s_dev,
+                            const fm_opts* opts, void* stream) {
+  if (!cphi) return fail(FM_EINVAL, "phi_1 needs both coefficient sets");
+  return batched(JOB_PHI1MV, false, ce, cphi, batch, dmax, d_dev, off_dev, A, t_dev, m, voff_dev,
+                 V, nullptr, nullptr, W, info_dev, s_dev, opts, stream);
+}
+
+fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                                   const int64_t* off_dev, const double* A, const double* t_dev,
+                                   const long* nsteps_dev, const int64_t* voff_dev,
+                                   const double* v, const double* wbar, double* W,
+                                   double* Abar, double* vbar, int* info_dev,
+                                   const fm_opts* opts, void* stream) {
+  if (!d_dev || !info_dev || !nsteps_dev || !wbar || !Abar || !vbar)
+    return fail(FM_EINVAL, "adjoint: NULL argument");
+  fm_opts o = resolve_opts(opts);
+  if (o.nsteps <= 0) return fail(FM_EINVAL, "adjoint: opts.nsteps must bound every nsteps_dev[b]");
+  Call c = {};
+  c.kind = JOB_ADJ;
+  c.ce = cs;
+  c.batch = batch;
+  c.dmax = dmax;
+  c.m = 1;
+  c.d_dev = d_dev;
+  c.off = off_dev;
+  c.voff = voff_dev;
+  c.t_dev = t_dev;
+  c.A = A;
+  c.V = v;
+  c.W = W;
+  c.wbar = wbar;
+  c.Abar = Abar;
+  c.vbar = vbar;
+  c.nsteps_dev = nsteps_dev;
+  c.nsteps_max = o.nsteps;
+  c.info_dev = info_dev;
+  fm_opts o2 = o;
+  o2.nsteps = 0;
+  o2.precision = FM_FP64;
+  return run(c, &o2, (cudaStream_t)stream);
+}
+
+const char* fm_last_error(void) { return g_err; }
+
+const char* fm_version(void) { return "fm 0.1 (sm_103a)"; }
+
+}  // extern "C"

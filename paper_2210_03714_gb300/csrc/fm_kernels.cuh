@@ -1,0 +1,578 @@
+// fm_kernels.cuh -- persistent batched kernels: one CTA owns one matrix at a
+// time and runs every step of the method on it (S. Blanes, arXiv:2210.03714):
+//
+//   a1  eta = ||tA||_1 (or anorm |t|); s = smallest with eta/2^s <= theta
+//       (N = ceil(eta/theta) for actions)                      Sec. 1, Sec. 3
+//   a2  B = tA/2^s  (B = (t/N) A for actions)                  Sec. 1
+//   a3  M_i = I - c_i B, LU with partial pivoting              Sec. 1, Sec. 2
+//   a4  Y_i = M_i^{-1} (c_i B R)  (roundoff form)              Eq. ParallRoundOff, Frac10R
+//   a5  mixed precision: factor/solve in single, then refine
+//       Y_i += M_i^{-1} (c_i B R - M_i Y_i) with the residual in double
+//   a6  F = a0 R + d1 B R + d2 B^2 R + sum_i b_i Y_i          Eq. ParallRoundOff, Frac10
+//   a7  s squarings F <- F F; phi_1 doubling (Phi, E) <- ((E+I)Phi/2, E^2);
+//       or N steps of the action with the factorizations reused   Sec. 1
+//
+// The element-wise steps are written in the same order as the textbook
+// definition (C = c_i B rounded once, M = I - C, F = F + b_i Y) so that the
+// only rounding differences against a plain double-precision evaluation come
+// from the factorizations and the products.
+#pragma once
+#include "cta_la.cuh"
+#include "fm_job.h"
+
+namespace fmk {
+
+template <class T>
+__device__ __forceinline__ T tdiag(int r, int c) {
+  return r == c ? Tr<T>::one() : Tr<T>::zero();
+}
+
+// b * y for a real-or-complex weight stored as (re, im)
+template <class T> __device__ __forceinline__ T wmul(double br, double bi, T y);
+template <> __device__ __forceinline__ double wmul<double>(double br, double, double y) {
+  return __dmul_rn(br, y);
+}
+template <> __device__ __forceinline__ zd wmul<zd>(double br, double bi, zd y) {
+  return Tr<zd>::mul(zd{br, bi}, y);
+}
+
+__device__ __forceinline__ int select_s(double eta, double theta) {
+  int s = 0;
+  while (eta > ldexp(theta, s) && s < 1023) ++s;
+  return s;
+}
+
+__device__ __forceinline__ double tscale(double a, int s) { return ldexp(a, -s); }
+__device__ __forceinline__ zd tscale(zd a, int s) { return {ldexp(a.x, -s), ldexp(a.y, -s)}; }
+
+// exact rounding error of fl(1 - c): returns fl(1 - c) - (1 - c)  (TwoSum)
+__device__ __forceinline__ double diag_err(double c) {
+  double a = 1.0, b = -c;
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double err = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return -err;
+}
+__device__ __forceinline__ double diag_err(zd c) { return diag_err(c.x); }
+
+template <class T> __device__ __forceinline__ T dscale(double dr, T y);
+template <> __device__ __forceinline__ double dscale<double>(double dr, double y) { return __dmul_rn(dr, y); }
+template <> __device__ __forceinline__ zd dscale<zd>(double dr, zd y) { return {__dmul_rn(dr, y.x), __dmul_rn(dr, y.y)}; }
+
+template <class T> __device__ __forceinline__ typename Tr<T>::R tmag(T a) { return Tr<T>::mag(a); }
+
+// ---------------------------------------------------------------------------
+// One shifted solve: Y = M^{-1} RHS with M = I - C (+ exact diagonal rounding
+// D), factors LU (type TL) already computed.  Double precision: one solve in
+// T.  Mixed: solve in TL, then max_ir refinement steps with the residual
+// RHS - M Y = ((RHS - Y) + C Y) - D Y evaluated in T.  Returns the last
+// relative correction (or -1 when none was made).
+// ---------------------------------------------------------------------------
+template <class T, class TL, int NB>
+__device__ __noinline__ double shifted_solve(const FmJob& J, int n, int m, const T* C, const double* D,
+                                const TL* LU, const int* piv, const T* RHS, T* Y, T* P, TL* RL,
+                                char* smem) {
+  using TT = Tr<T>;
+  using R = typename TT::R;
+  const int tid = threadIdx.x;
+  const size_t nm = (size_t)n * m;
+  if (sizeof(TL) == sizeof(T) && J.precision == 0) {
+    for (size_t e = tid; e < nm; e += NT) Y[e] = RHS[e];
+    __syncthreads();
+    cta_getrs<T, NB>(n, (const T*)LU, n, piv, m, Y, m, (T*)smem);
+    return -1.0;
+  }
+  for (size_t e = tid; e < nm; e += NT) RL[e] = cvt<TL, T>(RHS[e]);
+  __syncthreads();
+  cta_getrs<TL, NB>(n, LU, n, piv, m, RL, m, (TL*)smem);
+  for (size_t e = tid; e < nm; e += NT) Y[e] = cvt<T, TL>(RL[e]);
+  __syncthreads();
+  double q = -1.0;
+  R* red = (R*)(smem + 64);
+  for (int it = 0; it < J.max_ir; ++it) {
+    // P = C Y  (double-accurate product)
+    cta_gemm<T>(n, m, n, (R)1, C, n, Y, m, (R)0, P, m, (T*)(smem + 256));
+    for (size_t e = tid; e < nm; e += NT) {
+      int r = (int)(e / m);
+      T v = TT::add(TT::sub(RHS[e], Y[e]), P[e]);
+      v = TT::sub(v, dscale<T>(D[r], Y[e]));
+      RL[e] = cvt<TL, T>(v);
+    }
+    __syncthreads();
+    cta_getrs<TL, NB>(n, LU, n, piv, m, RL, m, (TL*)smem);
+    R dmax = 0, ymax = 0;
+    for (size_t e = tid; e < nm; e += NT) {
+      T dl = cvt<T, TL>(RL[e]);
+      T y = TT::add(Y[e], dl);
+      Y[e] = y;
+      dmax = fmax(dmax, tmag(dl));
+      ymax = fmax(ymax, tmag(y));
+    }
+    __syncthreads();
+    dmax = cta_max<R>(dmax, red);
+    ymax = cta_max<R>(ymax, red);
+    q = ymax > 0 ? (double)(dmax / ymax) : (double)dmax;
+  }
+  return q;
+}
+
+template <class T, class TL>
+__device__ __forceinline__ void build_shift(int n, double cre, double cim, const T* B, T* C, TL* LU,
+                                            double* D, bool mixed) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e / n, c = e % n;
+    T cv = wmul<T>(cre, cim, B[e]);  // C = c_i B, one rounding
+    C[e] = cv;
+    T mv = Tr<T>::sub(tdiag<T>(r, c), cv);  // M = I - C
+    LU[e] = cvt<TL, T>(mv);
+    if (r == c) D[r] = mixed ? diag_err(cv) : 0.0;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// matrix functions: exp (JOB_EXPM), phi_1 with exp (JOB_PHI1, JOB_PHI1MV)
+// ---------------------------------------------------------------------------
+template <class T, class TL, int NB>
+__device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem) {
+  using TT = Tr<T>;
+  using R = typename TT::R;
+  const int tid = threadIdx.x;
+  const bool batched = J.d != nullptr;
+  const int n = batched ? J.d[b] : J.d1;
+  const int64_t off = batched ? J.off[b] : 0;
+  const int lda = batched ? n : J.lda, ldf = batched ? n : J.ldf, lde = batched ? n : J.lde;
+  const double t = J.t ? J.t[b] : J.t1;
+  const bool mixed = J.precision != 0;
+  const bool two = (J.kind != JOB_EXPM);
+  const WsLayout L = ws_layout(J.kind == JOB_PHI1MV ? JOB_PHI1 : J.kind, n, J.m, cf.k, sizeof(T),
+                               sizeof(TL), 0);
+  T* B = (T*)(ws + L.B);
+  T* C = (T*)(ws + L.C);
+  T* Y = (T*)(ws + L.Y);
+  T* T1 = (T*)(ws + L.T1);
+  T* F = (T*)(ws + L.F);
+  T* Ph = (T*)(ws + L.Phi);
+  TL* LU = (TL*)(ws + L.LU);
+  TL* RL = (TL*)(ws + L.RL);
+  int* piv = (int*)(ws + L.piv);
+  double* D = (double*)(ws + L.D);
+  R* red = (R*)smem;
+  int* redi = (int*)(smem + 128);
+  const T* A = (const T*)J.A + off;
+
+  // a1/a2: B = tA, finiteness, eta = ||tA||_1, s, B = tA/2^s
+  int bad = !isfinite(t);
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e / n, c = e % n;
+    T a = A[(size_t)r * lda + c];
+    bad |= !TT::finite(a);
+    B[e] = TT::rscale(a, t);
+  }
+  __syncthreads();
+  bad = cta_or(bad, redi);
+  R cmax = 0;
+  for (int c = tid; c < n; c += NT) {
+    R s = 0;
+    for (int r = 0; r < n; ++r) s += tmag(B[r * n + c]);
+    cmax = (s > cmax || isnan(s)) ? s : cmax;
+  }
+  cmax = cta_max<R>(cmax, red);
+  int info = 0;
+  if (bad) info = -2;
+  const double eta = J.anorm > 0 ? J.anorm * fabs(t) : (double)cmax;
+  const int s = J.s_fixed >= 0 ? J.s_fixed : select_s(eta, cf.theta);
+  for (int e = tid; e < n * n; e += NT) B[e] = tscale(B[e], s);
+  // a6 (first part): F = base I (+ d1 B + d2 B^2) for each function
+  double base[2];
+  for (int f = 0; f < 2; ++f) {
+    base[f] = cf.a0[f];
+    if (J.form == 1)
+      for (int i = 0; i < cf.k; ++i) base[f] -= cf.b_re[f][i];
+  }
+  __syncthreads();
+  const bool hyb = cf.d1[0] != 0 || cf.d2[0] != 0 || (two && (cf.d1[1] != 0 || cf.d2[1] != 0));
+  bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0);
+  if (need_b2) cta_gemm<T>(n, n, n, (R)1, B, n, B, n, (R)0, T1, n, (T*)(smem + 256));
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e / n, c = e % n;
+    for (int f = 0; f < (two ? 2 : 1); ++f) {
+      T v = TT::rscale(tdiag<T>(r, c), base[f]);
+      if (hyb) {
+        if (cf.d1[f] != 0) v = TT::add(v, TT::rscale(B[e], cf.d1[f]));
+        if (cf.d2[f] != 0) v = TT::add(v, TT::rscale(T1[e], cf.d2[f]));
+      }
+      (f == 0 ? F : Ph)[e] = v;
+    }
+  }
+  __syncthreads();
+  double qmax = -1.0;
+  bool any_shift = false;
+  // a3-a6: the shifted solves, ascending i
+  for (int i = 0; i < cf.k && info == 0; ++i) {
+    const double cre = cf.c_re[i], cim = cf.c_im[i];
+    if (cre == 0.0 && cim == 0.0) {
+      if (J.form == 1) {  // plain form: b_i I
+        for (int e = tid; e < n * n; e += NT) {
+          int r = e / n, c = e % n;
+          for (int f = 0; f < (two ? 2 : 1); ++f) {
+            T* Fx = f == 0 ? F : Ph;
+            Fx[e] = TT::add(Fx[e], wmul<T>(cf.b_re[f][i], cf.b_im[f][i], tdiag<T>(r, c)));
+          }
+        }
+        __syncthreads();
+      }
+      continue;
+    }
+    any_shift = true;
+    build_shift<T, TL>(n, cre, cim, B, C, LU, D, mixed);
+    int fi = cta_getrf<TL, NB>(n, LU, n, piv, (TL*)smem);
+    if (fi) { info = i * n + fi; break; }
+    // right-hand side: C (roundoff form) or I (plain form), kept in T1
+    for (int e = tid; e < n * n; e += NT) {
+      int r = e / n, c = e % n;
+      T1[e] = J.form == 1 ? tdiag<T>(r, c) : C[e];
+    }
+    __syncthreads();
+    double q = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL, smem);
+    qmax = fmax(qmax, q);
+    for (int e = tid; e < n * n; e += NT)
+      for (int f = 0; f < (two ? 2 : 1); ++f) {
+        T* Fx = f == 0 ? F : Ph;
+        Fx[e] = TT::add(Fx[e], wmul<T>(cf.b_re[f][i], cf.b_im[f][i], Y[e]));
+      }
+    __syncthreads();
+  }
+  if (info == 0 && mixed && J.ir_tol > 0 && any_shift && (J.max_ir == 0 || qmax > J.ir_tol)) info = -1;
+  // a7: squarings / doublings
+  T* T2 = (T*)(ws + L.T2);
+  if (info == 0 || info == -1) {
+    for (int q = 0; q < s; ++q) {
+      if (!two) {
+        cta_gemm<T>(n, n, n, (R)1, F, n, F, n, (R)0, T1, n, (T*)(smem + 256));
+        T* tmp = F; F = T1; T1 = tmp;
+      } else {
+        // Phi <- (E + I) Phi / 2, then E <- E E
+        for (int r = tid; r < n; r += NT) F[r * n + r] = TT::add(F[r * n + r], TT::one());
+        __syncthreads();
+        cta_gemm<T>(n, n, n, (R)1, F, n, Ph, n, (R)0, T1, n, (T*)(smem + 256));
+        for (int e = tid; e < n * n; e += NT) Ph[e] = TT::rscale(T1[e], 0.5);
+        for (int r = tid; r < n; r += NT) F[r * n + r] = TT::sub(F[r * n + r], TT::one());
+        __syncthreads();
+        cta_gemm<T>(n, n, n, (R)1, F, n, F, n, (R)0, T2, n, (T*)(smem + 256));
+        T* tmp = F; F = T2; T2 = tmp;
+      }
+    }
+  }
+  __syncthreads();
+  // outputs
+  if (J.kind == JOB_EXPM) {
+    T* Fo = (T*)J.F + off;
+    for (int e = tid; e < n * n; e += NT) Fo[(size_t)(e / n) * ldf + e % n] = F[e];
+  } else if (J.kind == JOB_PHI1) {
+    T* Po = (T*)J.F + off;
+    for (int e = tid; e < n * n; e += NT) Po[(size_t)(e / n) * ldf + e % n] = Ph[e];
+    if (J.E) {
+      T* Eo = (T*)J.E + off;
+      for (int e = tid; e < n * n; e += NT) Eo[(size_t)(e / n) * lde + e % n] = F[e];
+    }
+  } else {  // PHI1MV: W = Phi V
+    const int m = J.m;
+    const int64_t vo = batched ? J.voff[b] : 0;
+    const int ldv = batched ? m : J.ldv, ldw = batched ? m : J.ldw;
+    cta_gemm<T>(n, m, n, (R)1, Ph, n, (const T*)J.V + vo, ldv, (R)0, (T*)J.W + vo, ldw,
+                (T*)(smem + 256));
+  }
+  if (tid == 0) {
+    if (J.info) J.info[b] = info;
+    if (J.sN) J.sN[b] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// action: W = exp(tA) V (JOB_EXPMV)
+// ---------------------------------------------------------------------------
+template <class T, class TL, int NB>
+__device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem) {
+  using TT = Tr<T>;
+  using R = typename TT::R;
+  const int tid = threadIdx.x;
+  const bool batched = J.d != nullptr;
+  const int n = batched ? J.d[b] : J.d1;
+  const int m = J.m;
+  const int64_t off = batched ? J.off[b] : 0;
+  const int64_t vo = batched ? J.voff[b] : 0;
+  const int lda = batched ? n : J.lda;
+  const int ldv = batched ? m : J.ldv, ldw = batched ? m : J.ldw;
+  const double t = J.t ? J.t[b] : J.t1;
+  const bool mixed = J.precision != 0;
+  const int k = cf.k;
+  const WsLayout L = ws_layout(JOB_EXPMV, n, m, k, sizeof(T), sizeof(TL), 0);
+  T* B = (T*)(ws + L.B);
+  T* Y = (T*)(ws + L.Y);
+  T* P = (T*)(ws + L.T1);
+  TL* RL = (TL*)(ws + L.RL);
+  T* Wc = (T*)(ws + L.Wc);
+  T* Wn = (T*)(ws + L.Wn);
+  T* U = (T*)(ws + L.U);
+  T* U2 = (T*)(ws + L.U2);
+  T* RHS = (T*)(ws + L.RHS);
+  R* red = (R*)smem;
+  int* redi = (int*)(smem + 128);
+  const T* A = (const T*)J.A + off;
+  const T* V = (const T*)J.V + vo;
+  const size_t nm = (size_t)n * m;
+
+  int bad = !isfinite(t);
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e / n, c = e % n;
+    T a = A[(size_t)r * lda + c];
+    bad |= !TT::finite(a);
+    B[e] = TT::rscale(a, t);
+  }
+  for (size_t e = tid; e < nm; e += NT) {
+    T v = V[(e / m) * ldv + e % m];
+    bad |= !TT::finite(v);
+    Wc[e] = v;
+  }
+  __syncthreads();
+  bad = cta_or(bad, redi);
+  R cmax = 0;
+  for (int c = tid; c < n; c += NT) {
+    R s = 0;
+    for (int r = 0; r < n; ++r) s += tmag(B[r * n + c]);
+    cmax = (s > cmax || isnan(s)) ? s : cmax;
+  }
+  cmax = cta_max<R>(cmax, red);
+  int info = bad ? -2 : 0;
+  const double eta = J.anorm > 0 ? J.anorm * fabs(t) : (double)cmax;
+  long long N = J.nsteps;
+  if (N <= 0) {
+    double qn = ceil(eta / cf.theta);
+    N = qn < 1.0 ? 1 : (long long)qn;
+  }
+  const double h = t / (double)N;
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e / n, c = e % n;
+    B[e] = TT::rscale(A[(size_t)r * lda + c], h);
+  }
+  __syncthreads();
+  double base = cf.a0[0];
+  if (J.form == 1)
+    for (int i = 0; i < k; ++i) base -= cf.b_re[0][i];
+  // a3: factor every shifted matrix once
+  for (int i = 0; i < k && info == 0; ++i) {
+    const double cre = cf.c_re[i], cim = cf.c_im[i];
+    if (cre == 0.0 && cim == 0.0) continue;
+    T* Ci = (T*)(ws + L.Cs) + (size_t)i * n * n;
+    TL* LUi = (TL*)(ws + L.LUs) + (size_t)i * n * n;
+    int* pivi = (int*)(ws + L.pivs) + (size_t)i * n;
+    double* Di = (double*)(ws + L.Ds) + (size_t)i * n;
+    build_shift<T, TL>(n, cre, cim, B, Ci, LUi, Di, mixed);
+    int fi = cta_getrf<TL, NB>(n, LUi, n, pivi, (TL*)smem);
+    if (fi) info = i * n + fi;
+  }
+  double qmax = -1.0;
+  bool any_shift = false;
+  // a4-a7: N steps W <- r(B) W
+  for (long long q = 0; q < N && info == 0; ++q) {
+    cta_gemm<T>(n, m, n, (R)1, B, n, Wc, m, (R)0, U, m, (T*)(smem + 256));
+    if (cf.d2[0] != 0) cta_gemm<T>(n, m, n, (R)1, B, n, U, m, (R)0, U2, m, (T*)(smem + 256));
+    for (size_t e = tid; e < nm; e += NT) {
+      T v = TT::rscale(Wc[e], base);
+      if (cf.d1[0] != 0) v = TT::add(v, TT::rscale(U[e], cf.d1[0]));
+      if (cf.d2[0] != 0) v = TT::add(v, TT::rscale(U2[e], cf.d2[0]));
+      Wn[e] = v;
+    }
+    __syncthreads();
+    for (int i = 0; i < k; ++i) {
+      const double cre = cf.c_re[i], cim = cf.c_im[i];
+      const double br = cf.b_re[0][i], bi = cf.b_im[0][i];
+      if (cre == 0.0 && cim == 0.0) {
+        if (J.form == 1) {
+          for (size_t e = tid; e < nm; e += NT) Wn[e] = TT::add(Wn[e], wmul<T>(br, bi, Wc[e]));
+          __syncthreads();
+        }
+        continue;
+      }
+      any_shift = true;
+      const T* Ci = (const T*)(ws + L.Cs) + (size_t)i * n * n;
+      const TL* LUi = (const TL*)(ws + L.LUs) + (size_t)i * n * n;
+      const int* pivi = (const int*)(ws + L.pivs) + (size_t)i * n;
+      const double* Di = (const double*)(ws + L.Ds) + (size_t)i * n;
+      for (size_t e = tid; e < nm; e += NT) RHS[e] = J.form == 1 ? Wc[e] : wmul<T>(cre, cim, U[e]);
+      __syncthreads();
+      double qq = shifted_solve<T, TL, NB>(J, n, m, Ci, Di, LUi, pivi, RHS, Y, P, RL, smem);
+      qmax = fmax(qmax, qq);
+      for (size_t e = tid; e < nm; e += NT) Wn[e] = TT::add(Wn[e], wmul<T>(br, bi, Y[e]));
+      __syncthreads();
+    }
+    T* tmp = Wc; Wc = Wn; Wn = tmp;
+  }
+  if (info == 0 && mixed && J.ir_tol > 0 && any_shift && (J.max_ir == 0 || qmax > J.ir_tol)) info = -1;
+  T* Wo = (T*)J.W + vo;
+  for (size_t e = tid; e < nm; e += NT) Wo[(e / m) * ldw + e % m] = Wc[e];
+  if (tid == 0) {
+    if (J.info) J.info[b] = info;
+    if (J.sN) J.sN[b] = (int)(N > 0x7fffffff ? 0x7fffffff : N);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the action (real, double, one vector): JOB_ADJ
+// ---------------------------------------------------------------------------
+template <int NB>
+__device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem) {
+  using T = double;
+  using TT = Tr<T>;
+  const int tid = threadIdx.x;
+  const int n = J.d[b];
+  const int64_t off = J.off[b], vo = J.voff[b];
+  const double t = J.t[b];
+  const long long N = J.nsteps_dev[b];
+  const int k = cf.k;
+  const WsLayout L = ws_layout(JOB_ADJ, n, 1, k, 8, 8, J.nsteps_max);
+  T* B = (T*)(ws + L.B);
+  T* Cb = (T*)(ws + L.C);   // Bbar accumulator (n x n)
+  T* u = (T*)(ws + L.U);
+  T* ub = (T*)(ws + L.U2);
+  T* wb = (T*)(ws + L.Wc);
+  T* wbp = (T*)(ws + L.Wn);
+  T* y = (T*)(ws + L.RHS);
+  T* Wst = (T*)(ws + L.Wst);
+  T* Yst = (T*)(ws + L.Yst);
+  T* Lam = (T*)(ws + L.Lam);  // n x (k+1): columns c_i lambda_i, then ubar
+  T* Yt = (T*)(ws + L.Yt);    // (k+1) x n: rows Y_i^T, then w^T
+  const T* A = (const T*)J.A + off;
+  int info = 0;
+  if (N <= 0 || N > J.nsteps_max) info = -3;
+  const double h = t / (double)(N > 0 ? N : 1);
+  for (int e = tid; e < n * n; e += NT) {
+    B[e] = TT::rscale(A[e], h);
+    Cb[e] = 0.0;
+  }
+  __syncthreads();
+  for (int i = 0; i < k && info == 0; ++i) {
+    if (cf.c_re[i] == 0.0) continue;
+    T* Ci = (T*)(ws + L.Cs) + (size_t)i * n * n;
+    T* LUi = (T*)(ws + L.LUs) + (size_t)i * n * n;
+    int* pivi = (int*)(ws + L.pivs) + (size_t)i * n;
+    double* Di = (double*)(ws + L.Ds) + (size_t)i * n;
+    build_shift<T, T>(n, cf.c_re[i], 0.0, B, Ci, LUi, Di, false);
+    int fi = cta_getrf<T, NB>(n, LUi, n, pivi, (T*)smem);
+    if (fi) info = i * n + fi;
+  }
+  if (info == 0) {
+    // forward sweep, storing w_q and Y_iq
+    for (int r = tid; r < n; r += NT) Wst[r] = ((const T*)J.V)[vo + r];
+    __syncthreads();
+    for (long long q = 1; q <= N; ++q) {
+      const T* wp = Wst + (size_t)(q - 1) * n;
+      T* wq = Wst + (size_t)q * n;
+      cta_gemm<T>(n, 1, n, 1.0, B, n, wp, 1, 0.0, u, 1, (T*)(smem + 256));
+      for (int r = tid; r < n; r += NT) wq[r] = TT::rscale(wp[r], cf.a0[0]);
+      __syncthreads();
+      for (int i = 0; i < k; ++i) {
+        T* yi = Yst + ((size_t)(q - 1) * k + i) * n;
+        if (cf.c_re[i] == 0.0) {
+          for (int r = tid; r < n; r += NT) yi[r] = 0.0;
+          __syncthreads();
+          continue;
+        }
+        for (int r = tid; r < n; r += NT) yi[r] = TT::rscale(u[r], cf.c_re[i]);
+        __syncthreads();
+        cta_getrs<T, NB>(n, (T*)(ws + L.LUs) + (size_t)i * n * n, n,
+                         (int*)(ws + L.pivs) + (size_t)i * n, 1, yi, 1, (T*)smem);
+        for (int r = tid; r < n; r += NT) wq[r] = TT::add(wq[r], TT::rscale(yi[r], cf.b_re[0][i]));
+        __syncthreads();
+      }
+    }
+    for (int r = tid; r < n; r += NT) {
+      ((T*)J.W)[vo + r] = Wst[(size_t)N * n + r];
+      wb[r] = J.wbar[vo + r];
+    }
+    __syncthreads();
+    // reverse sweep
+    for (long long q = N; q >= 1; --q) {
+      const T* wp = Wst + (size_t)(q - 1) * n;
+      for (int r = tid; r < n; r += NT) {
+        wbp[r] = TT::rscale(wb[r], cf.a0[0]);
+        ub[r] = 0.0;
+      }
+      __syncthreads();
+      int kk = 0;
+      for (int i = 0; i < k; ++i) {
+        const double c = cf.c_re[i];
+        if (c == 0.0) continue;
+        const T* yi = Yst + ((size_t)(q - 1) * k + i) * n;
+        for (int r = tid; r < n; r += NT) y[r] = TT::rscale(wb[r], cf.b_re[0][i]);
+        __syncthreads();
+        cta_getrs_t<T>(n, (T*)(ws + L.LUs) + (size_t)i * n * n, n,
+                       (int*)(ws + L.pivs) + (size_t)i * n, y);
+        for (int r = tid; r < n; r += NT) {
+          ub[r] = TT::add(ub[r], TT::rscale(y[r], c));
+          Lam[(size_t)r * (k + 1) + kk] = TT::rscale(y[r], c);
+          Yt[(size_t)kk * n + r] = yi[r];
+        }
+        __syncthreads();
+        ++kk;
+      }
+      for (int r = tid; r < n; r += NT) {
+        Lam[(size_t)r * (k + 1) + kk] = ub[r];
+        Yt[(size_t)kk * n + r] = wp[r];
+      }
+      __syncthreads();
+      // Bbar += [c_i lambda_i, ubar] [Y_i^T; w^T]
+      cta_gemm<T>(n, n, kk + 1, 1.0, Lam, k + 1, Yt, n, 1.0, Cb, n, (T*)(smem + 256));
+      // wbar_{q-1} += B^T ubar  (as the row vector ubar^T B)
+      cta_gemm<T>(1, n, n, 1.0, ub, n, B, n, 1.0, wbp, n, (T*)(smem + 256));
+      for (int r = tid; r < n; r += NT) wb[r] = wbp[r];
+      __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += NT) J.Abar[off + e] = TT::rscale(Cb[e], h);
+    for (int r = tid; r < n; r += NT) J.vbar[vo + r] = wb[r];
+  }
+  if (tid == 0 && J.info) J.info[b] = info;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel: a work queue over matrices, largest first
+// ---------------------------------------------------------------------------
+template <class T, class TL, int NB>
+__global__ void __launch_bounds__(NT) fm_persistent(FmJob J, FmCoef cf) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int s_item;
+  char* ws = J.ws + (size_t)blockIdx.x * J.ws_stride;
+  const int limit = J.order ? *(volatile int*)(J.counter + 1) : J.batch;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(J.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= limit) break;
+    const int b = J.order ? J.order[item] : item;
+    if (J.kind == JOB_EXPM || J.kind == JOB_PHI1 || J.kind == JOB_PHI1MV)
+      run_matfun<T, TL, NB>(J, cf, b, ws, smem + 1024);
+    else if (J.kind == JOB_EXPMV)
+      run_action<T, TL, NB>(J, cf, b, ws, smem + 1024);
+    else if constexpr (sizeof(T) == 8 && sizeof(TL) == 8)
+      run_adjoint<NB>(J, cf, b, ws, smem + 1024);
+  }
+}
+
+// dynamic shared memory the kernel needs for matrices up to n
+template <class T, int NB>
+inline size_t fm_smem_bytes(int n) {
+  size_t getrf = ((size_t)n * NB + 2 * GK * GLD) * sizeof(T) + 256;
+  size_t getrs = ((size_t)NB * NB + 2 * GK * GLD) * sizeof(T);
+  size_t gemm = 256 + 2 * GK * GLD * sizeof(T);
+  size_t m = getrf > getrs ? getrf : getrs;
+  m = m > gemm ? m : gemm;
+  return 1024 + m + 512;
+}
+
+}  // namespace fmk

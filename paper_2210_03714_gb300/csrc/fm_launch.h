@@ -1,0 +1,28 @@
+// fm_launch.h -- host-side entry points of the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "fm_job.h"
+
+namespace fmk {
+
+// dynamic shared memory of the persistent kernel for matrices up to dmax
+size_t launch_smem(bool cplx, int nb, int dmax);
+// resident CTAs per SM of the persistent kernel at that shared memory size
+int launch_occupancy(bool cplx, int precision, int nb, size_t smem);
+// the persistent kernel: grid CTAs, each pulling matrices from the queue
+cudaError_t launch_persistent(bool cplx, int precision, int nb, const FmJob& J, const FmCoef& cf,
+                              int grid, size_t smem, cudaStream_t st);
+// order the batch by d (largest first), reset the queue, flag bad d in info
+cudaError_t launch_order(const int* d, int batch, int dmax, int* order, int* counter, int* info,
+                         cudaStream_t st);
+// per-type launchers (fm_inst_*.cu)
+cudaError_t launch_real(int precision, int nb, const FmJob& J, const FmCoef& cf, int grid,
+                        size_t smem, cudaStream_t st);
+cudaError_t launch_cplx(int precision, int nb, const FmJob& J, const FmCoef& cf, int grid,
+                        size_t smem, cudaStream_t st);
+int occ_real(int precision, int nb, size_t smem);
+int occ_cplx(int precision, int nb, size_t smem);
+
+}  // namespace fmk

@@ -1,0 +1,99 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random numbers and scales them; it contains none of
+the method's arithmetic, so the tests may feed the same inputs to the CUDA
+library and to the CPU oracle.  Each generator documents its recipe.
+
+The paper uses randn matrices (Sec. 5: A = randn(100)), a Toeplitz matrix
+A_ij = 1/(1+(i-j)^2) (Eq. Ex2b) and trid{-1,2,-1} (Sec. 5); the batched and
+large shapes below stand in for those experiments at production sizes.
+"""
+import numpy as np
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def dense_scaled(d, norm1, seed, scale_sqrt=False):
+    """N(0,1) entries (divided by sqrt(d) if scale_sqrt), then scaled so that
+    ||A||_1 = norm1 exactly up to rounding."""
+    g = _rng(seed)
+    A = g.standard_normal((d, d))
+    if scale_sqrt:
+        A /= np.sqrt(d)
+    return A * (norm1 / np.abs(A).sum(axis=0).max())
+
+
+def single_d64(seed=0):
+    """One real d = 64 matrix, N(0,1) scaled to ||A||_1 = 2, and v ~ N(0,1)."""
+    A = dense_scaled(64, 2.0, seed)
+    v = _rng(seed + 1).standard_normal(64)
+    return A, v
+
+
+def batch_dims(batch, seed, choices=tuple(range(16, 257, 16))):
+    """d_b drawn uniformly from choices (default {16, 32, ..., 256})."""
+    return _rng(seed).choice(np.array(choices), size=batch)
+
+
+def batch_mixed_d(batch=4096, seed=1000, choices=tuple(range(16, 257, 16)), lo=0.5, hi=8.0):
+    """Batch of real dense matrices: d uniform over choices; entries
+    N(0,1)/sqrt(d); each scaled to ||A||_1 ~ U[lo, hi].  Returns (dims, list of
+    matrices, norms).  Matrix b uses seed + 1 + b."""
+    dims = batch_dims(batch, seed, choices)
+    norms = _rng(seed + 7919).uniform(lo, hi, size=batch)
+    mats = [dense_scaled(int(d), float(n), seed + 1 + b, scale_sqrt=True)
+            for b, (d, n) in enumerate(zip(dims, norms))]
+    return dims, mats, norms
+
+
+def batch_flat(dims, norms, seed=1000):
+    """The same batch as batch_mixed_d, packed back to back (float64)."""
+    out = np.empty(int(np.sum(np.asarray(dims, dtype=np.int64) ** 2)))
+    o = 0
+    for b, (d, n) in enumerate(zip(dims, norms)):
+        d = int(d)
+        out[o:o + d * d] = dense_scaled(d, float(n), seed + 1 + b, scale_sqrt=True).ravel()
+        o += d * d
+    return out
+
+
+def hermitian_action(d=4096, m=256, rho=20.0, seed=2000):
+    """A = -iH, H = (G + G^H)/2 with G complex N(0,1)/sqrt(d), scaled so that its
+    spectral radius is rho; V complex N(0,1), d x m.  Returns (A, V, rho)."""
+    g = _rng(seed)
+    G = (g.standard_normal((d, d)) + 1j * g.standard_normal((d, d))) / np.sqrt(d)
+    H = (G + G.conj().T) / 2
+    lam = np.linalg.eigvalsh(H)
+    H *= rho / np.abs(lam).max()
+    V = g.standard_normal((d, m)) + 1j * g.standard_normal((d, m))
+    return -1j * H, V, rho
+
+
+def diffusion_batch(batch=512, d=512, seed=3000, tmin=1e-4, tmax=1e-2):
+    """A_b = -L + 0.1 N_b, L = trid{-1, 2, -1} / h^2 with h = 1/(d+1), N_b with
+    N(0,1)/sqrt(d) entries; t_b log-uniform in [tmin, tmax]; u0_b, b_b ~ N(0,1)."""
+    h = 1.0 / (d + 1)
+    L = (np.diag(np.full(d, 2.0)) - np.diag(np.ones(d - 1), 1) - np.diag(np.ones(d - 1), -1)) / h ** 2
+    g = _rng(seed)
+    mats = [-L + 0.1 * g.standard_normal((d, d)) / np.sqrt(d) for _ in range(batch)]
+    ts = np.exp(g.uniform(np.log(tmin), np.log(tmax), size=batch))
+    u0 = g.standard_normal((batch, d))
+    bb = g.standard_normal((batch, d))
+    return mats, ts, u0, bb
+
+
+def grad_batch(batch=256, d=128, seed=4000):
+    """A_b with N(0,1)/sqrt(d) entries; v_b, y_b ~ N(0,1)."""
+    g = _rng(seed)
+    A = g.standard_normal((batch, d, d)) / np.sqrt(d)
+    v = g.standard_normal((batch, d))
+    y = g.standard_normal((batch, d))
+    return A, v, y
+
+
+def toeplitz_paper(d=100):
+    """Eq. (Ex2b): A_ij = 1/(1 + (i - j)^2)."""
+    i = np.arange(d)
+    return 1.0 / (1.0 + (i[:, None] - i[None, :]) ** 2)

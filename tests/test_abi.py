@@ -1,0 +1,84 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every
+entry point that include/fm.h declares; no compute call is made."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "fm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fm_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_parses():
+    names = header_functions()
+    assert "fm_expm" in names and "fm_expm_batched" in names and len(names) >= 20
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2210_03714_gb300 as fm
+    L = fm.lib()
+    missing = [n for n in header_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    # the Python binding covers the same names
+    assert set(header_functions()) <= set(fm.exported_symbols())
+
+
+def test_host_only_calls():
+    """Calls that need no GPU: builtins, theta, defaults, argument errors."""
+    import ctypes as C
+    import paper_2210_03714_gb300 as fm
+    from paper_2210_03714_gb300 import _ffi
+    L = fm.lib()
+    assert L.fm_version().startswith(b"fm")
+    assert L.fm_max_dim() >= 512
+    cs = _ffi.fm_coeffs()
+    assert L.fm_coeffs_builtin(3, C.byref(cs)) == 0 and cs.k == 9
+    assert L.fm_coeffs_builtin(99, C.byref(cs)) == _ffi.FM_EINVAL
+    o = _ffi.fm_opts()
+    L.fm_opts_default(C.byref(o))
+    assert o.precision == _ffi.FM_FP32_IR and o.max_ir_iters == 2 and o.s_fixed == -1
+    # argument validation happens before any device work
+    st = L.fm_expm(C.byref(cs), 0, None, 0, 1.0, None, 0, None, None, None, None)
+    assert st == _ffi.FM_ESHAPE
+    st = L.fm_expm(C.byref(cs), 4, None, 4, 1.0, None, 4, None, None, None, None)
+    assert st == _ffi.FM_EINVAL
+    assert b"NULL" in L.fm_last_error()
+
+
+def test_builtin_sets_match_oracle_exact_values():
+    """The library's own coefficient tables (printed rationals, and the phi_1
+    sets it derives by exact Lagrange interpolation) equal the oracle's exact
+    rationals to the last bit, and its theta agrees with the oracle's."""
+    import paper_2210_03714_gb300 as fm
+    from oracle import coeffs as oc
+    for name in ["R4", "R4_phi1", "R4_phi1_a5", "R8", "R8_phi1", "R5", "R10", "R10star"]:
+        lib = fm.Coeffs(name).as_dict()
+        ex = oc.SETS[name]
+        assert lib["c_re"] == [float(c) for c in ex.c], name
+        assert lib["b_re"] == [float(b) for b in ex.b], name
+        assert lib["a0"] == 1.0
+        if name.startswith("R10"):
+            assert lib["d1"] == float(ex.d[1]) and lib["d2"] == float(ex.d[2])
+        th = oc.theta(ex, oc.U_FP64)
+        assert abs(lib["theta"] / th - 1) < 1e-10, name
+    for name in ["pade22", "pade22_phi1"]:
+        lib = fm.Coeffs(name).as_dict()
+        ref = oc.oracle_coeffs(name)
+        assert abs(lib["c_re"][0] - ref["c_re"][0]) < 1e-16
+        assert abs(lib["c_im"][0] - ref["c_im"][0]) < 1e-16
+        assert abs(lib["b_im"][0] - ref["b_im"][0]) < 1e-15
+        assert abs(lib["theta"] / ref["theta"] - 1) < 1e-8
+
+
+def test_workspace_size_monotone():
+    import paper_2210_03714_gb300 as fm
+    L = fm.lib()
+    a = L.fm_workspace_size(0, 16, 64, 0, 9, None)
+    b = L.fm_workspace_size(0, 16, 256, 0, 9, None)
+    assert 0 < a < b
+    assert L.fm_workspace_size(0, 16, 100000, 0, 9, None) == 0
