@@ -225,6 +225,27 @@ fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, con
                                    double* Abar, double* vbar, int* info_dev,
                                    const fm_opts* opts, void* stream);
 
+/* ---- exp(tA) without any device allocation ------------------------------ */
+/* The paper has no counterpart: this is a deployment variant of fm_expm for
+ * callers that cannot allocate device memory (code that runs where cudaMalloc
+ * is forbidden or could deadlock, such as allocator or stream callbacks, and
+ * hosts that own every device byte).  Same arguments and results as fm_expm
+ * (real, one matrix), but its scratch is a fixed array inside the library
+ * image, reserved on every GPU that loads the library until the process exits;
+ * opts.workspace is ignored and nothing is allocated.
+ *   - d <= FM_NOALLOC_MAX_DIM and the scratch the call needs must fit in
+ *     FM_NOALLOC_SCRATCH_BYTES, else FM_ESHAPE with a message.
+ *   - Every call uses the same array: calls that overlap on the GPU (several
+ *     streams or host threads) race and give wrong results; serialize them.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make it before any stream capture.
+ *   - info_host / s_host (nullable) make the call synchronize the stream. */
+#define FM_NOALLOC_MAX_DIM 128
+#define FM_NOALLOC_SCRATCH_BYTES (2u << 20)
+fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A, int lda, double t,
+                          double* F, int ldf, const fm_opts* opts, void* stream, int* info_host,
+                          int* s_host);
+
 /* Message for the calling thread's last failing call ("" if none). */
 const char* fm_last_error(void);
 

@@ -592,3 +592,117 @@ const char* fm_last_error(void) { return g_err; }
 const char* fm_version(void) { return "fm 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fm_expm_noalloc: exp(tA) for one real matrix with no device allocation.
+//
+// Some callers cannot allocate device memory at all: code running where
+// cudaMalloc is forbidden or would deadlock (inside a custom allocator, a
+// memory-pool callback, or a host function enqueued on a stream), plugins
+// whose host application owns every device byte, and setups that must never
+// grow the device footprint after start-up.  For them this entry point uses a
+// fixed scratch array that lives in the library image itself (a file-scope
+// __device__ array below): it is reserved on every GPU where the library is
+// loaded, until the process exits, and it is the only scratch this call uses.
+// Inputs and outputs are still the caller's device buffers.
+//
+// Limits: d <= FM_NOALLOC_MAX_DIM (128) and the scratch the call needs must fit
+// in FM_NOALLOC_SCRATCH_BYTES (2 MiB); larger problems are rejected with
+// FM_ESHAPE.  All calls share the one array: calls that overlap on the GPU (two
+// streams, or two host threads) race on it and give wrong results; serialize
+// them.  The first call on each device looks up the array's device address
+// (cudaGetSymbolAddress) with that device current; make that first call before
+// any stream capture.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)FM_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices];  // device address of the array, per device
+
+// Once per device, with that device current: the device address of the array.
+// In host code the array's name only stands for it; a kernel must receive this
+// address instead.
+fm_status noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(FM_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FM_OK;
+}
+
+}  // namespace
+
+extern "C" fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A, int lda,
+                                     double t, double* F, int ldf, const fm_opts* optsp,
+                                     void* stream, int* info_host, int* s_host) {
+  cudaStream_t st = (cudaStream_t)stream;
+  fm_opts o = resolve_opts(optsp);
+  fm_status s = check_opts(o);
+  if (s) return s;
+  if (d < 1 || d > FM_NOALLOC_MAX_DIM)
+    return fail(FM_ESHAPE, "fm_expm_noalloc: d must be in [1, FM_NOALLOC_MAX_DIM = 128]");
+  if (!A || !F) return fail(FM_EINVAL, "A or F is NULL");
+  if (lda < d || ldf < d) return fail(FM_ESHAPE, "leading dimension smaller than the row length");
+  FmCoef cf;
+  s = pack(cs, nullptr, false, o.form, cf);
+  if (s) return s;
+  size_t elt, lelt;
+  type_sizes(false, o.precision, elt, lelt);
+  const size_t header = 256;
+  const size_t per_cta = fm_align(ws_layout(JOB_EXPM, d, 0, cf.k, elt, lelt, 0).total);
+  if (header + per_cta > kNoAllocBytes)
+    return fail(FM_ESHAPE, "fm_expm_noalloc: problem needs more scratch than FM_NOALLOC_SCRATCH_BYTES");
+  void* ws = nullptr;
+  s = noalloc_scratch(&ws);
+  if (s) return s;
+  char* base = (char*)ws;
+  FmJob J;
+  memset(&J, 0, sizeof J);
+  J.kind = JOB_EXPM;
+  J.precision = o.precision;
+  J.form = o.form;
+  J.max_ir = o.max_ir_iters;
+  J.ir_tol = o.ir_tol;
+  J.anorm = o.anorm;
+  J.s_fixed = o.s_fixed;
+  J.batch = 1;
+  J.dmax = d;
+  J.d1 = d;
+  J.lda = lda;
+  J.ldf = ldf;
+  J.t1 = t;
+  J.A = A;
+  J.F = F;
+  J.counter = (int*)base;  // work-queue head: must start at zero
+  J.info = (int*)(base + 8);
+  J.sN = (int*)(base + 12);
+  J.ws = base + header;
+  J.ws_stride = per_cta;
+  cudaError_t e = cudaMemsetAsync(base, 0, 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue reset)");
+  const int nb = pick_nb(d);
+  e = launch_persistent(false, o.precision, nb, J, cf, 1, smem_for(false, nb, d), st);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  if (info_host || s_host) {
+    int hdr[4];
+    e = cudaMemcpyAsync(hdr, base, sizeof hdr, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status");
+    if (info_host) *info_host = hdr[2];
+    if (s_host) *s_host = hdr[3];
+  }
+  return FM_OK;
+}
