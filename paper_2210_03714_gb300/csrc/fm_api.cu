@@ -160,7 +160,9 @@ void type_sizes(bool cplx, int precision, size_t& elt, size_t& lelt) {
   lelt = precision == FM_FP64 ? elt : elt / 2;
 }
 
-size_t smem_for(bool cplx, int nb, int dmax) { return launch_smem(cplx, nb, dmax); }
+size_t smem_for(bool cplx, int nb, int dmax, int precision) {
+  return launch_smem(cplx, nb, dmax, uses_tc(cplx, precision));
+}
 
 struct Plan {
   int grid;
@@ -174,11 +176,12 @@ struct Plan {
 Plan make_plan(int kind, bool cplx, int precision, int batch, int dmax, int m, int k, long long nmax) {
   Plan p;
   p.nb = pick_nb(dmax);
-  p.smem = smem_for(cplx, p.nb, dmax);
+  p.smem = smem_for(cplx, p.nb, dmax, precision);
   size_t elt, lelt;
   type_sizes(cplx, precision, elt, lelt);
   int lk = kind == JOB_PHI1MV ? JOB_PHI1 : kind;
-  p.per_cta = fm_align(ws_layout(lk, dmax, m, k, elt, lelt, nmax).total);
+  p.per_cta =
+      fm_align(ws_layout(lk, dmax, m, k, elt, lelt, nmax, uses_tc(cplx, precision)).total);
   int occ = launch_occupancy(cplx, precision, p.nb, p.smem);
   if (occ < 1) occ = 1;
   long long g = (long long)num_sms() * occ;
@@ -662,7 +665,8 @@ extern "C" fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A
   size_t elt, lelt;
   type_sizes(false, o.precision, elt, lelt);
   const size_t header = 256;
-  const size_t per_cta = fm_align(ws_layout(JOB_EXPM, d, 0, cf.k, elt, lelt, 0).total);
+  const size_t per_cta =
+      fm_align(ws_layout(JOB_EXPM, d, 0, cf.k, elt, lelt, 0, uses_tc(false, o.precision)).total);
   if (header + per_cta > kNoAllocBytes)
     return fail(FM_ESHAPE, "fm_expm_noalloc: problem needs more scratch than FM_NOALLOC_SCRATCH_BYTES");
   void* ws = nullptr;
@@ -694,7 +698,7 @@ extern "C" fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A
   cudaError_t e = cudaMemsetAsync(base, 0, 16, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue reset)");
   const int nb = pick_nb(d);
-  e = launch_persistent(false, o.precision, nb, J, cf, 1, smem_for(false, nb, d), st);
+  e = launch_persistent(false, o.precision, nb, J, cf, 1, smem_for(false, nb, d, o.precision), st);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   if (info_host || s_host) {
     int hdr[4];

@@ -68,11 +68,20 @@ struct WsLayout {
   size_t B, C, Y, F, Phi, T1, T2, LU, RL, piv, D;   // matrix-function part
   size_t Cs, LUs, pivs, Ds, Wc, Wn, U, U2, RHS;    // action part
   size_t Wst, Yst, Lam, Yt;                        // adjoint part
+  size_t gx, gy, ex, fy;                           // digit planes (tensor-core products)
   size_t total;
 };
 
+// digit-plane bytes of the tensor-core products (see ozaki.cuh): X operands up
+// to n x n, Y operands up to n x max(n, m); tiles of 128 x 32 and 64 x 32
+FM_HD size_t oz_x_bytes(int n) { return (size_t)((n + 127) / 128) * ((n + 31) / 32) * (7 * 128 * 32 * 2); }
+FM_HD size_t oz_y_bytes(int n, int m) {
+  int w = n > m ? n : m;
+  return (size_t)((w + 63) / 64) * ((n + 31) / 32) * (7 * 64 * 32 * 2);
+}
+
 FM_HD WsLayout ws_layout(int kind, int n, int m, int k, size_t elt, size_t lelt,
-                         long long nmax) {
+                         long long nmax, int tc = 0) {
   WsLayout L = {};
   size_t o = 0;
   const size_t nn = (size_t)n * n;
@@ -107,6 +116,13 @@ FM_HD WsLayout ws_layout(int kind, int n, int m, int k, size_t elt, size_t lelt,
       L.Lam = take((size_t)n * (k + 1) * elt);
       L.Yt = take((size_t)n * (k + 1) * elt);
     }
+  }
+  if (tc) {
+    const int w = n > m ? n : m;
+    L.gx = take(oz_x_bytes(n));
+    L.gy = take(oz_y_bytes(n, m));
+    L.ex = take((size_t)((n + 127) / 128) * 128 * 4);
+    L.fy = take((size_t)((w + 63) / 64) * 64 * 4);
   }
   L.total = o;
   return L;

@@ -19,6 +19,7 @@
 #pragma once
 #include "cta_la.cuh"
 #include "fm_job.h"
+#include "ozaki.cuh"
 
 namespace fmk {
 
@@ -62,6 +63,35 @@ template <> __device__ __forceinline__ zd dscale<zd>(double dr, zd y) { return {
 template <class T> __device__ __forceinline__ typename Tr<T>::R tmag(T a) { return Tr<T>::mag(a); }
 
 // ---------------------------------------------------------------------------
+// P = X Y accurate to double: the Ozaki tensor-core product when the CTA has a
+// tensor-core context (real mixed path), else the double-precision CTA GEMM.
+// Returns nonzero when a tensor-core wait timed out.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ int prod(oz::Ctx* oc, int M, int N, int K, const T* X, int ldx,
+                                    const T* Y, int ldy, T* P, int ldp, char* smem) {
+  if constexpr (sizeof(T) == 8) {
+    if (oc) return oz::gemm(*oc, M, N, K, (const double*)X, ldx, (const double*)Y, ldy,
+                            (double*)P, ldp);
+  }
+  cta_gemm<T>(M, N, K, (typename Tr<T>::R)1, X, ldx, Y, ldy, (typename Tr<T>::R)0, P, ldp,
+              (T*)(smem + 256));
+  return 0;
+}
+
+// point the tensor-core context at this matrix's digit-plane scratch
+__device__ __forceinline__ void oz_bind(oz::Ctx* oc, char* ws, const WsLayout& L) {
+  if (!oc) return;
+  if (threadIdx.x == 0) {
+    oc->gx = (unsigned char*)(ws + L.gx);
+    oc->gy = (unsigned char*)(ws + L.gy);
+    oc->ex = (int*)(ws + L.ex);
+    oc->fy = (int*)(ws + L.fy);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // One shifted solve: Y = M^{-1} RHS with M = I - C (+ exact diagonal rounding
 // D), factors LU (type TL) already computed.  Double precision: one solve in
 // T.  Mixed: solve in TL, then max_ir refinement steps with the residual
@@ -71,7 +101,7 @@ template <class T> __device__ __forceinline__ typename Tr<T>::R tmag(T a) { retu
 template <class T, class TL, int NB>
 __device__ __noinline__ double shifted_solve(const FmJob& J, int n, int m, const T* C, const double* D,
                                 const TL* LU, const int* piv, const T* RHS, T* Y, T* P, TL* RL,
-                                char* smem) {
+                                char* smem, oz::Ctx* oc, int* terr) {
   using TT = Tr<T>;
   using R = typename TT::R;
   const int tid = threadIdx.x;
@@ -91,7 +121,7 @@ __device__ __noinline__ double shifted_solve(const FmJob& J, int n, int m, const
   R* red = (R*)(smem + 64);
   for (int it = 0; it < J.max_ir; ++it) {
     // P = C Y  (double-accurate product)
-    cta_gemm<T>(n, m, n, (R)1, C, n, Y, m, (R)0, P, m, (T*)(smem + 256));
+    *terr |= prod<T>(oc, n, m, n, C, n, Y, m, P, m, smem);
     for (size_t e = tid; e < nm; e += NT) {
       int r = (int)(e / m);
       T v = TT::add(TT::sub(RHS[e], Y[e]), P[e]);
@@ -135,7 +165,8 @@ __device__ __forceinline__ void build_shift(int n, double cre, double cim, const
 // matrix functions: exp (JOB_EXPM), phi_1 with exp (JOB_PHI1, JOB_PHI1MV)
 // ---------------------------------------------------------------------------
 template <class T, class TL, int NB>
-__device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem) {
+__device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem,
+                                        oz::Ctx* oc) {
   using TT = Tr<T>;
   using R = typename TT::R;
   const int tid = threadIdx.x;
@@ -147,7 +178,9 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   const bool mixed = J.precision != 0;
   const bool two = (J.kind != JOB_EXPM);
   const WsLayout L = ws_layout(J.kind == JOB_PHI1MV ? JOB_PHI1 : J.kind, n, J.m, cf.k, sizeof(T),
-                               sizeof(TL), 0);
+                               sizeof(TL), 0, oc != nullptr);
+  oz_bind(oc, ws, L);
+  int terr = 0;
   T* B = (T*)(ws + L.B);
   T* C = (T*)(ws + L.C);
   T* Y = (T*)(ws + L.Y);
@@ -194,7 +227,7 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   __syncthreads();
   const bool hyb = cf.d1[0] != 0 || cf.d2[0] != 0 || (two && (cf.d1[1] != 0 || cf.d2[1] != 0));
   bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0);
-  if (need_b2) cta_gemm<T>(n, n, n, (R)1, B, n, B, n, (R)0, T1, n, (T*)(smem + 256));
+  if (need_b2) terr |= prod<T>(oc, n, n, n, B, n, B, n, T1, n, smem);
   for (int e = tid; e < n * n; e += NT) {
     int r = e / n, c = e % n;
     for (int f = 0; f < (two ? 2 : 1); ++f) {
@@ -235,7 +268,8 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
       T1[e] = J.form == 1 ? tdiag<T>(r, c) : C[e];
     }
     __syncthreads();
-    double q = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL, smem);
+    double q = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL, smem,
+                                        oc, &terr);
     qmax = fmax(qmax, q);
     for (int e = tid; e < n * n; e += NT)
       for (int f = 0; f < (two ? 2 : 1); ++f) {
@@ -247,20 +281,44 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   if (info == 0 && mixed && J.ir_tol > 0 && any_shift && (J.max_ir == 0 || qmax > J.ir_tol)) info = -1;
   // a7: squarings / doublings
   T* T2 = (T*)(ws + L.T2);
-  if (info == 0 || info == -1) {
+  if ((info == 0 || info == -1) && oc != nullptr && s > 0) {
+    // Tensor-core products are accurate relative to the largest entry of each
+    // row and column, so square the deviation from the identity instead of
+    // F itself: (I + E)^2 = I + (2E + E E); for phi_1 with Phi = I + Psi,
+    // (E_F + I) Phi / 2 = I + (Psi + E/2 + E Psi / 2).  Same recurrence.
+    for (int r = tid; r < n; r += NT) {
+      F[r * n + r] = TT::sub(F[r * n + r], TT::one());
+      if (two) Ph[r * n + r] = TT::sub(Ph[r * n + r], TT::one());
+    }
+    __syncthreads();
+    for (int q = 0; q < s; ++q) {
+      if (two) terr |= prod<T>(oc, n, n, n, F, n, Ph, n, T1, n, smem);
+      terr |= prod<T>(oc, n, n, n, F, n, F, n, T2, n, smem);
+      for (int e = tid; e < n * n; e += NT) {
+        const T E = F[e];
+        if (two) Ph[e] = TT::add(TT::add(Ph[e], TT::rscale(E, 0.5)), TT::rscale(T1[e], 0.5));
+        F[e] = TT::add(TT::rscale(E, 2.0), T2[e]);
+      }
+      __syncthreads();
+    }
+    for (int r = tid; r < n; r += NT) {
+      F[r * n + r] = TT::add(F[r * n + r], TT::one());
+      if (two) Ph[r * n + r] = TT::add(Ph[r * n + r], TT::one());
+    }
+  } else if (info == 0 || info == -1) {
     for (int q = 0; q < s; ++q) {
       if (!two) {
-        cta_gemm<T>(n, n, n, (R)1, F, n, F, n, (R)0, T1, n, (T*)(smem + 256));
+        terr |= prod<T>(oc, n, n, n, F, n, F, n, T1, n, smem);
         T* tmp = F; F = T1; T1 = tmp;
       } else {
         // Phi <- (E + I) Phi / 2, then E <- E E
         for (int r = tid; r < n; r += NT) F[r * n + r] = TT::add(F[r * n + r], TT::one());
         __syncthreads();
-        cta_gemm<T>(n, n, n, (R)1, F, n, Ph, n, (R)0, T1, n, (T*)(smem + 256));
+        terr |= prod<T>(oc, n, n, n, F, n, Ph, n, T1, n, smem);
         for (int e = tid; e < n * n; e += NT) Ph[e] = TT::rscale(T1[e], 0.5);
         for (int r = tid; r < n; r += NT) F[r * n + r] = TT::sub(F[r * n + r], TT::one());
         __syncthreads();
-        cta_gemm<T>(n, n, n, (R)1, F, n, F, n, (R)0, T2, n, (T*)(smem + 256));
+        terr |= prod<T>(oc, n, n, n, F, n, F, n, T2, n, smem);
         T* tmp = F; F = T2; T2 = tmp;
       }
     }
@@ -281,9 +339,9 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
     const int m = J.m;
     const int64_t vo = batched ? J.voff[b] : 0;
     const int ldv = batched ? m : J.ldv, ldw = batched ? m : J.ldw;
-    cta_gemm<T>(n, m, n, (R)1, Ph, n, (const T*)J.V + vo, ldv, (R)0, (T*)J.W + vo, ldw,
-                (T*)(smem + 256));
+    terr |= prod<T>(oc, n, m, n, Ph, n, (const T*)J.V + vo, ldv, (T*)J.W + vo, ldw, smem);
   }
+  if (terr && (info == 0 || info == -1)) info = -7;
   if (tid == 0) {
     if (J.info) J.info[b] = info;
     if (J.sN) J.sN[b] = s;
@@ -295,7 +353,8 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
 // action: W = exp(tA) V (JOB_EXPMV)
 // ---------------------------------------------------------------------------
 template <class T, class TL, int NB>
-__device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem) {
+__device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem,
+                                        oz::Ctx* oc) {
   using TT = Tr<T>;
   using R = typename TT::R;
   const int tid = threadIdx.x;
@@ -309,7 +368,9 @@ __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b,
   const double t = J.t ? J.t[b] : J.t1;
   const bool mixed = J.precision != 0;
   const int k = cf.k;
-  const WsLayout L = ws_layout(JOB_EXPMV, n, m, k, sizeof(T), sizeof(TL), 0);
+  const WsLayout L = ws_layout(JOB_EXPMV, n, m, k, sizeof(T), sizeof(TL), 0, oc != nullptr);
+  oz_bind(oc, ws, L);
+  int terr = 0;
   T* B = (T*)(ws + L.B);
   T* Y = (T*)(ws + L.Y);
   T* P = (T*)(ws + L.T1);
@@ -378,8 +439,8 @@ __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b,
   bool any_shift = false;
   // a4-a7: N steps W <- r(B) W
   for (long long q = 0; q < N && info == 0; ++q) {
-    cta_gemm<T>(n, m, n, (R)1, B, n, Wc, m, (R)0, U, m, (T*)(smem + 256));
-    if (cf.d2[0] != 0) cta_gemm<T>(n, m, n, (R)1, B, n, U, m, (R)0, U2, m, (T*)(smem + 256));
+    terr |= prod<T>(oc, n, m, n, B, n, Wc, m, U, m, smem);
+    if (cf.d2[0] != 0) terr |= prod<T>(oc, n, m, n, B, n, U, m, U2, m, smem);
     for (size_t e = tid; e < nm; e += NT) {
       T v = TT::rscale(Wc[e], base);
       if (cf.d1[0] != 0) v = TT::add(v, TT::rscale(U[e], cf.d1[0]));
@@ -404,7 +465,8 @@ __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b,
       const double* Di = (const double*)(ws + L.Ds) + (size_t)i * n;
       for (size_t e = tid; e < nm; e += NT) RHS[e] = J.form == 1 ? Wc[e] : wmul<T>(cre, cim, U[e]);
       __syncthreads();
-      double qq = shifted_solve<T, TL, NB>(J, n, m, Ci, Di, LUi, pivi, RHS, Y, P, RL, smem);
+      double qq = shifted_solve<T, TL, NB>(J, n, m, Ci, Di, LUi, pivi, RHS, Y, P, RL, smem, oc,
+                                           &terr);
       qmax = fmax(qmax, qq);
       for (size_t e = tid; e < nm; e += NT) Wn[e] = TT::add(Wn[e], wmul<T>(br, bi, Y[e]));
       __syncthreads();
@@ -412,6 +474,7 @@ __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b,
     T* tmp = Wc; Wc = Wn; Wn = tmp;
   }
   if (info == 0 && mixed && J.ir_tol > 0 && any_shift && (J.max_ir == 0 || qmax > J.ir_tol)) info = -1;
+  if (terr && (info == 0 || info == -1)) info = -7;
   T* Wo = (T*)J.W + vo;
   for (size_t e = tid; e < nm; e += NT) Wo[(e / m) * ldw + e % m] = Wc[e];
   if (tid == 0) {
@@ -542,37 +605,85 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
 // ---------------------------------------------------------------------------
 // the persistent kernel: a work queue over matrices, largest first
 // ---------------------------------------------------------------------------
-template <class T, class TL, int NB>
-__global__ void __launch_bounds__(NT) fm_persistent(FmJob J, FmCoef cf) {
-  extern __shared__ __align__(16) char smem[];
+template <class T, class TL, int NB, bool TCK = false>
+__global__ void __launch_bounds__(NT, 1) fm_persistent(FmJob J, FmCoef cf) {
+  extern __shared__ __align__(1024) char smem[];
   __shared__ int s_item;
+  __shared__ oz::Ctx s_oz;
+  __shared__ __align__(8) uint64_t s_bars[4];
+  __shared__ uint32_t s_tmem;
   char* ws = J.ws + (size_t)blockIdx.x * J.ws_stride;
   const int limit = J.order ? *(volatile int*)(J.counter + 1) : J.batch;
+  oz::Ctx* oc = nullptr;
+  if constexpr (TCK) {
+    // one tensor-memory allocation (all 512 columns) for the CTA's lifetime;
+    // the launch keeps one CTA per SM, so the allocation never waits
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < 4; ++i) tc::mbar_init(&s_bars[i], 1);
+      tc::mbar_fence_init();
+    }
+    if ((threadIdx.x >> 5) == 0) {
+      tc::tmem_alloc(&s_tmem, oz::TMEM_COLS);
+      tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x == 0) {
+      s_oz.tmem = s_tmem;
+      s_oz.bar = s_bars;
+      s_oz.smem = (unsigned char*)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
+      s_oz.use[0] = s_oz.use[1] = 0;
+      s_oz.err = 0;
+    }
+    __syncthreads();
+    oc = &s_oz;
+  }
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(J.counter, 1);
     __syncthreads();
     const int item = s_item;
     __syncthreads();
     if (item >= limit) break;
+    if constexpr (TCK) {
+      if (s_oz.err) break;  // a tensor-core wait timed out: stop taking work
+    }
     const int b = J.order ? J.order[item] : item;
     if (J.kind == JOB_EXPM || J.kind == JOB_PHI1 || J.kind == JOB_PHI1MV)
-      run_matfun<T, TL, NB>(J, cf, b, ws, smem + 1024);
+      run_matfun<T, TL, NB>(J, cf, b, ws, smem + 1024, oc);
     else if (J.kind == JOB_EXPMV)
-      run_action<T, TL, NB>(J, cf, b, ws, smem + 1024);
+      run_action<T, TL, NB>(J, cf, b, ws, smem + 1024, oc);
     else if constexpr (sizeof(T) == 8 && sizeof(TL) == 8)
       run_adjoint<NB>(J, cf, b, ws, smem + 1024);
+  }
+  if constexpr (TCK) {
+    tc::fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && s_oz.err) {
+      // let MMAs still in flight finish before the memory is released
+      for (int st = 0; st < 2; ++st)
+        if (s_oz.use[st]) {
+          tc::mbar_wait(&s_bars[st], (s_oz.use[st] - 1) & 1, oz::WAIT);      // copies
+          tc::mbar_wait(&s_bars[2 + st], (s_oz.use[st] - 1) & 1, oz::WAIT);  // MMAs
+        }
+    }
+    __syncthreads();
+    tc::fence_after();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(s_tmem, oz::TMEM_COLS);
   }
 }
 
 // dynamic shared memory the kernel needs for matrices up to n
 template <class T, int NB>
-inline size_t fm_smem_bytes(int n) {
+inline size_t fm_smem_bytes(int n, bool tck = false) {
   size_t getrf = ((size_t)n * NB + 2 * GK * GLD) * sizeof(T) + 256;
   size_t getrs = ((size_t)NB * NB + 2 * GK * GLD) * sizeof(T);
   size_t gemm = 256 + 2 * GK * GLD * sizeof(T);
   size_t m = getrf > getrs ? getrf : getrs;
   m = m > gemm ? m : gemm;
-  return 1024 + m + 512;
+  size_t need = 1024 + m + 512;
+  if (tck && need < oz::SMEM + 2048) need = oz::SMEM + 2048;
+  return need;
 }
 
 }  // namespace fmk

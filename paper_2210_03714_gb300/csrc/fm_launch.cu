@@ -4,9 +4,9 @@
 
 namespace fmk {
 
-size_t launch_smem(bool cplx, int nb, int dmax) {
+size_t launch_smem(bool cplx, int nb, int dmax, bool tck) {
   if (cplx) return nb == 16 ? fm_smem_bytes<zd, 16>(dmax) : fm_smem_bytes<zd, 8>(dmax);
-  return nb == 16 ? fm_smem_bytes<double, 16>(dmax) : fm_smem_bytes<double, 8>(dmax);
+  return nb == 16 ? fm_smem_bytes<double, 16>(dmax, tck) : fm_smem_bytes<double, 8>(dmax, tck);
 }
 
 int launch_occupancy(bool cplx, int precision, int nb, size_t smem) {

@@ -8,7 +8,9 @@
 namespace fmk {
 
 // dynamic shared memory of the persistent kernel for matrices up to dmax
-size_t launch_smem(bool cplx, int nb, int dmax);
+size_t launch_smem(bool cplx, int nb, int dmax, bool tck = false);
+// whether a (type, precision) pair runs the tensor-core kernel
+inline bool uses_tc(bool cplx, int precision) { return !cplx && precision != 0; }
 // resident CTAs per SM of the persistent kernel at that shared memory size
 int launch_occupancy(bool cplx, int precision, int nb, size_t smem);
 // the persistent kernel: grid CTAs, each pulling matrices from the queue

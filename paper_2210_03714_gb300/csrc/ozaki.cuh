@@ -1,0 +1,349 @@
+// ozaki.cuh -- double-accurate products P = X Y on the 5th-generation tensor
+// cores, for the refinement residuals and the squarings of the mixed
+// precision path (one CTA, called from the persistent kernel).
+//
+// Error-free splitting (the Ozaki scheme): every row i of X is scaled by 2^-e_i
+// (|x| < 2^e_i) and every column j of Y by 2^-f_j, and the scaled values are
+// cut into S = 7 signed 8-bit digits,  x~ = sum_p d_p 2^(-8p),  d_1 in
+// [-256, 256], d_p in [-128, 127] (p > 1), 56 bits in all.  Each digit is a
+// BF16 number exactly, and so is each product of two digits; a K-long sum of
+// products of digit pairs (p, q) is an integer multiple of 2^(-8(p+q)).  Pairs
+// of one level L = p + q are summed in one FP32 accumulator in tensor memory:
+// with K <= 128 the sum stays within 2^24 units of its level (level 8 is
+// split over two accumulators to stay within it), so every FP32 accumulation
+// is exact, whatever rounding the tensor core's adder applies; levels >= 9 are
+// dropped (with random digits about 2^-53 of max|x| max|y| per entry, like the
+// rounding of a double GEMM of this size).  Every 128 values of K the eight
+// accumulators are read out and added, exactly, into two 64-bit integers:
+// levels 2-5 in units of 2^-40 and levels 6-8 in units of 2^-64.  The final
+// value hi 2^24 + lo (a 128-bit integer) is rounded to double once.  28
+// digit-pair products replace each double product.
+//
+// Accuracy is relative to max_k|x_ik| max_k|y_kj| (fixed point per row and
+// column), so operands with a dominant diagonal (I + E) should be passed as E.
+//
+// Data flow: the digits are written once per operand to global scratch in
+// the tensor-core operand layout (8-row x 16-byte core matrices, K-major),
+// then streamed into shared memory by bulk copies (two stages, mbarriers)
+// while one thread issues tcgen05.mma into eight 128 x 64 accumulators.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "cta_la.cuh"
+#include "tc.cuh"
+
+namespace fmk {
+namespace oz {
+
+constexpr int S = 7;            // digits per value
+constexpr int TM = 128;         // output tile rows (MMA M)
+constexpr int TN = 64;          // output tile columns (MMA N)
+constexpr int KC = 32;          // K per pipeline stage
+constexpr int FLUSH = 4;        // stages per exact accumulation group (K = 128)
+constexpr int NACC = 8;         // accumulators: levels 2..7, and level 8 in two parts
+constexpr uint32_t XBLK = TM * KC * 2;  // bytes of one digit plane of an X tile
+constexpr uint32_t YBLK = TN * KC * 2;
+constexpr uint32_t XSTAGE = S * XBLK;   // 57344
+constexpr uint32_t YSTAGE = S * YBLK;   // 28672
+constexpr uint32_t STAGE = XSTAGE + YSTAGE;
+constexpr uint32_t SMEM = 2 * STAGE;    // 172032 bytes of operand staging
+constexpr uint32_t TMEM_COLS = 512;
+constexpr long long WAIT = 4000000000LL;  // ~2 s of clock cycles per wait
+
+// accumulator of digit pair (p, q), 1-based digits.  Bounds at K = 128 in
+// units of the level (|d_1| <= 256, |d_p| <= 128): level 2: 2^23; 3: 2^23;
+// 4: 2^23 + 2^21; 5: 1.5 2^23; 6: 1.75 2^23; 7: 2^24; level 8 as
+// {(1,7),(7,1),(2,6),(6,2)}: 1.5 2^23 and {(3,5),(5,3),(4,4)}: 1.5 2^22.
+__host__ __device__ constexpr int acc_of(int p, int q) {
+  return (p + q) <= 7 ? (p + q - 2) : ((p <= 2 || q <= 2) ? 6 : 7);
+}
+
+// scratch bytes in global memory for operands up to n x n (X) and n x m (Y)
+__host__ __device__ inline size_t xs_bytes(int n, int k) {
+  return (size_t)((n + TM - 1) / TM) * ((k + KC - 1) / KC) * XSTAGE;
+}
+__host__ __device__ inline size_t ys_bytes(int k, int m) {
+  return (size_t)((m + TN - 1) / TN) * ((k + KC - 1) / KC) * YSTAGE;
+}
+
+struct Ctx {
+  uint32_t tmem;       // TMEM base address (512 columns)
+  uint64_t* bar;       // [0,1] loads of stage 0/1, [2,3] MMAs of stage 0/1
+  unsigned char* smem; // SMEM bytes, 1024-aligned
+  unsigned char* gx;   // digit planes of X (global)
+  unsigned char* gy;   // digit planes of Y (global)
+  int* ex;             // row exponents of X (global, >= M)
+  int* fy;             // column exponents of Y (global, >= N)
+  uint32_t use[2];     // how many times each stage buffer has been filled
+  int err;             // a wait timed out
+};
+
+// byte offset of element (r, k) inside one digit plane of a tile (r < 128 or
+// 64, k < 32): core matrix (r/8, k/8), K-adjacent cores 128 B apart (LBO),
+// row-adjacent cores 512 B apart (SBO)
+__device__ __forceinline__ uint32_t plane_off(int r, int k) {
+  return (uint32_t)(((r >> 3) * (KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// The 7 digits of x * 2^-e (|x| < 2^e), as BF16 values d_p 2^(-8p).
+__device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long q = 0;
+  if (E != 0) {  // zero or subnormal: all digits 0
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+    const int sh = E - 1019 - e;  // q = round(|x| 2^(56 - e))
+    if (sh >= 0) q = mant << sh;
+    else if (sh > -63) q = (mant + (1LL << (-sh - 1))) >> (-sh);
+  }
+  const bool neg = bits < 0;
+  int d[S];
+#pragma unroll
+  for (int p = S - 1; p >= 1; --p) {
+    int v = (int)((q + 128) & 255) - 128;
+    d[p] = v;
+    q = (q - v) >> 8;
+  }
+  d[0] = (int)q;
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+    float f = (float)(neg ? -d[p] : d[p]) * __int_as_float((127 - 8 * (p + 1)) << 23);
+    out[p] = __float2bfloat16_rn(f);
+  }
+}
+
+// round-to-nearest double of (hi 2^24 + lo) 2^e2, hi and lo exact integers
+__device__ __forceinline__ double combine_scaled(long long hi, long long lo, int e2) {
+  __int128 v = ((__int128)hi << 24) + (__int128)lo;
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
+  const int nb = ah ? 128 - __clzll(ah) : 64 - __clzll(al);  // bit length
+  unsigned long long m;
+  int e = e2;
+  if (nb <= 53) {
+    m = al;
+  } else {
+    const int sh = nb - 53;
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    const unsigned __int128 rem = a & (((unsigned __int128)1 << sh) - 1);
+    m = (unsigned long long)(a >> sh);
+    if (rem > half || (rem == half && (m & 1))) m += 1;
+    e += sh;
+  }
+  const double r = ldexp((double)m, e);  // m < 2^54: exact conversion
+  return neg ? -r : r;
+}
+
+// exponent e with |x| < 2^e for the largest |x| (0 for an all-zero set)
+__device__ __forceinline__ int exp_above(double mx) {
+  if (!(mx > 0)) return 0;
+  int e;
+  frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
+  return e;
+}
+
+// Split X (M x K, row-major, ld) row-wise into digit planes in ctx.gx.
+static __device__ void split_rows(Ctx& c, int M, int K, const double* X, int ldx, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int mt = (M + TM - 1) / TM, kc = (K + KC - 1) / KC;
+  for (int r = warp; r < mt * TM; r += NT / 32) {
+    double mx = 0;
+    if (r < M)
+      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[(size_t)r * ldx + k]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) c.ex[r] = exp_above(mx);
+  }
+  __syncthreads();
+  // work item: one row, 8 consecutive k -> 7 x 16-byte stores
+  const int items = mt * TM * kc * (KC / 8);
+  for (int it = tid; it < items; it += NT) {
+    const int k8 = it % (kc * (KC / 8));
+    const int r = it / (kc * (KC / 8));
+    const int e = c.ex[r];
+    __align__(16) __nv_bfloat16 dig[S][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k8 * 8 + j;
+      const double x = (r < M && k < K) ? X[(size_t)r * ldx + k] : 0.0;
+      __nv_bfloat16 t[S];
+      digits(x, e, t);
+#pragma unroll
+      for (int p = 0; p < S; ++p) dig[p][j] = t[p];
+    }
+    const int tile = r / TM, chunk = (k8 * 8) / KC;
+    unsigned char* base = c.gx + ((size_t)tile * kc + chunk) * XSTAGE;
+    const uint32_t off = plane_off(r % TM, (k8 * 8) % KC);
+#pragma unroll
+    for (int p = 0; p < S; ++p) *(uint4*)(base + p * XBLK + off) = *(const uint4*)dig[p];
+  }
+  (void)red;
+}
+
+// Split Y (K x N, row-major, ld) column-wise into digit planes in ctx.gy
+// (stored N-major: the B operand of the MMA is K-major).
+static __device__ void split_cols(Ctx& c, int K, int N, const double* Y, int ldy) {
+  const int tid = threadIdx.x;
+  const int nt = (N + TN - 1) / TN, kc = (K + KC - 1) / KC;
+  for (int j = tid; j < nt * TN; j += NT) {
+    double mx = 0;
+    if (j < N)
+      for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(Y[(size_t)k * ldy + j]));
+    c.fy[j] = exp_above(mx);
+  }
+  __syncthreads();
+  const int items = nt * TN * kc * (KC / 8);
+  for (int it = tid; it < items; it += NT) {
+    const int j = it % (nt * TN);
+    const int k8 = it / (nt * TN);
+    const int e = c.fy[j];
+    __align__(16) __nv_bfloat16 dig[S][8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int k = k8 * 8 + jj;
+      const double y = (j < N && k < K) ? Y[(size_t)k * ldy + j] : 0.0;
+      __nv_bfloat16 t[S];
+      digits(y, e, t);
+#pragma unroll
+      for (int p = 0; p < S; ++p) dig[p][jj] = t[p];
+    }
+    const int tile = j / TN, chunk = (k8 * 8) / KC;
+    unsigned char* base = c.gy + ((size_t)tile * kc + chunk) * YSTAGE;
+    const uint32_t off = plane_off(j % TN, (k8 * 8) % KC);
+#pragma unroll
+    for (int p = 0; p < S; ++p) *(uint4*)(base + p * YBLK + off) = *(const uint4*)dig[p];
+  }
+}
+
+// issue the bulk copies of chunk `chunk` of tile (mt, nt) into stage s
+__device__ __forceinline__ void load_stage(Ctx& c, int s, int mt, int nt, int chunk, int kc) {
+  uint64_t* lb = c.bar + s;
+  unsigned char* dst = c.smem + s * STAGE;
+  tc::mbar_arrive_expect_tx(lb, STAGE);
+  tc::bulk_g2s(dst, c.gx + ((size_t)mt * kc + chunk) * XSTAGE, XSTAGE, lb);
+  tc::bulk_g2s(dst + XSTAGE, c.gy + ((size_t)nt * kc + chunk) * YSTAGE, YSTAGE, lb);
+}
+
+// the 28 digit-pair MMAs of one stage (two K=16 steps each)
+__device__ __forceinline__ void mma_stage(Ctx& c, int s, bool first_in_group) {
+  const uint32_t sx = tc::saddr(c.smem + s * STAGE);
+  const uint32_t sy = sx + XSTAGE;
+  constexpr uint32_t idesc = tc::idesc_bf16(TM, TN);
+  bool fresh[NACC];
+#pragma unroll
+  for (int a = 0; a < NACC; ++a) fresh[a] = first_in_group;
+#pragma unroll
+  for (int p = 1; p <= S; ++p)
+#pragma unroll
+    for (int q = 1; q <= S; ++q) {
+      if (p + q > 8) continue;
+      const int a = acc_of(p, q);
+#pragma unroll
+      for (int ks = 0; ks < KC / 16; ++ks) {
+        const uint64_t ad = tc::sdesc(sx + (p - 1) * XBLK + ks * 256, 128, (KC / 8) * 128);
+        const uint64_t bd = tc::sdesc(sy + (q - 1) * YBLK + ks * 256, 128, (KC / 8) * 128);
+        tc::mma_bf16(c.tmem + a * TN, ad, bd, idesc, fresh[a] ? 0u : 1u);
+        fresh[a] = false;
+      }
+    }
+}
+
+// P (M x N) = X (M x K) Y (K x N), all double, row-major.  All NT threads.
+// Returns 0, or 1 when a wait timed out (P is then not valid).
+static __device__ __noinline__ int gemm(Ctx& c, int M, int N, int K, const double* X, int ldx,
+                                 const double* Y, int ldy, double* P, int ldp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  split_rows(c, M, K, X, ldx, nullptr);
+  split_cols(c, K, N, Y, ldy);
+  tc::fence_proxy_async();
+  __syncthreads();
+  const int mtn = (M + TM - 1) / TM, ntn = (N + TN - 1) / TN, kc = (K + KC - 1) / KC;
+  const int row = 32 * (warp & 3) + lane;  // TMEM lane this thread reads
+  const int colh = 32 * (warp >> 2);       // first of its 32 tile columns
+  __shared__ int s_err;
+  if (tid == 0) s_err = c.err;
+  __syncthreads();
+  for (int mt = 0; mt < mtn; ++mt)
+    for (int nt = 0; nt < ntn; ++nt) {
+      long long ahi[32], alo[32];  // levels 2-5 (units 2^-40), 6-8 (units 2^-64)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) ahi[j] = alo[j] = 0;
+      for (int g0 = 0; g0 < kc; g0 += FLUSH) {
+        const int g1 = min(kc, g0 + FLUSH);
+        if (tid == 0 && !s_err) {
+          // stage s holds chunk (ch % 2); before refilling it, the MMAs of the
+          // chunk that used it last must be done (their commit on bar[2 + s])
+          for (int ch = g0; ch < g1; ++ch) {
+            const int s = ch & 1;
+            if (ch == g0) {
+              load_stage(c, s, mt, nt, ch, kc);
+              c.use[s] += 1;
+            }
+            if (!tc::mbar_wait(c.bar + s, (c.use[s] - 1) & 1, WAIT)) { s_err = 1; break; }
+            tc::fence_after();
+            mma_stage(c, s, ch == g0);
+            tc::mma_commit(c.bar + 2 + s);
+            if (ch + 1 < g1) {
+              const int s2 = (ch + 1) & 1;
+              // the other stage: wait for the MMAs that read it (chunk ch - 1)
+              if (ch > g0 && !tc::mbar_wait(c.bar + 2 + s2, (c.use[s2] - 1) & 1, WAIT)) {
+                s_err = 1;
+                break;
+              }
+              load_stage(c, s2, mt, nt, ch + 1, kc);
+              c.use[s2] += 1;
+            }
+          }
+          // every MMA of the group is covered by the last commit
+          const int sl = (g1 - 1) & 1;
+          if (!s_err && !tc::mbar_wait(c.bar + 2 + sl, (c.use[sl] - 1) & 1, WAIT)) s_err = 1;
+          // the other stage's last commit (if used in this group) completed earlier
+          if (!s_err && g1 - g0 > 1) {
+            const int so = sl ^ 1;
+            if (!tc::mbar_wait(c.bar + 2 + so, (c.use[so] - 1) & 1, WAIT)) s_err = 1;
+          }
+        }
+        __syncthreads();
+        tc::fence_after();
+        if (!s_err) {
+          // read the eight accumulators of this group into the two exact sums
+#pragma unroll 1
+          for (int a = 0; a < NACC; ++a) {
+            uint32_t r[32];
+            tc::tmem_ld32(c.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + a * TN + colh, r);
+            tc::tmem_ld_wait();
+            if (a < 4) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                ahi[j] += __float2ll_rn(__uint_as_float(r[j]) * 1099511627776.0f);  // 2^40
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                alo[j] += __float2ll_rn(__uint_as_float(r[j]) * 18446744073709551616.0f);  // 2^64
+            }
+          }
+        }
+        tc::fence_before();
+        __syncthreads();
+      }
+      // P = (hi 2^24 + lo) 2^(e_i + f_j - 64), rounded once
+      const int i = mt * TM + row;
+      if (!s_err && i < M) {
+        const int ei = c.ex[i];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int jj = nt * TN + colh + j;
+          if (jj < N) P[(size_t)i * ldp + jj] = combine_scaled(ahi[j], alo[j], ei + c.fy[jj] - 64);
+        }
+      }
+      __syncthreads();
+    }
+  const int err = s_err;
+  if (tid == 0) c.err = err;
+  __syncthreads();
+  return err;
+}
+
+}  // namespace oz
+}  // namespace fmk
