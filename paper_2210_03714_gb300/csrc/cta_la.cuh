@@ -187,18 +187,31 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, typename Tr<T>::R alp
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = TT::zero();
-      for (int k0 = 0; k0 < K; k0 += GK) {
+      // the next K chunk is loaded into registers while this one is used
+      constexpr int PER = GT * GK / NT;
+      T ra[PER], rb[PER];
+      auto fetch = [&](int k0) {
 #pragma unroll
-        for (int e0 = 0; e0 < GT * GK; e0 += NT) {
-          int e = e0 + tid;
+        for (int u = 0; u < PER; ++u) {
+          int e = u * NT + tid;
           int r = e >> 4, kk = e & 15;
           int gr = m0 + r, gk = k0 + kk;
-          sA[kk * GLD + r] = (gr < M && gk < K) ? A[(size_t)gr * lda + gk] : TT::zero();
+          ra[u] = (gr < M && gk < K) ? A[(size_t)gr * lda + gk] : TT::zero();
           int kb = e >> 6, c = e & 63;
           int gkb = k0 + kb, gc = n0 + c;
-          sB[kb * GLD + c] = (gkb < K && gc < N) ? B[(size_t)gkb * ldb + gc] : TT::zero();
+          rb[u] = (gkb < K && gc < N) ? B[(size_t)gkb * ldb + gc] : TT::zero();
+        }
+      };
+      fetch(0);
+      for (int k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          int e = u * NT + tid;
+          sA[(e & 15) * GLD + (e >> 4)] = ra[u];
+          sB[(e >> 6) * GLD + (e & 63)] = rb[u];
         }
         __syncthreads();
+        if (k0 + GK < K) fetch(k0 + GK);
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
           T a[4], b[4];
@@ -244,7 +257,8 @@ __device__ __noinline__ int cta_getrf(int n, T* A, int lda, int* piv, T* smem) {
   T* gsm = smem + (size_t)n * NB;           // GEMM tiles
   R* red = (R*)(gsm + 2 * GK * GLD);        // reduction scratch (8 R + 8 int)
   int* redi = (int*)(red + 8);
-  __shared__ int s_piv, s_info;
+  __shared__ int s_piv, s_info, s_moved;
+  __shared__ int s_pp[NB];
   const int tid = threadIdx.x;
   if (tid == 0) s_info = 0;
   for (int j0 = 0; j0 < n; j0 += NB) {
@@ -279,6 +293,9 @@ __device__ __noinline__ int cta_getrf(int n, T* A, int lda, int* piv, T* smem) {
         if (ii == 0x7fffffff) ii = jj;  // all NaN: keep the diagonal
         s_piv = ii;
         piv[j0 + jj] = j0 + ii;
+        s_pp[jj] = j0 + ii;
+        if (jj == 0) s_moved = 0;
+        if (ii != jj) s_moved = 1;
       }
       __syncthreads();
       const int p = s_piv;
@@ -310,10 +327,10 @@ __device__ __noinline__ int cta_getrf(int n, T* A, int lda, int* piv, T* smem) {
       A[(size_t)(j0 + r) * lda + j0 + c] = P[r * NB + c];
     }
     // 4. apply the panel's row exchanges to the other columns (thread owns columns)
-    for (int c = tid; c < n - jb; c += NT) {
+    for (int c = tid; c < n - jb && s_moved; c += NT) {
       int col = c < j0 ? c : c + jb;
       for (int jj = 0; jj < jb; ++jj) {
-        int p = piv[j0 + jj];
+        int p = s_pp[jj];
         if (p != j0 + jj) {
           T t = A[(size_t)(j0 + jj) * lda + col];
           A[(size_t)(j0 + jj) * lda + col] = A[(size_t)p * lda + col];
@@ -426,6 +443,244 @@ __device__ __noinline__ void cta_getrs(int n, const T* LU, int lda, const int* p
       cta_gemm<T>(j0, m, jb, (R)-1, LU + j0, lda, X + (size_t)j0 * ldx, ldx, (R)1, X, ldx, gsm);
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------
+// Solve (P^T L U) X = X, with column slices of X resident in shared memory.
+// For each slice of W columns: gather the rows through the pivot permutation,
+// then forward and backward substitution by 16-row blocks, every update done
+// in shared memory (the factors are read once per slice, 16-column panels
+// staged in shared memory).  smem: n*W slice + 16*n panel + n ints.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __noinline__ void cta_getrs_sm(int n, const T* LU, int lda, const int* piv, int m,
+                                          T* X, int ldx, T* smem, int W) {
+  using TT = Tr<T>;
+  constexpr int BK = 16;
+  T* S = smem;                           // [n][W] slice
+  T* Pn = smem + (size_t)n * W;          // [n][BK] panel (column block of L or U)
+  int* perm = (int*)(Pn + (size_t)n * BK);
+  const int tid = threadIdx.x;
+  if (tid == 0) {  // compose the row exchanges into a gather permutation
+    for (int k = 0; k < n; ++k) perm[k] = k;
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[k];
+      if (p != k) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < m; c0 += W) {
+    const int w = min(W, m - c0);
+    for (int e = tid; e < n * W; e += NT) {
+      const int r = e / W, c = e % W;
+      S[e] = c < w ? X[(size_t)perm[r] * ldx + c0 + c] : TT::zero();
+    }
+    __syncthreads();
+    // forward, unit lower: block rows [j0, j0+jb)
+    for (int j0 = 0; j0 < n; j0 += BK) {
+      const int jb = min(BK, n - j0);
+      // stage L[j0.., j0..j0+jb) (rows j0..n)
+      for (int e = tid; e < (n - j0) * BK; e += NT) {
+        const int r = e / BK, c = e % BK;
+        Pn[e] = c < jb ? LU[(size_t)(j0 + r) * lda + j0 + c] : TT::zero();
+      }
+      __syncthreads();
+      // diagonal block: one thread per column
+      for (int c = tid; c < W; c += NT) {
+        T x[BK];
+#pragma unroll
+        for (int r = 0; r < BK; ++r) x[r] = r < jb ? S[(size_t)(j0 + r) * W + c] : TT::zero();
+#pragma unroll
+        for (int r = 1; r < BK; ++r)
+#pragma unroll
+          for (int l = 0; l < r; ++l) x[r] = TT::sub(x[r], TT::mul(Pn[r * BK + l], x[l]));
+#pragma unroll
+        for (int r = 0; r < BK; ++r)
+          if (r < jb) S[(size_t)(j0 + r) * W + c] = x[r];
+      }
+      __syncthreads();
+      // rows below: S[r, :] -= L[r, j0:j0+jb] S[j0:j0+jb, :]
+      for (int e = tid; e < (n - j0 - jb) * W; e += NT) {
+        const int r = j0 + jb + e / W, c = e % W;
+        T acc = S[(size_t)r * W + c];
+        const T* Lr = Pn + (size_t)(r - j0) * BK;
+#pragma unroll
+        for (int l = 0; l < BK; ++l)
+          if (l < jb) acc = TT::sub(acc, TT::mul(Lr[l], S[(size_t)(j0 + l) * W + c]));
+        S[(size_t)r * W + c] = acc;
+      }
+      __syncthreads();
+    }
+    // backward, upper: block rows from the bottom
+    for (int j0 = ((n - 1) / BK) * BK; j0 >= 0; j0 -= BK) {
+      const int jb = min(BK, n - j0);
+      // stage U[0..j0+jb, j0..j0+jb)
+      for (int e = tid; e < (j0 + jb) * BK; e += NT) {
+        const int r = e / BK, c = e % BK;
+        Pn[e] = c < jb ? LU[(size_t)r * lda + j0 + c] : TT::zero();
+      }
+      __syncthreads();
+      for (int c = tid; c < W; c += NT) {
+        T x[BK];
+#pragma unroll
+        for (int r = 0; r < BK; ++r) x[r] = r < jb ? S[(size_t)(j0 + r) * W + c] : TT::zero();
+#pragma unroll
+        for (int r = BK - 1; r >= 0; --r) {
+          if (r >= jb) continue;
+#pragma unroll
+          for (int l = r + 1; l < BK; ++l)
+            if (l < jb) x[r] = TT::sub(x[r], TT::mul(Pn[(j0 + r) * BK + l], x[l]));
+          x[r] = TT::div(x[r], Pn[(j0 + r) * BK + r]);
+        }
+#pragma unroll
+        for (int r = 0; r < BK; ++r)
+          if (r < jb) S[(size_t)(j0 + r) * W + c] = x[r];
+      }
+      __syncthreads();
+      for (int e = tid; e < j0 * W; e += NT) {
+        const int r = e / W, c = e % W;
+        T acc = S[(size_t)r * W + c];
+        const T* Ur = Pn + (size_t)r * BK;
+#pragma unroll
+        for (int l = 0; l < BK; ++l)
+          if (l < jb) acc = TT::sub(acc, TT::mul(Ur[l], S[(size_t)(j0 + l) * W + c]));
+        S[(size_t)r * W + c] = acc;
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < n * W; e += NT) {
+      const int r = e / W, c = e % W;
+      if (c < w) X[(size_t)r * ldx + c0 + c] = S[e];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Solve (P^T L U) X = X, left-looking by 16-row blocks.  Block j of the
+// solution is X_j = D_j^{-1} (X_j - F_j X_known) with F_j the already solved
+// part of row block j of L (forward) or U (backward), staged k-major in shared
+// memory.  Each thread owns one column (and a share of k when m < NT) and
+// keeps the 16 rows of its column block in registers: per k one global load
+// of X, four broadcast shared loads and 16 FMAs; every block of X is written
+// once.  smem: 16*n panel + NT*16 partial sums.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __noinline__ void cta_getrs_ll(int n, const T* LU, int lda, const int* piv, int m,
+                                          T* X, int ldx, T* smem) {
+  using TT = Tr<T>;
+  constexpr int BK = 16;
+  T* Pn = smem;                       // [k][BK]
+  T* part = smem + (size_t)BK * n;    // [group][BK][lane-column]
+  const int tid = threadIdx.x;
+  const int G = m >= NT ? 1 : min(BK, NT / m);  // groups sharing the k loop
+  const int cpp = NT / G;                       // columns per pass
+  const int g = tid / cpp, cl = tid % cpp;
+  // row exchanges, in order (thread owns columns); none when piv is the identity
+  int moved = 0;
+  for (int k = tid; k < n; k += NT) moved |= (piv[k] != k);
+  if (__syncthreads_or(moved))
+    for (int c = tid; c < m; c += NT)
+      for (int k = 0; k < n; ++k) {
+        const int p = piv[k];
+        if (p != k) {
+          T t = X[(size_t)k * ldx + c];
+          X[(size_t)k * ldx + c] = X[(size_t)p * ldx + c];
+          X[(size_t)p * ldx + c] = t;
+        }
+      }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {  // 0: forward with L, 1: backward with U
+    const int nblk = (n + BK - 1) / BK;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int j0 = pass == 0 ? bi * BK : (nblk - 1 - bi) * BK;
+      const int jb = min(BK, n - j0);
+      // known range of k and the staged panel Pn[k][r] = F(j0 + r, k)
+      const int k0 = pass == 0 ? 0 : j0 + jb, k1 = pass == 0 ? j0 : n;
+      for (int e = tid; e < (k1 - k0 + jb) * BK; e += NT) {
+        const int kk = e / BK, r = e % BK;
+        // rows: the known part [k0, k1), then the diagonal block [j0, j0+jb)
+        const int k = kk < k1 - k0 ? k0 + kk : j0 + (kk - (k1 - k0));
+        Pn[e] = r < jb ? LU[(size_t)(j0 + r) * lda + k] : TT::zero();
+      }
+      __syncthreads();
+      for (int c0 = 0; c0 < m; c0 += cpp) {
+        const int c = c0 + cl;
+        T acc[BK];
+#pragma unroll
+        for (int r = 0; r < BK; ++r) acc[r] = TT::zero();
+        if (c < m) {
+          const int kn = k1 - k0;
+          const int kb = (kn * g) / G, ke = (kn * (g + 1)) / G;
+          // eight loads in flight per thread before their FMAs
+          int kk = kb;
+          for (; kk + 8 <= ke; kk += 8) {
+            T x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = X[(size_t)(k0 + kk + u) * ldx + c];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const T* pr = Pn + (size_t)(kk + u) * BK;
+#pragma unroll
+              for (int r = 0; r < BK; ++r) TT::mac(acc[r], pr[r], x[u]);
+            }
+          }
+          for (; kk < ke; ++kk) {
+            const T x = X[(size_t)(k0 + kk) * ldx + c];
+            const T* pr = Pn + (size_t)kk * BK;
+#pragma unroll
+            for (int r = 0; r < BK; ++r) TT::mac(acc[r], pr[r], x);
+          }
+        }
+        if (G > 1) {
+#pragma unroll
+          for (int r = 0; r < BK; ++r) part[((size_t)g * BK + r) * cpp + cl] = acc[r];
+          __syncthreads();
+          if (g == 0)
+            for (int h = 1; h < G; ++h)
+#pragma unroll
+              for (int r = 0; r < BK; ++r)
+                acc[r] = TT::add(acc[r], part[((size_t)h * BK + r) * cpp + cl]);
+        }
+        if (g == 0 && c < m) {
+          T x[BK];
+#pragma unroll
+          for (int r = 0; r < BK; ++r)
+            x[r] = r < jb ? TT::sub(X[(size_t)(j0 + r) * ldx + c], acc[r]) : TT::zero();
+          const T* D = Pn + (size_t)(k1 - k0) * BK;  // D[l][r] = F(j0 + r, j0 + l)
+          if (pass == 0) {
+#pragma unroll
+            for (int r = 1; r < BK; ++r)
+#pragma unroll
+              for (int l = 0; l < r; ++l) x[r] = TT::sub(x[r], TT::mul(D[l * BK + r], x[l]));
+          } else {
+#pragma unroll
+            for (int r = BK - 1; r >= 0; --r) {
+              if (r >= jb) continue;
+#pragma unroll
+              for (int l = r + 1; l < BK; ++l)
+                if (l < jb) x[r] = TT::sub(x[r], TT::mul(D[l * BK + r], x[l]));
+              x[r] = TT::div(x[r], D[r * BK + r]);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < BK; ++r)
+            if (r < jb) X[(size_t)(j0 + r) * ldx + c] = x[r];
+        }
+        if (G > 1) __syncthreads();
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// slice width that fits the shared memory budget (elements of T)
+__host__ __device__ inline int getrs_width(int n, int m, size_t budget_elems) {
+  long w = (long)((budget_elems - 16L * n - n) / n);
+  if (w > 64) w = 64;
+  if (w > m) w = m;
+  if (w < 1) w = 1;
+  return (int)w;
 }
 
 // ---------------------------------------------------------------------------

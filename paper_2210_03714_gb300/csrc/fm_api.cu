@@ -296,6 +296,7 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   J.order = c.d_dev ? (int*)(base + 256) : nullptr;
   J.ws = base + p.header;
   J.ws_stride = p.per_cta;
+  J.smem_avail = p.smem > 2048 ? p.smem - 2048 : 0;
   J.info = c.d_dev ? c.info_dev : (int*)(base + 8);
   J.sN = c.d_dev ? c.s_dev : (int*)(base + 12);
 
@@ -698,7 +699,9 @@ extern "C" fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A
   cudaError_t e = cudaMemsetAsync(base, 0, 16, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (queue reset)");
   const int nb = pick_nb(d);
-  e = launch_persistent(false, o.precision, nb, J, cf, 1, smem_for(false, nb, d, o.precision), st);
+  const size_t smem = smem_for(false, nb, d, o.precision);
+  J.smem_avail = smem > 2048 ? smem - 2048 : 0;
+  e = launch_persistent(false, o.precision, nb, J, cf, 1, smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   if (info_host || s_host) {
     int hdr[4];

@@ -57,6 +57,7 @@ struct FmJob {
   size_t ws_stride;  // bytes of scratch per CTA
   const int* order;  // matrices sorted by d, largest first
   int* counter;      // work queue head
+  size_t smem_avail; // bytes of shared memory the per-matrix routines may use
 };
 
 FM_HD size_t fm_align(size_t x) { return (x + 255) & ~(size_t)255; }

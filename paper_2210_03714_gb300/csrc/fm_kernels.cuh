@@ -69,10 +69,11 @@ template <class T> __device__ __forceinline__ typename Tr<T>::R tmag(T a) { retu
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ int prod(oz::Ctx* oc, int M, int N, int K, const T* X, int ldx,
-                                    const T* Y, int ldy, T* P, int ldp, char* smem) {
+                                    const T* Y, int ldy, T* P, int ldp, char* smem,
+                                    bool reuse_x = false) {
   if constexpr (sizeof(T) == 8) {
     if (oc) return oz::gemm(*oc, M, N, K, (const double*)X, ldx, (const double*)Y, ldy,
-                            (double*)P, ldp);
+                            (double*)P, ldp, reuse_x);
   }
   cta_gemm<T>(M, N, K, (typename Tr<T>::R)1, X, ldx, Y, ldy, (typename Tr<T>::R)0, P, ldp,
               (T*)(smem + 256));
@@ -89,6 +90,17 @@ __device__ __forceinline__ void oz_bind(oz::Ctx* oc, char* ws, const WsLayout& L
     oc->fy = (int*)(ws + L.fy);
   }
   __syncthreads();
+}
+
+// LU solve with the right-hand sides staged in shared memory when they fit
+template <class T, int NB>
+__device__ __forceinline__ void solve_lu(const FmJob& J, int n, const T* LU, const int* piv, int m,
+                                         T* X, char* smem) {
+  const size_t budget = J.smem_avail / sizeof(T);
+  if (budget > 0 && (size_t)16 * n + (size_t)NT * 16 + 64 <= budget)
+    cta_getrs_ll<T>(n, LU, n, piv, m, X, m, (T*)smem);
+  else
+    cta_getrs<T, NB>(n, LU, n, piv, m, X, m, (T*)smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -109,19 +121,19 @@ __device__ __noinline__ double shifted_solve(const FmJob& J, int n, int m, const
   if (sizeof(TL) == sizeof(T) && J.precision == 0) {
     for (size_t e = tid; e < nm; e += NT) Y[e] = RHS[e];
     __syncthreads();
-    cta_getrs<T, NB>(n, (const T*)LU, n, piv, m, Y, m, (T*)smem);
+    solve_lu<T, NB>(J, n, (const T*)LU, piv, m, Y, smem);
     return -1.0;
   }
   for (size_t e = tid; e < nm; e += NT) RL[e] = cvt<TL, T>(RHS[e]);
   __syncthreads();
-  cta_getrs<TL, NB>(n, LU, n, piv, m, RL, m, (TL*)smem);
+  solve_lu<TL, NB>(J, n, LU, piv, m, RL, smem);
   for (size_t e = tid; e < nm; e += NT) Y[e] = cvt<T, TL>(RL[e]);
   __syncthreads();
   double q = -1.0;
   R* red = (R*)(smem + 64);
   for (int it = 0; it < J.max_ir; ++it) {
     // P = C Y  (double-accurate product)
-    *terr |= prod<T>(oc, n, m, n, C, n, Y, m, P, m, smem);
+    *terr |= prod<T>(oc, n, m, n, C, n, Y, m, P, m, smem, it > 0);
     for (size_t e = tid; e < nm; e += NT) {
       int r = (int)(e / m);
       T v = TT::add(TT::sub(RHS[e], Y[e]), P[e]);
@@ -129,7 +141,7 @@ __device__ __noinline__ double shifted_solve(const FmJob& J, int n, int m, const
       RL[e] = cvt<TL, T>(v);
     }
     __syncthreads();
-    cta_getrs<TL, NB>(n, LU, n, piv, m, RL, m, (TL*)smem);
+    solve_lu<TL, NB>(J, n, LU, piv, m, RL, smem);
     R dmax = 0, ymax = 0;
     for (size_t e = tid; e < nm; e += NT) {
       T dl = cvt<T, TL>(RL[e]);
@@ -547,8 +559,8 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
         }
         for (int r = tid; r < n; r += NT) yi[r] = TT::rscale(u[r], cf.c_re[i]);
         __syncthreads();
-        cta_getrs<T, NB>(n, (T*)(ws + L.LUs) + (size_t)i * n * n, n,
-                         (int*)(ws + L.pivs) + (size_t)i * n, 1, yi, 1, (T*)smem);
+        solve_lu<T, NB>(J, n, (T*)(ws + L.LUs) + (size_t)i * n * n,
+                        (int*)(ws + L.pivs) + (size_t)i * n, 1, yi, smem);
         for (int r = tid; r < n; r += NT) wq[r] = TT::add(wq[r], TT::rscale(yi[r], cf.b_re[0][i]));
         __syncthreads();
       }
@@ -679,8 +691,12 @@ inline size_t fm_smem_bytes(int n, bool tck = false) {
   size_t getrf = ((size_t)n * NB + 2 * GK * GLD) * sizeof(T) + 256;
   size_t getrs = ((size_t)NB * NB + 2 * GK * GLD) * sizeof(T);
   size_t gemm = 256 + 2 * GK * GLD * sizeof(T);
+  // left-looking solves: a 16 x n panel and the partial sums
+  size_t slice = ((size_t)16 * n + (size_t)NT * 16 + 64) * sizeof(T);
+  if (slice > 200 * 1024) slice = 200 * 1024;
   size_t m = getrf > getrs ? getrf : getrs;
   m = m > gemm ? m : gemm;
+  m = m > slice ? m : slice;
   size_t need = 1024 + m + 512;
   if (tck && need < oz::SMEM + 2048) need = oz::SMEM + 2048;
   return need;

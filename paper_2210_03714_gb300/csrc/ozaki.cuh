@@ -132,7 +132,17 @@ __device__ __forceinline__ double combine_scaled(long long hi, long long lo, int
     if (rem > half || (rem == half && (m & 1))) m += 1;
     e += sh;
   }
-  const double r = ldexp((double)m, e);  // m < 2^54: exact conversion
+  // assemble the double directly: m 2^e with m <= 2^53
+  const int nbm = 64 - __clzll((long long)m);
+  const int ef = e + nbm - 1 + 1023;  // biased exponent of the result
+  if (ef >= 1 && ef <= 2046) {
+    const unsigned long long mant = nbm <= 53 ? (m << (53 - nbm)) : (m >> (nbm - 53));
+    const unsigned long long bits = ((unsigned long long)ef << 52) |
+                                    (mant & 0xFFFFFFFFFFFFFULL) |
+                                    (neg ? 0x8000000000000000ULL : 0ULL);
+    return __longlong_as_double((long long)bits);
+  }
+  const double r = ldexp((double)m, e);  // outside the normal range
   return neg ? -r : r;
 }
 
@@ -188,8 +198,10 @@ static __device__ void split_cols(Ctx& c, int K, int N, const double* Y, int ldy
   const int nt = (N + TN - 1) / TN, kc = (K + KC - 1) / KC;
   for (int j = tid; j < nt * TN; j += NT) {
     double mx = 0;
-    if (j < N)
+    if (j < N) {
+#pragma unroll 8
       for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(Y[(size_t)k * ldy + j]));
+    }
     c.fy[j] = exp_above(mx);
   }
   __syncthreads();
@@ -251,10 +263,12 @@ __device__ __forceinline__ void mma_stage(Ctx& c, int s, bool first_in_group) {
 
 // P (M x N) = X (M x K) Y (K x N), all double, row-major.  All NT threads.
 // Returns 0, or 1 when a wait timed out (P is then not valid).
+// reuse_x: X is the operand of the previous call (its digit planes are kept)
 static __device__ __noinline__ int gemm(Ctx& c, int M, int N, int K, const double* X, int ldx,
-                                 const double* Y, int ldy, double* P, int ldp) {
+                                 const double* Y, int ldy, double* P, int ldp,
+                                 bool reuse_x = false) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  split_rows(c, M, K, X, ldx, nullptr);
+  if (!reuse_x) split_rows(c, M, K, X, ldx, nullptr);
   split_cols(c, K, N, Y, ldy);
   tc::fence_proxy_async();
   __syncthreads();
