@@ -597,11 +597,15 @@ __device__ __noinline__ void cta_getrs_ll(int n, const T* LU, int lda, const int
       const int jb = min(BK, n - j0);
       // known range of k and the staged panel Pn[k][r] = F(j0 + r, k)
       const int k0 = pass == 0 ? 0 : j0 + jb, k1 = pass == 0 ? j0 : n;
-      for (int e = tid; e < (k1 - k0 + jb) * BK; e += NT) {
-        const int kk = e / BK, r = e % BK;
-        // rows: the known part [k0, k1), then the diagonal block [j0, j0+jb)
-        const int k = kk < k1 - k0 ? k0 + kk : j0 + (kk - (k1 - k0));
-        Pn[e] = r < jb ? LU[(size_t)(j0 + r) * lda + k] : TT::zero();
+      // rows j0..j0+jb of the factor, read along the row (coalesced), stored
+      // k-major: the known part [k0, k1), then the diagonal block [j0, j0+jb)
+      {
+        const int nk = k1 - k0 + jb;
+        for (int e = tid; e < nk * BK; e += NT) {
+          const int r = e / nk, kk = e % nk;
+          const int k = kk < k1 - k0 ? k0 + kk : j0 + (kk - (k1 - k0));
+          Pn[kk * BK + r] = r < jb ? LU[(size_t)(j0 + r) * lda + k] : TT::zero();
+        }
       }
       __syncthreads();
       for (int c0 = 0; c0 < m; c0 += cpp) {

@@ -617,8 +617,11 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
 // ---------------------------------------------------------------------------
 // the persistent kernel: a work queue over matrices, largest first
 // ---------------------------------------------------------------------------
+// Two CTAs share an SM on the double path (more warps to feed the FP64
+// pipe); the tensor-core path keeps one CTA per SM (its operand staging and
+// tensor memory are sized for the whole SM).
 template <class T, class TL, int NB, bool TCK = false>
-__global__ void __launch_bounds__(NT, 1) fm_persistent(FmJob J, FmCoef cf) {
+__global__ void __launch_bounds__(NT, TCK ? 1 : 2) fm_persistent(FmJob J, FmCoef cf) {
   extern __shared__ __align__(1024) char smem[];
   __shared__ int s_item;
   __shared__ oz::Ctx s_oz;
@@ -628,21 +631,15 @@ __global__ void __launch_bounds__(NT, 1) fm_persistent(FmJob J, FmCoef cf) {
   const int limit = J.order ? *(volatile int*)(J.counter + 1) : J.batch;
   oz::Ctx* oc = nullptr;
   if constexpr (TCK) {
-    // one tensor-memory allocation (all 512 columns) for the CTA's lifetime;
-    // the launch keeps one CTA per SM, so the allocation never waits
+    // mbarriers for the split products; tensor memory is taken per product
     if (threadIdx.x == 0) {
       for (int i = 0; i < 4; ++i) tc::mbar_init(&s_bars[i], 1);
       tc::mbar_fence_init();
     }
-    if ((threadIdx.x >> 5) == 0) {
-      tc::tmem_alloc(&s_tmem, oz::TMEM_COLS);
-      tc::tmem_relinquish();
-    }
-    tc::fence_before();
     __syncthreads();
-    tc::fence_after();
     if (threadIdx.x == 0) {
-      s_oz.tmem = s_tmem;
+      s_oz.tslot = &s_tmem;
+      s_oz.tmem = 0;
       s_oz.bar = s_bars;
       s_oz.smem = (unsigned char*)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
       s_oz.use[0] = s_oz.use[1] = 0;
@@ -667,21 +664,6 @@ __global__ void __launch_bounds__(NT, 1) fm_persistent(FmJob J, FmCoef cf) {
       run_action<T, TL, NB>(J, cf, b, ws, smem + 1024, oc);
     else if constexpr (sizeof(T) == 8 && sizeof(TL) == 8)
       run_adjoint<NB>(J, cf, b, ws, smem + 1024);
-  }
-  if constexpr (TCK) {
-    tc::fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0 && s_oz.err) {
-      // let MMAs still in flight finish before the memory is released
-      for (int st = 0; st < 2; ++st)
-        if (s_oz.use[st]) {
-          tc::mbar_wait(&s_bars[st], (s_oz.use[st] - 1) & 1, oz::WAIT);      // copies
-          tc::mbar_wait(&s_bars[2 + st], (s_oz.use[st] - 1) & 1, oz::WAIT);  // MMAs
-        }
-    }
-    __syncthreads();
-    tc::fence_after();
-    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(s_tmem, oz::TMEM_COLS);
   }
 }
 

@@ -38,8 +38,8 @@ namespace oz {
 constexpr int S = 7;            // digits per value
 constexpr int TM = 128;         // output tile rows (MMA M)
 constexpr int TN = 64;          // output tile columns (MMA N)
-constexpr int KC = 32;          // K per pipeline stage
-constexpr int FLUSH = 4;        // stages per exact accumulation group (K = 128)
+constexpr int KC = 32;          // K per pipeline stage (two MMA K-steps)
+constexpr int FLUSH = 128 / KC; // stages per exact accumulation group (K = 128)
 constexpr int NACC = 8;         // accumulators: levels 2..7, and level 8 in two parts
 constexpr uint32_t XBLK = TM * KC * 2;  // bytes of one digit plane of an X tile
 constexpr uint32_t YBLK = TN * KC * 2;
@@ -67,7 +67,8 @@ __host__ __device__ inline size_t ys_bytes(int k, int m) {
 }
 
 struct Ctx {
-  uint32_t tmem;       // TMEM base address (512 columns)
+  uint32_t* tslot;     // shared word receiving the TMEM address of each product
+  uint32_t tmem;       // TMEM base address (512 columns) while a product runs
   uint64_t* bar;       // [0,1] loads of stage 0/1, [2,3] MMAs of stage 0/1
   unsigned char* smem; // SMEM bytes, 1024-aligned
   unsigned char* gx;   // digit planes of X (global)
@@ -79,8 +80,8 @@ struct Ctx {
 };
 
 // byte offset of element (r, k) inside one digit plane of a tile (r < 128 or
-// 64, k < 32): core matrix (r/8, k/8), K-adjacent cores 128 B apart (LBO),
-// row-adjacent cores 512 B apart (SBO)
+// 64, k < KC): core matrix (r/8, k/8), K-adjacent cores 128 B apart (LBO),
+// row-adjacent cores (KC/8)*128 B apart (SBO)
 __device__ __forceinline__ uint32_t plane_off(int r, int k) {
   return (uint32_t)(((r >> 3) * (KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
@@ -108,8 +109,19 @@ __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out) {
 #pragma unroll
   for (int p = 0; p < S; ++p) {
     float f = (float)(neg ? -d[p] : d[p]) * __int_as_float((127 - 8 * (p + 1)) << 23);
-    out[p] = __float2bfloat16_rn(f);
+    out[p] = __float2bfloat16_rn(f);  // exact: |d_p| <= 256 has at most 8 significant bits
   }
+}
+
+// exact integer k with v = k 2^-q for an FP32 value v known to be such a
+// multiple with |k| < 2^31 (integer bit manipulation, no conversion unit)
+__device__ __forceinline__ int exact_int(uint32_t b, int q) {
+  if ((b & 0x7FFFFFFFu) == 0) return 0;
+  const int E = (int)((b >> 23) & 0xFF);
+  const int mant = (int)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = E - 150 + q;
+  const int k = sh >= 0 ? (mant << sh) : (mant >> (-sh));
+  return (b >> 31) ? -k : k;
 }
 
 // round-to-nearest double of (hi 2^24 + lo) 2^e2, hi and lo exact integers
@@ -277,6 +289,13 @@ static __device__ __noinline__ int gemm(Ctx& c, int M, int N, int K, const doubl
   const int colh = 32 * (warp >> 2);       // first of its 32 tile columns
   __shared__ int s_err;
   if (tid == 0) s_err = c.err;
+  // tensor memory for this product only: all 512 columns in one request, so
+  // a CTA waiting for it never holds part of it (two CTAs share an SM)
+  if (warp == 0) tc::tmem_alloc(c.tslot, TMEM_COLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (tid == 0) c.tmem = *c.tslot;
   __syncthreads();
   for (int mt = 0; mt < mtn; ++mt)
     for (int nt = 0; nt < ntn; ++nt) {
@@ -327,14 +346,17 @@ static __device__ __noinline__ int gemm(Ctx& c, int M, int N, int K, const doubl
             uint32_t r[32];
             tc::tmem_ld32(c.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + a * TN + colh, r);
             tc::tmem_ld_wait();
+            // accumulator a holds an exact multiple of 2^-8L (L = a + 2, level 8
+            // for a = 6, 7): its integer, shifted to the unit of its sum
+            const int L = a < 6 ? a + 2 : 8;
             if (a < 4) {
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                ahi[j] += __float2ll_rn(__uint_as_float(r[j]) * 1099511627776.0f);  // 2^40
+                ahi[j] += (long long)exact_int(r[j], 8 * L) << (40 - 8 * L);  // 2^-40 units
             } else {
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                alo[j] += __float2ll_rn(__uint_as_float(r[j]) * 18446744073709551616.0f);  // 2^64
+                alo[j] += (long long)exact_int(r[j], 8 * L) << (64 - 8 * L);  // 2^-64 units
             }
           }
         }
@@ -354,7 +376,20 @@ static __device__ __noinline__ int gemm(Ctx& c, int M, int N, int K, const doubl
       __syncthreads();
     }
   const int err = s_err;
-  if (tid == 0) c.err = err;
+  if (tid == 0) {
+    c.err = err;
+    if (err) {  // let copies and MMAs still in flight finish before freeing
+      for (int st = 0; st < 2; ++st)
+        if (c.use[st]) {
+          tc::mbar_wait(c.bar + st, (c.use[st] - 1) & 1, WAIT);
+          tc::mbar_wait(c.bar + 2 + st, (c.use[st] - 1) & 1, WAIT);
+        }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(c.tmem, TMEM_COLS);
   __syncthreads();
   return err;
 }
