@@ -44,10 +44,10 @@ def load_peaks():
         return {}
 
 
-# FP64 FMA peak of this GPU: 152 SMs x 64 FP64 flop/clk... is not what GB300
-# has; its FP64 rate is 1.25 TFLOP/s nominal (about 2 DFMA per SM per clock).
-FP64_NOMINAL_TFLOPS = 1.25
-FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch of the persistent kernel on the full
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
+# None until captured for the current kernel.
+TRAFFIC = {"mixed": None, "fp64": None}
 
 
 class Clocks:
@@ -108,11 +108,61 @@ def make_batch():
 
 
 def method_flops(dims, s):
-    """Algorithmic flops of one evaluation (per matrix): k = 8 shifted LU + d-RHS
-    solves at 8/3 d^3 each (Sec. 1: "8/3 d^3 flops") and s squarings at 2 d^3."""
+    """Algorithmic flops of one evaluation (per matrix) in the paper's count: k = 8
+    shifted LU + d-RHS solves at 8/3 d^3 each (Sec. 1: "8/3 d^3 flops") and s
+    squarings at 2 d^3."""
     import numpy as np
     d3 = np.asarray(dims, dtype=np.float64) ** 3
     return float(np.sum(8 * (8.0 / 3.0) * d3 + 2.0 * np.asarray(s, dtype=np.float64) * d3))
+
+
+def pipe_work(dims, s, precision, k=8, max_ir=2, digits=7):
+    """Algorithmic work of the persistent kernel per pipe, per launch (flops).
+
+    double path: every factorization, solve and squaring on the FP64 pipe
+      (k (2/3 + 2) d^3 + 2 s d^3).
+    mixed path: FP32 pipe: k factorizations (2/3 d^3) and 1 + max_ir solves with
+      d right-hand sides (2 d^3 each); tensor pipe (BF16 digit products):
+      k max_ir residual products and s squarings, each digits (digits+1)/2 = 28
+      digit-pair products of 2 d^3.
+    Elementwise work is O(d^2) and left out."""
+    import numpy as np
+    d3 = np.asarray(dims, dtype=np.float64) ** 3
+    sv = np.asarray(s, dtype=np.float64)
+    if precision == "fp64":
+        return {"fp64": float(np.sum(k * (8.0 / 3.0) * d3 + 2.0 * sv * d3))}
+    pairs = digits * (digits + 1) // 2
+    return {"fp32": float(np.sum(k * (2.0 / 3.0 + 2.0 * (1 + max_ir)) * d3)),
+            "tensor_bf16": float(np.sum((k * max_ir + sv) * pairs * 2.0 * d3))}
+
+
+def pipe_peaks(peaks):
+    """TFLOP/s per pipe.  BF16 tensor: the measured burst figure; FP32 and FP64
+    are derived from unit counts and the maximum SM clock (152 SMs; 128 FP32
+    lanes and, on GB300, about 2 FP64 FMA per SM per clock)."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return {"fp32": (152 * 128 * 2 * mhz * 1e6 / 1e12, "derived: 152 SMs x 128 lanes x 2 x max clock"),
+            "fp64": (152 * 2 * 2 * mhz * 1e6 / 1e12, "derived: 152 SMs x 2 DFMA x 2 x max clock"),
+            "tensor_bf16": ((peaks["bf16_tflops"], "measured burst") if "bf16_tflops" in peaks
+                            else (1900.0, "fallback"))}
+
+
+def roofline_of(work, ms, peaks):
+    """The pipe with the largest lower-bound time sets the roofline; every pipe's
+    achieved rate and fraction is listed beside it."""
+    pk = pipe_peaks(peaks)
+    t = ms / 1000.0
+    pipes = {}
+    for name, flops in work.items():
+        peak, src = pk[name]
+        ach = flops / t / 1e12
+        pipes[name] = {"achieved": ach, "peak": peak, "peak_source": src, "frac": ach / peak,
+                       "flops_per_launch": flops}
+    bound = max(pipes, key=lambda n: pipes[n]["flops_per_launch"] / pipes[n]["peak"])
+    b = pipes[bound]
+    return {"bound": "tensor" if bound == "tensor_bf16" else "alu", "pipe": bound,
+            "achieved": b["achieved"], "peak": b["peak"], "unit": "TFLOP/s",
+            "frac": b["frac"], "traffic": None, "pipes": pipes}
 
 
 def cpu_baseline(dims, norms, sample, gpu_F=None, P=None):
@@ -306,15 +356,14 @@ def main():
         e2e = run_e2e(args, fm, torch, flat, dims, cs, stream, barrier, max_over_ranks, world,
                       dev)
 
-    # roofline of the dominant kernel (the persistent per-matrix kernel)
-    flops = method_flops(dims, s_host)
+    # roofline of the dominant kernel (the persistent per-matrix kernel: every
+    # launch but the microsecond ordering kernel), from the per-step event time
     peaks = load_peaks()
-    achieved = flops / (ms / 1000.0) / 1e12
-    fp64_peak = peaks.get("fp64_tflops", FP64_NOMINAL_TFLOPS)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "note": "method flops (8 x 8/3 d^3 + 2 s d^3 per matrix) per launch / call time; "
-                        "peak = FP64 FMA rate (nominal 1.25 TFLOP/s)"}
+    achieved = method_flops(dims, s_host) / (ms / 1000.0) / 1e12
+    roofline = roofline_of(pipe_work(dims, s_host, args.precision), ms, peaks)
+    roofline["traffic"] = TRAFFIC.get(args.precision) if BATCH == 4096 and not args.dims else None
+    fp64_roofline = (roofline_of(pipe_work(dims, s_host, "fp64"), fp64_ms, peaks)
+                     if fp64_ms else None)
 
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -333,6 +382,7 @@ def main():
             "speedup_vs_fp64": (fp64_ms / ms) if fp64_ms else None,
             "max_rel_diff_vs_fp64": maxdiff,
             "method_tflops": achieved,
+            "fp64_roofline": fp64_roofline,
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(dims, norms, args.cpu_sample, F, P)
