@@ -111,6 +111,22 @@ fm_status fm_theta(const fm_coeffs* cs, int func, double tol, double* theta_out)
 
 enum { FM_FP64 = 0, FM_FP32_IR = 1 };   /* precision of the shifted solves      */
 enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       */
+/* Execution path.  FM_PATH_CTA: one thread block per matrix, every step in it
+ * (LU with partial pivoting of each shifted matrix; d <= fm_max_dim()).
+ * FM_PATH_GRID (single-matrix calls only): the matrix is spread over every SM;
+ * each shifted system (I - c_i B) Y_i = c_i B is solved by the residual-
+ * correction (Newton-Schulz) iteration Y <- Y + (I + Y)(C - (I - C) Y),
+ * C = c_i B, whose only heavy steps are matrix products, until the largest
+ * residual entry times d is below 2^-30 (then one more correction); it needs
+ * the spectral radius of c_i B well below 1, as every set here gives with
+ * ||B||_1 <= theta (||c_i B||_1 <= 0.05).  Products run on the FP64 pipe
+ * (FM_FP64) or as BF16 digit products on the tensor cores with exact
+ * accumulation (FM_FP32_IR), both accurate to double.  The action forms the
+ * matrix r(B) once and applies it N times.  The call synchronizes its stream
+ * (s or N and the iteration counts are chosen on the host).
+ * FM_PATH_AUTO: single-matrix calls with d > fm_max_dim() take the grid path,
+ * everything else the one-CTA kernels. */
+enum { FM_PATH_AUTO = 0, FM_PATH_CTA = 1, FM_PATH_GRID = 2 };
 
 typedef struct {
   int precision;      /* FM_FP64: every step in double.  FM_FP32_IR: factor and
@@ -125,6 +141,7 @@ typedef struct {
   long nsteps;        /* > 0: force N for actions (default 0)                   */
   void* workspace;    /* device scratch or NULL                                 */
   size_t workspace_bytes;
+  int path;           /* FM_PATH_AUTO (default), FM_PATH_CTA or FM_PATH_GRID     */
 } fm_opts;
 
 /* Defaults: FM_FP32_IR, FM_ROUNDOFF, 2 refinement steps, ir_tol 1e-8, automatic
@@ -139,7 +156,10 @@ enum { FM_JOB_EXPM = 0, FM_JOB_PHI1 = 1, FM_JOB_EXPMV = 2, FM_JOB_PHI1MV = 3,
  * vectors, k terms, on the current device. */
 size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_opts* opts);
 
-/* Largest d the kernels accept (same for every job). */
+/* Largest d of the one-CTA-per-matrix kernels: every batched call, and the
+ * single-matrix calls on FM_PATH_CTA.  Single-matrix exp / phi_1 and their
+ * actions (real and complex) of larger order take the grid path, limited by
+ * device memory only (fm_workspace_size with batch = 1). */
 int fm_max_dim(void);
 
 /* ---- single matrix ------------------------------------------------------ */

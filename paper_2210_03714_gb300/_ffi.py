@@ -32,7 +32,8 @@ class fm_coeffs(C.Structure):
 class fm_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("form", C.c_int), ("max_ir_iters", C.c_int),
                 ("ir_tol", C.c_double), ("anorm", C.c_double), ("s_fixed", C.c_int),
-                ("nsteps", C.c_long), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+                ("nsteps", C.c_long), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+                ("path", C.c_int)]
 
 
 class FmError(RuntimeError):
@@ -125,5 +126,7 @@ def default_opts(**kw):
             v = {"fp64": FM_FP64, "mixed": FM_FP32_IR, "fp32_ir": FM_FP32_IR}[v]
         if k == "form" and isinstance(v, str):
             v = {"roundoff": FM_ROUNDOFF, "plain": FM_PLAIN}[v]
+        if k == "path" and isinstance(v, str):
+            v = {"auto": 0, "cta": 1, "grid": 2}[v]
         setattr(o, k, v)
     return o

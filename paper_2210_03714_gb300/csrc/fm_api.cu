@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/fm.h"
+#include "fm_grid.h"
 #include "fm_job.h"
 #include "fm_launch.h"
 
@@ -151,6 +152,7 @@ fm_status check_opts(const fm_opts& o) {
   if (!(o.ir_tol >= 0) || !isfinite(o.anorm) || o.anorm < 0) return fail(FM_EINVAL, "opts.ir_tol / opts.anorm");
   if (o.s_fixed > 1000) return fail(FM_EINVAL, "opts.s_fixed");
   if (o.nsteps < 0) return fail(FM_EINVAL, "opts.nsteps");
+  if (o.path < FM_PATH_AUTO || o.path > FM_PATH_GRID) return fail(FM_EINVAL, "opts.path");
   return FM_OK;
 }
 
@@ -222,12 +224,64 @@ struct Call {
   long* n_host;
 };
 
+// single matrix over the whole GPU (fm_grid.cu)
+fm_status run_grid(const Call& c, const fm_opts& o, cudaStream_t st) {
+  const int n = c.d1;
+  const bool act = c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV;
+  if (act && c.m < 1) return fail(FM_ESHAPE, "m must be >= 1");
+  if (!c.A) return fail(FM_EINVAL, "A is NULL");
+  if (!act && !c.F) return fail(FM_EINVAL, "output is NULL");
+  if (act && (!c.V || !c.W)) return fail(FM_EINVAL, "V / W is NULL");
+  if (c.lda < n || (!act && c.ldf < n) || (c.E && c.lde < n) ||
+      (act && (c.ldv < c.m || c.ldw < c.m)))
+    return fail(FM_ESHAPE, "leading dimension smaller than the row length");
+  GridJob g;
+  memset(&g, 0, sizeof g);
+  fm_status s = pack(c.ce, c.cp, c.cplx, o.form, g.cf);
+  if (s) return s;
+  g.kind = c.kind;
+  g.cplx = c.cplx;
+  g.precision = o.precision;
+  g.form = o.form;
+  g.d = n;
+  g.m = c.m;
+  g.A = c.A;
+  g.lda = c.lda;
+  g.t = c.t1;
+  g.F = c.F;
+  g.ldf = c.ldf;
+  g.E = c.E;
+  g.lde = c.lde;
+  g.V = c.V;
+  g.ldv = c.ldv;
+  g.W = c.W;
+  g.ldw = c.ldw;
+  g.anorm = o.anorm;
+  g.s_fixed = o.s_fixed;
+  g.nsteps = o.nsteps;
+  g.max_iters = 40;
+  g.st = st;
+  g.info_host = c.info_host;
+  g.s_host = c.s_host;
+  g.n_host = c.n_host;
+  g.ws_bytes = grid_ws_bytes(c.kind, c.cplx, o.precision, n, c.m);
+  s = get_scratch(g.ws_bytes, &o, &g.ws, st);
+  if (s) return s;
+  return (fm_status)grid_run(g, g_err, sizeof g_err);
+}
+
 fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   fm_opts o = resolve_opts(optsp);
   fm_status s = check_opts(o);
   if (s) return s;
   if (c.kind == JOB_ADJ) o.precision = FM_FP64;
   if (c.batch < 1) return fail(FM_ESHAPE, "batch must be >= 1");
+  const bool single = c.d_dev == nullptr && c.kind != JOB_ADJ;
+  if (o.path == FM_PATH_GRID && !single)
+    return fail(FM_EINVAL, "opts.path = FM_PATH_GRID is for single-matrix calls");
+  if (single && c.dmax >= 1 &&
+      (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && c.dmax > fm_max_dim())))
+    return run_grid(c, o, st);
   if (c.dmax < 1 || c.dmax > fm_max_dim()) return fail(FM_ESHAPE, "d (or dmax) must be in [1, fm_max_dim()]");
   if ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV) && c.m < 1) return fail(FM_ESHAPE, "m must be >= 1");
   if (!c.A) return fail(FM_EINVAL, "A is NULL");
@@ -337,6 +391,7 @@ void fm_opts_default(fm_opts* o) {
   o->anorm = 0.0;
   o->s_fixed = -1;
   o->nsteps = 0;
+  o->path = FM_PATH_AUTO;
 }
 
 int fm_max_dim(void) { return 1024; }
@@ -354,7 +409,11 @@ size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_op
     case FM_JOB_EXPMV_ADJ: kind = JOB_ADJ; nmax = o.nsteps > 0 ? o.nsteps : 1; o.precision = FM_FP64; break;
     default: return 0;
   }
-  if (batch < 1 || dmax < 1 || dmax > fm_max_dim() || k < 1 || k > FM_MAX_TERMS) return 0;
+  if (batch < 1 || dmax < 1 || k < 1 || k > FM_MAX_TERMS) return 0;
+  if (batch == 1 && kind != JOB_ADJ &&
+      (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && dmax > fm_max_dim())))
+    return grid_ws_bytes(kind, cplx, o.precision, dmax, m);
+  if (dmax > fm_max_dim()) return 0;
   return make_plan(kind, cplx, o.precision, batch, dmax, m, k, nmax).total;
 }
 

@@ -1,0 +1,49 @@
+// fm_grid.h -- host side of the grid-wide path (one matrix over every SM),
+// called by the C ABI for single-matrix calls of large order.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "fm_job.h"
+
+namespace fmk {
+
+struct GridJob {
+  int kind;       // JOB_EXPM, JOB_PHI1, JOB_EXPMV or JOB_PHI1MV
+  bool cplx;
+  int precision;  // 0: products on the FP64 pipe; else tensor-core digit products
+  int form;       // 0 roundoff, 1 plain
+  int d, m;
+  const void* A;
+  int lda;
+  double t;
+  void* F;        // exp (or phi_1) result, ldf
+  int ldf;
+  void* E;        // phi_1 only: exp result (nullable), lde
+  int lde;
+  const void* V;  // actions: d x m, ldv
+  int ldv;
+  void* W;        // actions: d x m result, ldw
+  int ldw;
+  double anorm;
+  int s_fixed;
+  long long nsteps;
+  int max_iters;  // limit of the correction iterations per shifted system
+  FmCoef cf;
+  void* ws;
+  size_t ws_bytes;
+  cudaStream_t st;
+  int* info_host;
+  int* s_host;
+  long* n_host;
+};
+
+// scratch bytes the grid path needs
+size_t grid_ws_bytes(int kind, bool cplx, int precision, int d, int m);
+
+// runs the whole evaluation; returns an fm_status value and writes a message
+// into msg on failure.  Synchronizes the stream (the step counts are chosen on
+// the host from the norm computed on the device).
+int grid_run(const GridJob& g, char* msg, size_t msglen);
+
+}  // namespace fmk

@@ -1,0 +1,199 @@
+"""Parity of the grid-wide path (one matrix over every SM) with the FP64 oracle.
+
+The grid path solves each shifted system by residual correction instead of
+LU; both sides solve the same systems to double accuracy, so the bar is the
+same 1e-12 relative Frobenius error per result.  Sizes span several 128 x 64
+product tiles with ragged edges; d > 1024 checks the automatic routing; the
+Hermitian action at d = 4096, m = 256 (N = 206 steps) is checked through
+properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_03714_gb300 import workloads as wl
+
+from _common import TOL_FP64, need_gpu, oracle_set, relerr
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module")
+def fm():
+    need_gpu()
+    import paper_2210_03714_gb300 as fm_
+    fm_.lib()
+    return fm_
+
+
+def T(x):
+    import torch
+    x = np.ascontiguousarray(x)
+    dt = torch.complex128 if np.iscomplexobj(x) else torch.float64
+    return torch.tensor(x, dtype=dt, device="cuda")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("d,norm", [(1, 0.3), (37, 0.05), (200, 6.0), (300, 40.0)])
+def test_grid_expm(fm, prec, d, norm):
+    A = wl.dense_scaled(d, norm, 500 + d)
+    cs = oracle_set("R8")
+    F_ref, s_ref, _ = oracle.expm(A, 1.0, cs)
+    F, info, s = fm.expm(T(A), 1.0, fm.Coeffs(cs), precision=prec, path="grid")
+    assert info == 0 and s == s_ref
+    assert relerr(F.cpu().numpy(), F_ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["R4", "R10star"])
+def test_grid_expm_other_sets(fm, prec, name):
+    """k = 4 (one zero node) and the hybrid R10* (d1 B + d2 B^2 terms).  R10*
+    buys its large theta with large weights (Sec. 4.3: max |b_i| ~ 5e6), so any
+    double evaluation of sum_i b_i Y_i rounds at u sum_i |b_i c_i| theta, and
+    s squarings double that relative error s times: the bar is
+    max(1e-12, 2^s u sum_i |b_i c_i| theta)."""
+    A = wl.dense_scaled(150, 3.0, 777)
+    cs = oracle_set(name)
+    F_ref, s_ref, _ = oracle.expm(A, 1.0, cs)
+    F, info, s = fm.expm(T(A), 1.0, fm.Coeffs(cs), precision=prec, path="grid")
+    assert info == 0 and s == s_ref
+    bc = np.abs((np.array(cs["b_re"]) + 1j * np.array(cs["b_im"])) *
+                (np.array(cs["c_re"]) + 1j * np.array(cs["c_im"]))).sum()
+    tol = max(TOL_FP64, 2.0 ** s * 2.0 ** -53 * bc * cs["theta"])
+    assert relerr(F.cpu().numpy(), F_ref) <= tol
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid_plain_form(fm, prec):
+    A = wl.dense_scaled(130, 2.0, 778)
+    cs = oracle_set("R8")
+    F_ref, s_ref, _ = oracle.expm(A, 1.0, cs, form=oracle.PLAIN)
+    F, info, s = fm.expm(T(A), 1.0, fm.Coeffs(cs), precision=prec, path="grid", form="plain")
+    assert info == 0 and s == s_ref
+    # the plain form carries the cancellation of sum_i b_i (Sec. 4.3) on both sides
+    assert relerr(F.cpu().numpy(), F_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid_phi1(fm, prec):
+    A = wl.dense_scaled(170, 3.0, 21)
+    ce, cp = oracle_set("R8"), oracle_set("R8_phi1")
+    Phi_ref, E_ref, s_ref, _ = oracle.phi1(A, 0.7, ce, cp)
+    Phi, E, info, s = fm.phi1(T(A), 0.7, fm.Coeffs(ce), fm.Coeffs(cp), precision=prec,
+                              path="grid")
+    assert info == 0 and s == s_ref
+    assert relerr(Phi.cpu().numpy(), Phi_ref) <= TOL_FP64
+    assert relerr(E.cpu().numpy(), E_ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid_phi1mv(fm, prec):
+    A = wl.dense_scaled(140, 2.0, 23)
+    V = np.random.default_rng(24).standard_normal((140, 5))
+    ce, cp = oracle_set("R8"), oracle_set("R8_phi1")
+    W_ref, s_ref, _ = oracle.phi1mv(A, V, 0.5, ce, cp)
+    W, info, s = fm.phi1mv(T(A), T(V), 0.5, fm.Coeffs(ce), fm.Coeffs(cp), precision=prec,
+                           path="grid")
+    assert info == 0 and s == s_ref
+    assert relerr(W.cpu().numpy(), W_ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("d,m", [(1, 1), (200, 1), (257, 70)])
+def test_grid_expmv(fm, prec, d, m):
+    A = wl.dense_scaled(d, 4.0, 600 + d)
+    V = np.random.default_rng(601 + d).standard_normal((d, m))
+    cs = oracle_set("R8")
+    W_ref, N_ref, _ = oracle.expmv(A, V, 1.0, cs)
+    W, info, N = fm.expmv(T(A), T(V), 1.0, fm.Coeffs(cs), precision=prec, path="grid")
+    assert info == 0 and N == N_ref
+    assert relerr(W.cpu().numpy(), W_ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid_complex(fm, prec):
+    A, V, rho = wl.hermitian_action(d=160, m=9, rho=20.0, seed=62)
+    cs = oracle_set("R8")
+    W_ref, N_ref, _ = oracle.zexpmv(A, V, 1.0, cs, anorm=rho)
+    W, info, N = fm.expmv(T(A), T(V), 1.0, fm.Coeffs(cs), precision=prec, anorm=rho,
+                          path="grid")
+    assert info == 0 and N == N_ref
+    assert relerr(W.cpu().numpy(), W_ref) <= TOL_FP64
+    G = np.random.default_rng(63).standard_normal((130, 130)) + 1j * np.random.default_rng(
+        64).standard_normal((130, 130))
+    G *= 3.0 / np.abs(G).sum(0).max()
+    F_ref, s_ref, _ = oracle.zexpm(G, 1.0, cs)
+    F, info, s = fm.expm(T(G), 1.0, fm.Coeffs(cs), precision=prec, path="grid")
+    assert info == 0 and s == s_ref
+    assert relerr(F.cpu().numpy(), F_ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid_auto_route_d1100(fm, prec):
+    """d > fm_max_dim() takes the grid path without being asked."""
+    d = 1100
+    A = wl.dense_scaled(d, 2.0, 1100)
+    V = np.random.default_rng(1101).standard_normal((d, 3))
+    cs = oracle_set("R8")
+    W_ref, N_ref, _ = oracle.expmv(A, V, 1.0, cs)
+    W, info, N = fm.expmv(T(A), T(V), 1.0, fm.Coeffs(cs), precision=prec)
+    assert info == 0 and N == N_ref
+    assert relerr(W.cpu().numpy(), W_ref) <= TOL_FP64
+
+
+def test_grid_matches_cta_path(fm):
+    """The two paths solve the same shifted systems: same s, results within the bar."""
+    A = wl.dense_scaled(256, 5.0, 31)
+    cs = fm.Coeffs("R8")
+    F1, i1, s1 = fm.expm(T(A), 1.0, cs, path="cta")
+    F2, i2, s2 = fm.expm(T(A), 1.0, cs, path="grid")
+    assert i1 == i2 == 0 and s1 == s2
+    assert relerr(F2.cpu().numpy(), F1.cpu().numpy()) <= TOL_FP64
+
+
+def test_grid_nonfinite_and_zero(fm):
+    A = wl.dense_scaled(70, 1.0, 5)
+    A[3, 4] = np.nan
+    F, info, s = fm.expm(T(A), 1.0, "R8", path="grid")
+    assert info == -2
+    Z = np.zeros((90, 90))
+    F, info, s = fm.expm(T(Z), 1.0, "R8", path="grid")
+    assert info == 0 and s == 0
+    assert np.array_equal(F.cpu().numpy(), np.eye(90))
+
+
+def test_grid_rejects_batched(fm):
+    import torch
+    P = fm.Packed([T(wl.dense_scaled(8, 1.0, 1))])
+    with pytest.raises(fm.FmError):
+        fm.expm_batched(P, torch.ones(1, dtype=torch.float64, device="cuda"), "R8",
+                        path="grid")
+
+
+def test_hermitian_action_d4096(fm):
+    """The Hermitian action at full size: A = -iH, d = 4096, V 4096 x 256,
+    spectral radius 20 (anorm = 20 gives N = 206).  Checked by (1) the mixed
+    and the double grid forms agreeing at 1e-12, (2) unitarity: every column
+    keeps its norm to N u-level, (3) the closed form Q exp(-i Lambda) Q^H V
+    from a double eigendecomposition, within its own rounding (d u ||H|| per
+    entry of the decomposition, about 1e-12 relative here)."""
+    import torch
+    A, V, rho = wl.hermitian_action(d=4096, m=256, rho=20.0, seed=2000)
+    cs = fm.Coeffs("R8")
+    N_ref = oracle.select_nsteps(rho, cs.theta)
+    assert N_ref == 206
+    Wm, info, N = fm.expmv(T(A), T(V), 1.0, cs, precision="mixed", anorm=rho)
+    assert info == 0 and N == N_ref
+    Wd, info, N = fm.expmv(T(A), T(V), 1.0, cs, precision="fp64", anorm=rho)
+    assert info == 0 and N == N_ref
+    Wm, Wd = Wm.cpu().numpy(), Wd.cpu().numpy()
+    assert relerr(Wm, Wd) <= TOL_FP64
+    nv = np.linalg.norm(V, axis=0)
+    assert np.max(np.abs(np.linalg.norm(Wm, axis=0) - nv) / nv) <= 1e-12
+    H = 1j * A  # A = -iH
+    lam, Q = np.linalg.eigh(H)
+    Wx = Q @ (np.exp(-1j * lam)[:, None] * (Q.conj().T @ V))
+    assert relerr(Wm, Wx) <= 1e-11
+    del torch
