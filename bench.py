@@ -190,6 +190,91 @@ def cpu_baseline(dims, norms, sample, gpu_F=None, P=None):
                 seconds=dt), errs
 
 
+def run_single(args):
+    """One large matrix on the grid path: the Hermitian action (A = -iH, d = 4096,
+    V complex 4096 x 256, spectral radius 20, R8, N = 206) or exp of one real
+    dense matrix of order --dim (entries N(0,1)/sqrt(d), ||A||_1 = 4, R8)."""
+    import numpy as np
+    import torch
+    import paper_2210_03714_gb300 as fm
+    from paper_2210_03714_gb300 import workloads as wl
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fm.lib()
+    cs = fm.Coeffs("R8")
+    if args.workload == "hermitian":
+        A, V, rho = wl.hermitian_action(d=4096, m=256, rho=20.0, seed=2000)
+        Ad = torch.tensor(A, dtype=torch.complex128, device=dev)
+        Vd = torch.tensor(V, dtype=torch.complex128, device=dev)
+        call = lambda prec: fm.expmv(Ad, Vd, 1.0, cs, precision=prec, anorm=rho)[0]
+        workload = ("exp(-iH) V: H dense Hermitian d=4096 (G complex N(0,1)/sqrt(d), "
+                    "spectral radius 20), V complex 4096x256, R8, anorm=20 (N=206 steps)")
+        metric = "complex action evals/sec at <=1e-12 rel err (grid path)"
+        ref = lambda: fm.expmv(Ad, Vd, 1.0, cs, precision="fp64", anorm=rho)[0]
+    else:
+        d = args.dim
+        A = wl.dense_scaled(d, 4.0, 9, scale_sqrt=True)
+        Ad = torch.tensor(A, dtype=torch.float64, device=dev)
+        call = lambda prec: fm.expm(Ad, 1.0, cs, precision=prec)[0]
+        workload = "exp(A): one real dense matrix d=%d, N(0,1)/sqrt(d) scaled to ||A||_1=4, R8" % d
+        metric = "dense exp evals/sec at <=1e-12 rel err (grid path)"
+        ref = lambda: fm.expm(Ad, 1.0, cs, precision="fp64")[0]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        call(args.precision)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    per = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = call(args.precision)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    st = fm.last_stats()
+    ms = sum(per) / len(per)
+    peaks = load_peaks()
+    pk = pipe_peaks(peaks)
+    if args.precision == "mixed":
+        pipe, flops = "tensor_bf16", st["digit_flops"]
+    else:
+        pipe, flops = "fp64", st["product_flops"]
+    ach = flops / (ms / 1000.0) / 1e12
+    roofline = {"bound": "tensor" if pipe == "tensor_bf16" else "alu", "pipe": pipe,
+                "achieved": ach, "peak": pk[pipe][0], "peak_source": pk[pipe][1],
+                "unit": "TFLOP/s", "frac": ach / pk[pipe][0], "traffic": None,
+                "note": "all grid-path kernels of one call (products, splits, epilogues, "
+                        "elementwise) over the call's event time; flops = the digit products "
+                        "(28 per product flop) or the double products"}
+    diff = None
+    fp64_ms = None
+    if not args.no_fp64 and args.precision == "mixed":
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R = ref()
+        torch.cuda.synchronize()
+        fp64_ms = (time.perf_counter() - t0) * 1e3
+        diff = float(((out - R).norm() / R.norm()).item())
+    line = {"metric": metric, "value": 1000.0 / ms, "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "replicas", "vs_baseline": None,
+            "dtype": "bf16 digits, f64 accumulate" if args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": {"workload": workload, "precision": args.precision,
+                                             "path": "grid", "l2": "working set > L2"},
+            "roofline": roofline, "products": st["products"],
+            "corrections": st["corrections"], "fp64_ms": fp64_ms,
+            "rel_diff_vs_fp64": diff, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -265,7 +350,14 @@ def main():
                     help="matrices per step (default 4096; smaller values are for profiling)")
     ap.add_argument("--dims", default=None,
                     help="comma-separated orders d is drawn from (default 16,32,...,256)")
+    ap.add_argument("--workload", default="batch", choices=["batch", "hermitian", "dense"],
+                    help="batch: the 4096-matrix exp batch (default); hermitian: exp(-iH)V, "
+                         "d = 4096, V 4096 x 256, N = 206 steps; dense: exp(A), one real "
+                         "matrix of order --dim (both on the grid path)")
+    ap.add_argument("--dim", type=int, default=2048)
     args = ap.parse_args()
+    if args.workload != "batch":
+        return run_single(args)
     if args.batch != BATCH or args.dims:
         BATCH = args.batch
         if args.dims:

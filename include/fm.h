@@ -269,6 +269,20 @@ fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A, int lda, 
 /* Message for the calling thread's last failing call ("" if none). */
 const char* fm_last_error(void);
 
+/* Work done by the calling thread's last call on the grid path (zeros after a
+ * call on the one-CTA path): matrix products, their algorithmic flops (2MNK
+ * real, 8MNK complex), the tensor-core flops of their digit products (28
+ * digit-pair products per product flop; 0 on the FP64 pipe), and the largest
+ * number of correction steps one shifted system took.  The library has no
+ * counterpart in the paper; it serves measurement. */
+typedef struct {
+  long long products;
+  double product_flops;
+  double digit_flops;
+  int corrections;
+} fm_stats;
+void fm_last_stats(fm_stats* out);
+
 /* Library version string. */
 const char* fm_version(void);
 

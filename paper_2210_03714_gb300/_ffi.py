@@ -36,6 +36,18 @@ class fm_opts(C.Structure):
                 ("path", C.c_int)]
 
 
+class fm_stats(C.Structure):
+    _fields_ = [("products", C.c_longlong), ("product_flops", C.c_double),
+                ("digit_flops", C.c_double), ("corrections", C.c_int)]
+
+
+def last_stats():
+    """fm_last_stats of the calling thread as a dict."""
+    s = fm_stats()
+    lib().fm_last_stats(C.byref(s))
+    return {k: getattr(s, k) for k, _ in fm_stats._fields_}
+
+
 class FmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("fm status %d: %s" % (status, msg))
@@ -85,6 +97,7 @@ _SIGS = {
     "fm_expm_noalloc": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, _P, C.c_int, C.c_double, _P,
                                   C.c_int, C.POINTER(fm_opts), _P, c_ip, c_ip]),
     "fm_last_error": (C.c_char_p, []),
+    "fm_last_stats": (None, [C.c_void_p]),
     "fm_version": (C.c_char_p, []),
 }
 

@@ -19,6 +19,7 @@ using namespace fmk;
 namespace {
 
 thread_local char g_err[512] = "";
+thread_local fm_stats g_stats;
 
 fm_status fail(fm_status s, const char* msg) {
   snprintf(g_err, sizeof g_err, "%s", msg);
@@ -264,6 +265,7 @@ fm_status run_grid(const Call& c, const fm_opts& o, cudaStream_t st) {
   g.info_host = c.info_host;
   g.s_host = c.s_host;
   g.n_host = c.n_host;
+  g.stats = &g_stats;
   g.ws_bytes = grid_ws_bytes(c.kind, c.cplx, o.precision, n, c.m);
   s = get_scratch(g.ws_bytes, &o, &g.ws, st);
   if (s) return s;
@@ -271,6 +273,7 @@ fm_status run_grid(const Call& c, const fm_opts& o, cudaStream_t st) {
 }
 
 fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
+  memset(&g_stats, 0, sizeof g_stats);
   fm_opts o = resolve_opts(optsp);
   fm_status s = check_opts(o);
   if (s) return s;
@@ -651,6 +654,10 @@ fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, con
 }
 
 const char* fm_last_error(void) { return g_err; }
+
+void fm_last_stats(fm_stats* out) {
+  if (out) *out = g_stats;
+}
 
 const char* fm_version(void) { return "fm 0.1 (sm_103a)"; }
 

@@ -64,9 +64,9 @@ Layout layout(int kind, bool cplx, int precision, int d, int m) {
   L.ex = take((size_t)Mp * 4);
   L.fy = take((size_t)Np * 4);
   if (precision != 0) {
-    const int kc = (d + oz::KC - 1) / oz::KC;
-    L.pxs = (size_t)(Mp / oz::TM) * kc * oz::XSTAGE;
-    L.pys = (size_t)(Np / oz::TN) * kc * oz::YSTAGE;
+    const int kc = (d + grid::GKC - 1) / grid::GKC;
+    L.pxs = (size_t)(Mp / oz::TM) * kc * grid::GXST;
+    L.pys = (size_t)(Np / oz::TN) * kc * grid::GYST;
     L.px = take(L.pxs * (cplx ? 2 : 1));
     L.py = take(L.pys * (cplx ? 3 : 1));
     L.acc = take((size_t)(cplx ? 2 : 1) * Mp * Np * 16);
@@ -116,6 +116,7 @@ class Runner {
   unsigned char *px_ = nullptr, *py_ = nullptr;
   long long* acc_ = nullptr;
   cudaError_t err_ = cudaSuccess;
+  fm_stats* stats_ = nullptr;
 
   int blocks(size_t count) const {
     size_t b = (count + kThreads - 1) / kThreads;
@@ -157,6 +158,12 @@ class Runner {
   void prod(int M, int N, int K, const T* X, int ldx, bool split_x, const T* Yp, int ldy,
             const grid::Epi& e, T* out, int ldo) {
     if (err_ != cudaSuccess) return;
+    if (stats_) {
+      const double f = (grid::El<T>::parts == 2 ? 8.0 : 2.0) * M * (double)N * K;
+      stats_->products += 1;
+      stats_->product_flops += f;
+      if (tcp_) stats_->digit_flops += 28.0 * f;
+    }
     if (!tcp_) {
       const int tiles = ((M + GT - 1) / GT) * ((N + GT - 1) / GT);
       grid::dgemm_tiles<T><<<tiles, NT, 0, st_>>>(M, N, K, X, ldx, Yp, ldy, Tm_, N);
@@ -167,16 +174,16 @@ class Runner {
       return;
     }
     const int parts = grid::El<T>::parts;
-    const int kc = (K + oz::KC - 1) / oz::KC;
+    const int kc = (K + grid::GKC - 1) / grid::GKC;
     const int mtn = (M + oz::TM - 1) / oz::TM, ntn = (N + oz::TN - 1) / oz::TN;
     const int Mp = mtn * oz::TM, Np = ntn * oz::TN;
     // plane-set strides for this K (the buffers are sized for K = d)
-    const size_t pxs = (size_t)mtn * kc * oz::XSTAGE, pys = (size_t)ntn * kc * oz::YSTAGE;
+    const size_t pxs = (size_t)mtn * kc * grid::GXST, pys = (size_t)ntn * kc * grid::GYST;
     if (split_x) {
       memset0(rmax_, (size_t)M * 8, "row maxima reset");
       grid::row_max<T><<<blocks((size_t)M * 32), kThreads, 0, st_>>>(M, K, X, ldx, rmax_);
       check("row maxima");
-      const size_t items = (size_t)Mp * kc * (oz::KC / 8);
+      const size_t items = (size_t)Mp * kc * (grid::GKC / 8);
       grid::split_rows<T><<<blocks(items), kThreads, 0, st_>>>(M, K, X, ldx, rmax_, px_, pxs, kc, ex_);
       check("row digit planes");
     }
@@ -190,7 +197,7 @@ class Runner {
       check("column maxima");
     }
     {
-      const size_t items = (size_t)Np * kc * (oz::KC / 8);
+      const size_t items = (size_t)Np * kc * (grid::GKC / 8);
       grid::split_cols<T><<<blocks(items), kThreads, 0, st_>>>(K, N, Yp, ldy, cmax_, py_, pys, kc, fy_);
       check("column digit planes");
     }
@@ -217,14 +224,24 @@ class Runner {
       a.sx[1][1] = 1; a.sy[1][1] = 0;
     }
     const int tiles = parts * mtn * ntn;
-    const int groups = (a.nseg * kc + oz::FLUSH - 1) / oz::FLUSH;
-    int ksplit = (2 * sms_ + tiles - 1) / tiles;
-    if (ksplit > groups) ksplit = groups;
-    if (ksplit < 1) ksplit = 1;
+    const int groups = (a.nseg * kc + grid::GSTEPS - 1) / grid::GSTEPS;
+    // split K so the CTAs fill whole waves: estimated time = waves x (groups
+    // per CTA + about 1.5 groups of fixed cost per CTA)
+    int ksplit = 1;
+    double best = 1e300;
+    for (int ks = 1; ks <= groups && ks <= 32; ++ks) {
+      const long long ctas = (long long)tiles * ks;
+      const double waves = (double)((ctas + sms_ - 1) / sms_);
+      const double est = waves * ((double)((groups + ks - 1) / ks) + 1.5);
+      if (est < best - 1e-9) {
+        best = est;
+        ksplit = ks;
+      }
+    }
     a.ksplit = ksplit;
     a.acc = acc_;
     a.err = &misc_->tc_err;
-    grid::oz_tiles<<<tiles * ksplit, NT, oz::SMEM + 1024, st_>>>(a);
+    grid::oz_tiles<<<tiles * ksplit, grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
     check("tensor-core product");
     grid::epilogue<T><<<blocks((size_t)M * N), kThreads, 0, st_>>>(
         M, N, acc_, parts, Mp, Np, ex_, fy_, nullptr, 0, e, out, ldo);
@@ -246,6 +263,8 @@ int Runner<T>::run() {
   const GridJob& g = g_;
   st_ = g.st;
   n_ = g.d;
+  stats_ = (fm_stats*)g.stats;
+  if (stats_) memset(stats_, 0, sizeof *stats_);
   sms_ = sms_of_device();
   tcp_ = g.precision != 0;
   const int n = n_;
@@ -276,7 +295,7 @@ int Runner<T>::run() {
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
       cudaError_t e = cudaFuncSetAttribute(grid::oz_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           oz::SMEM + 1024);
+                                           grid::GSMEM + 1024);
       if (e != cudaSuccess) {
         snprintf(msg_, len_, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         return FM_ECUDA;
@@ -393,6 +412,7 @@ int Runner<T>::run() {
         break;
       }
       prev = em;
+      if (stats_ && it + 1 > stats_->corrections) stats_->corrections = it + 1;
       // Y = Y E + Y + E  (= Y + (I + Y) E)
       grid::Epi e2;
       e2.Z1 = Y_;

@@ -36,6 +36,7 @@ struct GridJob {
   int* info_host;
   int* s_host;
   long* n_host;
+  void* stats;  // fm_stats of the calling thread (written during the call)
 };
 
 // scratch bytes the grid path needs

@@ -251,12 +251,26 @@ __global__ void __launch_bounds__(NT, 2) dgemm_tiles(int M, int N, int K, const 
 }
 
 // ---- products on the tensor cores ------------------------------------------
-// Digit planes in global memory, in the layout of ozaki.cuh: for plane set s,
-// row tile mt (128 rows) and K chunk c (32 values), XSTAGE bytes at
-//   px + s * pxs + (mt * kc + c) * XSTAGE
-// (7 planes of 128 x 32 BF16 in 8 x 16-byte core matrices), likewise Y with
-// column tiles of 64.  A complex operand has sets (re, im) for X and
-// (re, im, -im) for Y, all sharing one exponent per row (column).
+// Digit planes in global memory: for plane set s, row tile mt (128 rows) and
+// K chunk c (16 values), GXST bytes at  px + s * pxs + (mt * kc + c) * GXST
+// (7 planes of 128 x 16 BF16 in 8 x 16-byte core matrices, K-major), likewise
+// Y with column tiles of 64 (GYST bytes).  A complex operand has sets (re, im)
+// for X and (re, im, -im) for Y, all sharing one exponent per row (column).
+constexpr int GKC = 16;                          // K per stage: one MMA K-step
+constexpr int GSTEPS = 7;                        // stages per exact group: K = 112
+constexpr int GNST = 4;                          // stages in the ring
+constexpr int GNACC = 7;                         // accumulators: levels 2..8
+constexpr uint32_t GXB = oz::TM * GKC * 2;       // one X plane of a stage (4 KB)
+constexpr uint32_t GYB = oz::TN * GKC * 2;       // one Y plane (2 KB)
+constexpr uint32_t GXST = oz::S * GXB;           // 28672
+constexpr uint32_t GYST = oz::S * GYB;           // 14336
+constexpr uint32_t GST = GXST + GYST;            // 43008
+constexpr uint32_t GSMEM = GNST * GST;           // 172032
+constexpr int GTHREADS = NT + 32;                // 8 readout warps + 1 producer / MMA warp
+
+__device__ __forceinline__ uint32_t plane_off16(int r, int k) {
+  return (uint32_t)(((r >> 3) * (GKC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
 
 // largest |re|, |im| of every row of X (bits, dst zeroed by the caller)
 template <class T>
@@ -304,11 +318,11 @@ template <class T>
 __global__ void split_rows(int M, int K, const T* X, int ldx, const unsigned long long* rmax,
                            unsigned char* px, size_t pxs, int kc, int* ex) {
   const int mtn = (M + oz::TM - 1) / oz::TM;
-  const long long items = (long long)mtn * oz::TM * kc * (oz::KC / 8);
+  const long long items = (long long)mtn * oz::TM * kc * (GKC / 8);
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
        it += (long long)gridDim.x * blockDim.x) {
-    const int k8 = (int)(it % (kc * (oz::KC / 8)));
-    const int r = (int)(it / (kc * (oz::KC / 8)));
+    const int k8 = (int)(it % (kc * (GKC / 8)));
+    const int r = (int)(it / (kc * (GKC / 8)));
     const int e = r < M ? exp_of_bits(rmax[r]) : 0;
     if (k8 == 0) ex[r] = e;
     __align__(16) __nv_bfloat16 dr[oz::S][8], di[oz::S][8];
@@ -326,15 +340,15 @@ __global__ void split_rows(int M, int K, const T* X, int ldx, const unsigned lon
         for (int p = 0; p < oz::S; ++p) di[p][j] = t[p];
       }
     }
-    const int tile = r / oz::TM, chunk = (k8 * 8) / oz::KC;
-    const size_t blk = ((size_t)tile * kc + chunk) * oz::XSTAGE;
-    const uint32_t off = oz::plane_off(r % oz::TM, (k8 * 8) % oz::KC);
+    const int tile = r / oz::TM, chunk = (k8 * 8) / GKC;
+    const size_t blk = ((size_t)tile * kc + chunk) * GXST;
+    const uint32_t off = plane_off16(r % oz::TM, (k8 * 8) % GKC);
 #pragma unroll
-    for (int p = 0; p < oz::S; ++p) *(uint4*)(px + blk + p * oz::XBLK + off) = *(const uint4*)dr[p];
+    for (int p = 0; p < oz::S; ++p) *(uint4*)(px + blk + p * GXB + off) = *(const uint4*)dr[p];
     if (El<T>::parts == 2) {
 #pragma unroll
       for (int p = 0; p < oz::S; ++p)
-        *(uint4*)(px + pxs + blk + p * oz::XBLK + off) = *(const uint4*)di[p];
+        *(uint4*)(px + pxs + blk + p * GXB + off) = *(const uint4*)di[p];
     }
   }
 }
@@ -344,7 +358,7 @@ template <class T>
 __global__ void split_cols(int K, int N, const T* Y, int ldy, const unsigned long long* cmax,
                            unsigned char* py, size_t pys, int kc, int* fy) {
   const int ntn = (N + oz::TN - 1) / oz::TN;
-  const long long items = (long long)ntn * oz::TN * kc * (oz::KC / 8);
+  const long long items = (long long)ntn * oz::TN * kc * (GKC / 8);
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
        it += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(it % (ntn * oz::TN));
@@ -369,25 +383,41 @@ __global__ void split_cols(int K, int N, const T* Y, int ldy, const unsigned lon
         }
       }
     }
-    const int tile = j / oz::TN, chunk = (k8 * 8) / oz::KC;
-    const size_t blk = ((size_t)tile * kc + chunk) * oz::YSTAGE;
-    const uint32_t off = oz::plane_off(j % oz::TN, (k8 * 8) % oz::KC);
+    const int tile = j / oz::TN, chunk = (k8 * 8) / GKC;
+    const size_t blk = ((size_t)tile * kc + chunk) * GYST;
+    const uint32_t off = plane_off16(j % oz::TN, (k8 * 8) % GKC);
 #pragma unroll
-    for (int p = 0; p < oz::S; ++p) *(uint4*)(py + blk + p * oz::YBLK + off) = *(const uint4*)dr[p];
+    for (int p = 0; p < oz::S; ++p) *(uint4*)(py + blk + p * GYB + off) = *(const uint4*)dr[p];
     if (El<T>::parts == 2) {
 #pragma unroll
       for (int p = 0; p < oz::S; ++p) {
-        *(uint4*)(py + pys + blk + p * oz::YBLK + off) = *(const uint4*)di[p];
-        *(uint4*)(py + 2 * pys + blk + p * oz::YBLK + off) = *(const uint4*)dn[p];
+        *(uint4*)(py + pys + blk + p * GYB + off) = *(const uint4*)di[p];
+        *(uint4*)(py + 2 * pys + blk + p * GYB + off) = *(const uint4*)dn[p];
       }
     }
   }
 }
 
 // One work item per CTA: output tile (mt, nt) of part `part` over a range of
-// exact accumulation groups (128 values of the concatenated K).  The part's
-// K runs over nseg segments, segment g pairing X plane set sx[part][g] with Y
-// plane set sy[part][g] (complex: re = Xr Yr + Xi (-Yi), im = Xr Yi + Xi Yr).
+// exact groups (112 values of the concatenated K).  The part's K runs over
+// nseg segments, segment g pairing X plane set sx[part][g] with Y plane set
+// sy[part][g] (complex: re = Xr Yr + Xi (-Yi), im = Xr Yi + Xi Yr).
+//
+// Accumulator a (TMEM columns 64a .. 64a + 63) holds level L = a + 2 (digit
+// pairs p + q = L).  Bounds at K = 112 in units of the level (|d_1| <= 256,
+// |d_p| <= 128 for p > 1): L = 2: 2^23, 3: 2^23, 4: 1.25 2^23, 5: 1.5 2^23,
+// 6: 1.75 2^23, 7: 1.75 2^23, 8: 1.97 2^23 -- every partial sum is an integer
+// below 2^24 units, exact in FP32 whatever the adder's rounding.  For digit p
+// of X, the Y planes q = 1 .. 8 - p are adjacent in shared memory and their
+// accumulators adjacent in TMEM, so one MMA of N = 64 (8 - p) (split at 256)
+// covers them: 10 MMAs per K step.
+//
+// Warps 0-7 read the accumulators after each group (warp w: TMEM lanes
+// 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31 of every accumulator) into
+// two exact 64-bit sums per output; warp 8 lane 0 keeps a ring of 4 stages
+// filled by bulk copies and issues the MMAs.  mbarriers: full[s] (copies
+// landed), empty[s] (the stage's MMAs finished), accf (a group's MMAs
+// finished), accr (the 8 readout warps released the accumulators).
 struct OzTiles {
   const unsigned char* px;
   const unsigned char* py;
@@ -400,9 +430,9 @@ struct OzTiles {
   int* err;
 };
 
-__global__ void __launch_bounds__(NT, 1) oz_tiles(OzTiles a) {
+__global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
   extern __shared__ unsigned char dsm[];
-  __shared__ __align__(8) uint64_t bar[4];
+  __shared__ __align__(8) uint64_t full[GNST], empty[GNST], accf, accr;
   __shared__ uint32_t tslot;
   __shared__ int s_err;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -415,13 +445,19 @@ __global__ void __launch_bounds__(NT, 1) oz_tiles(OzTiles a) {
   const int mt = item % a.mtn;
   const int part = item / a.mtn;
   const int nch = a.nseg * a.kc;
-  const int groups = (nch + oz::FLUSH - 1) / oz::FLUSH;
+  const int groups = (nch + GSTEPS - 1) / GSTEPS;
   const int gpb = (groups + a.ksplit - 1) / a.ksplit;
   const int g0 = ks * gpb, g1 = min(groups, g0 + gpb);
   if (g0 >= g1) return;  // the whole CTA leaves before any barrier or allocation
+  const int c0 = g0 * GSTEPS, c1 = min(nch, g1 * GSTEPS);
 
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) tc::mbar_init(&bar[i], 1);
+    for (int i = 0; i < GNST; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(&accf, 1);
+    tc::mbar_init(&accr, NT / 32);
     tc::mbar_fence_init();
     s_err = 0;
   }
@@ -430,110 +466,132 @@ __global__ void __launch_bounds__(NT, 1) oz_tiles(OzTiles a) {
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tslot;
-  uint32_t use0 = 0, use1 = 0;  // fills of each stage (thread 0)
-  auto use = [&](int s) -> uint32_t { return s ? use1 : use0; };
-  auto load = [&](int s, int ch) {
-    const int seg = ch / a.kc, c = ch % a.kc;
-    const unsigned char* xs =
-        a.px + (size_t)a.sx[part][seg] * a.pxs + ((size_t)mt * a.kc + c) * oz::XSTAGE;
-    const unsigned char* ys =
-        a.py + (size_t)a.sy[part][seg] * a.pys + ((size_t)nt * a.kc + c) * oz::YSTAGE;
-    unsigned char* dst = smem + s * oz::STAGE;
-    tc::mbar_arrive_expect_tx(&bar[s], oz::STAGE);
-    tc::bulk_g2s(dst, xs, oz::XSTAGE, &bar[s]);
-    tc::bulk_g2s(dst + oz::XSTAGE, ys, oz::YSTAGE, &bar[s]);
-    if (s) ++use1; else ++use0;
-  };
-  auto mma = [&](int s, bool first) {
-    const uint32_t sx = tc::saddr(smem + s * oz::STAGE);
-    const uint32_t sy = sx + oz::XSTAGE;
-    constexpr uint32_t idesc = tc::idesc_bf16(oz::TM, oz::TN);
-    bool fresh[oz::NACC];
-#pragma unroll
-    for (int q = 0; q < oz::NACC; ++q) fresh[q] = first;
-#pragma unroll
-    for (int p = 1; p <= oz::S; ++p)
-#pragma unroll
-      for (int q = 1; q <= oz::S; ++q) {
-        if (p + q > 8) continue;
-        const int ac = oz::acc_of(p, q);
-#pragma unroll
-        for (int k16 = 0; k16 < oz::KC / 16; ++k16) {
-          const uint64_t ad = tc::sdesc(sx + (p - 1) * oz::XBLK + k16 * 256, 128, (oz::KC / 8) * 128);
-          const uint64_t bd = tc::sdesc(sy + (q - 1) * oz::YBLK + k16 * 256, 128, (oz::KC / 8) * 128);
-          tc::mma_bf16(tmem + ac * oz::TN, ad, bd, idesc, fresh[ac] ? 0u : 1u);
-          fresh[ac] = false;
-        }
-      }
-  };
 
-  long long ahi[32], alo[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) ahi[j] = alo[j] = 0;
-  const int colh = 32 * (warp >> 2);
-  for (int g = g0; g < g1; ++g) {
-    const int c0 = g * oz::FLUSH, c1 = min(nch, c0 + oz::FLUSH);
-    if (tid == 0 && !s_err) {
-      // chunk ch uses stage ch & 1; the first chunk of a group is loaded here,
-      // the next one while the MMAs of the current chunk run
-      for (int ch = c0; ch < c1; ++ch) {
-        const int s = ch & 1;
-        if (ch == c0) load(s, ch);
-        if (!tc::mbar_wait(&bar[s], (use(s) - 1) & 1, oz::WAIT)) { s_err = 1; break; }
+  if (warp == NT / 32) {
+    // ---- producer and MMA issuer (one thread) ----
+    if (lane == 0) {
+      int err = 0;
+      int issued = c0;          // next chunk to load
+      int mma_chunks = 0;       // chunks whose MMAs were issued
+      auto load = [&](int ch) {
+        const int s = (ch - c0) % GNST;
+        const int seg = ch / a.kc, c = ch % a.kc;
+        const unsigned char* xs =
+            a.px + (size_t)a.sx[part][seg] * a.pxs + ((size_t)mt * a.kc + c) * GXST;
+        const unsigned char* ys =
+            a.py + (size_t)a.sy[part][seg] * a.pys + ((size_t)nt * a.kc + c) * GYST;
+        unsigned char* dst = smem + s * GST;
+        tc::mbar_arrive_expect_tx(&full[s], GST);
+        tc::bulk_g2s(dst, xs, GXST, &full[s]);
+        tc::bulk_g2s(dst + GXST, ys, GYST, &full[s]);
+      };
+      constexpr uint32_t LBO = 128, SBO = (GKC / 8) * 128;
+      for (int ch = c0; ch < c1 && !err; ++ch) {
+        // keep up to GNST chunks in flight: a stage is refilled once the MMAs
+        // of the chunk that used it (GNST chunks back) have finished
+        while (issued < c1 && issued < ch + GNST) {
+          const int k = issued - c0;
+          if (k >= GNST && !tc::mbar_wait(&empty[k % GNST], ((k / GNST) - 1) & 1, oz::WAIT)) {
+            err = 1;
+            break;
+          }
+          load(issued);
+          ++issued;
+        }
+        if (err) break;
+        const int k = ch - c0, s = k % GNST;
+        const int gi = (ch / GSTEPS) - g0;  // group index within this CTA
+        const bool first = (ch % GSTEPS) == 0 || ch == c0;
+        if (first && gi > 0 && !tc::mbar_wait(&accr, (gi - 1) & 1, oz::WAIT)) {
+          err = 1;
+          break;
+        }
+        if (!tc::mbar_wait(&full[s], (k / GNST) & 1, oz::WAIT)) {
+          err = 1;
+          break;
+        }
         tc::fence_after();
-        mma(s, ch == c0);
-        tc::mma_commit(&bar[2 + s]);
-        if (ch + 1 < c1) {
-          const int s2 = (ch + 1) & 1;
-          if (ch > c0 && !tc::mbar_wait(&bar[2 + s2], (use(s2) - 1) & 1, oz::WAIT)) { s_err = 1; break; }
-          load(s2, ch + 1);
+        const uint32_t sx = tc::saddr(smem + s * GST);
+        const uint32_t sy = sx + GXST;
+#pragma unroll
+        for (int p = 1; p <= oz::S; ++p) {
+          const uint64_t ad = tc::sdesc(sx + (p - 1) * GXB, LBO, SBO);
+#pragma unroll
+          for (int q0 = 1; q0 <= 8 - p; q0 += 4) {
+            const int nq = min(4, 8 - p - q0 + 1);
+            const uint64_t bd = tc::sdesc(sy + (q0 - 1) * GYB, LBO, SBO);
+            const uint32_t id = tc::idesc_bf16(oz::TM, oz::TN * nq);
+            // the first K step of a group starts every accumulator (p = 1 covers all 7)
+            tc::mma_bf16(tmem + (p + q0 - 2) * oz::TN, ad, bd, id, (first && p == 1) ? 0u : 1u);
+          }
         }
+        tc::mma_commit(&empty[s]);
+        ++mma_chunks;
+        const bool last = ((ch + 1) % GSTEPS) == 0 || ch + 1 == c1;
+        if (last) tc::mma_commit(&accf);
       }
-      const int sl = (c1 - 1) & 1;
-      if (!s_err && !tc::mbar_wait(&bar[2 + sl], (use(sl) - 1) & 1, oz::WAIT)) s_err = 1;
-      if (!s_err && c1 - c0 > 1 && !tc::mbar_wait(&bar[2 + (sl ^ 1)], (use(sl ^ 1) - 1) & 1, oz::WAIT))
+      if (err) {
         s_err = 1;
+        atomicOr(a.err, 1);
+      }
+      // drain before TMEM is freed: the copies still landing, and the last
+      // commit (it covers every MMA issued before it)
+      const int nl = issued - c0, nm = mma_chunks;
+      for (int k = max(0, nl - GNST); k < nl; ++k)
+        tc::mbar_wait(&full[k % GNST], (k / GNST) & 1, oz::WAIT);
+      if (nm > 0) tc::mbar_wait(&empty[(nm - 1) % GNST], ((nm - 1) / GNST) & 1, oz::WAIT);
     }
-    __syncthreads();
-    tc::fence_after();
-    if (!s_err) {
-#pragma unroll 1
-      for (int q = 0; q < oz::NACC; ++q) {
-        uint32_t r[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + q * oz::TN + colh, r);
-        tc::tmem_ld_wait();
-        const int L = q < 6 ? q + 2 : 8;
-        if (q < 4) {
+  } else {
+    // ---- readout warps ----
+    long long ahi[32], alo[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) ahi[j] += (long long)oz::exact_int(r[j], 8 * L) << (40 - 8 * L);
-        } else {
+    for (int j = 0; j < 32; ++j) ahi[j] = alo[j] = 0;
+    const int colh = 32 * (warp >> 2);
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    bool ok = true;
+    for (int g = g0; g < g1; ++g) {
+      const int gi = g - g0;
+      if (!tc::mbar_wait(&accf, gi & 1, oz::WAIT)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) alo[j] += (long long)oz::exact_int(r[j], 8 * L) << (64 - 8 * L);
+      for (int q = 0; q < GNACC; ++q) {
+        // level L = q + 2: value = k 2^-8L exactly with |k| < 2^24; k by the
+        // FP32 -> int32 conversion (the 64-bit one runs on the FP64 unit)
+        const int L = q + 2;
+        const float sc = __int_as_float((127 + 8 * L) << 23);  // 2^(8L)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t r[16];
+          tc::tmem_ld16(tmem + lane_base + q * oz::TN + colh + 16 * h, r);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long k = __float2int_rz(__uint_as_float(r[j]) * sc);
+            if (q < 4) ahi[16 * h + j] += k << (40 - 8 * L);   // 2^-40 units
+            else alo[16 * h + j] += k << (64 - 8 * L);         // 2^-64 units
+          }
         }
       }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&accr);
     }
-    tc::fence_before();
-    __syncthreads();
-  }
-  if (!s_err) {
-    const int Mp = a.mtn * oz::TM, Np = a.ntn * oz::TN;
-    const int row = mt * oz::TM + 32 * (warp & 3) + lane;
-    unsigned long long* dst =
-        (unsigned long long*)a.acc + (((size_t)part * Mp + row) * Np + nt * oz::TN + colh) * 2;
+    if (ok && !s_err) {
+      const int Mp = a.mtn * oz::TM, Np = a.ntn * oz::TN;
+      const int row = mt * oz::TM + 32 * (warp & 3) + lane;
+      unsigned long long* dst =
+          (unsigned long long*)a.acc + (((size_t)part * Mp + row) * Np + nt * oz::TN + colh) * 2;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (ahi[j]) atomicAdd(dst + 2 * j, (unsigned long long)ahi[j]);
-      if (alo[j]) atomicAdd(dst + 2 * j + 1, (unsigned long long)alo[j]);
-    }
-  }
-  if (tid == 0 && s_err) {
-    atomicOr(a.err, 1);
-    // let copies and MMAs still in flight finish before the memory is freed
-    for (int s = 0; s < 2; ++s)
-      if (use(s)) {
-        tc::mbar_wait(&bar[s], (use(s) - 1) & 1, oz::WAIT);
-        tc::mbar_wait(&bar[2 + s], (use(s) - 1) & 1, oz::WAIT);
+      for (int j = 0; j < 32; ++j) {
+        if (ahi[j]) atomicAdd(dst + 2 * j, (unsigned long long)ahi[j]);
+        if (alo[j]) atomicAdd(dst + 2 * j + 1, (unsigned long long)alo[j]);
       }
+    } else if (!ok && lane == 0) {
+      atomicOr(a.err, 1);
+    }
   }
   tc::fence_before();
   __syncthreads();

@@ -113,17 +113,6 @@ __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out) {
   }
 }
 
-// exact integer k with v = k 2^-q for an FP32 value v known to be such a
-// multiple with |k| < 2^31 (integer bit manipulation, no conversion unit)
-__device__ __forceinline__ int exact_int(uint32_t b, int q) {
-  if ((b & 0x7FFFFFFFu) == 0) return 0;
-  const int E = (int)((b >> 23) & 0xFF);
-  const int mant = (int)((b & 0x7FFFFFu) | 0x800000u);
-  const int sh = E - 150 + q;
-  const int k = sh >= 0 ? (mant << sh) : (mant >> (-sh));
-  return (b >> 31) ? -k : k;
-}
-
 // round-to-nearest double of (hi 2^24 + lo) 2^e2, hi and lo exact integers
 __device__ __forceinline__ double combine_scaled(long long hi, long long lo, int e2) {
   __int128 v = ((__int128)hi << 24) + (__int128)lo;
@@ -349,14 +338,16 @@ static __device__ __noinline__ int gemm(Ctx& c, int M, int N, int K, const doubl
             // accumulator a holds an exact multiple of 2^-8L (L = a + 2, level 8
             // for a = 6, 7): its integer, shifted to the unit of its sum
             const int L = a < 6 ? a + 2 : 8;
+            // k = value 2^(8L), |k| < 2^24, by the FP32 -> int32 conversion
+            const float sc = __int_as_float((127 + 8 * L) << 23);
             if (a < 4) {
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                ahi[j] += (long long)exact_int(r[j], 8 * L) << (40 - 8 * L);  // 2^-40 units
+                ahi[j] += (long long)__float2int_rz(__uint_as_float(r[j]) * sc) << (40 - 8 * L);
             } else {
 #pragma unroll
               for (int j = 0; j < 32; ++j)
-                alo[j] += (long long)exact_int(r[j], 8 * L) << (64 - 8 * L);  // 2^-64 units
+                alo[j] += (long long)__float2int_rz(__uint_as_float(r[j]) * sc) << (64 - 8 * L);
             }
           }
         }
