@@ -355,6 +355,9 @@ def main():
                          "d = 4096, V 4096 x 256, N = 206 steps; dense: exp(A), one real "
                          "matrix of order --dim (both on the grid path)")
     ap.add_argument("--dim", type=int, default=2048)
+    ap.add_argument("--path", default="auto", choices=["auto", "cta", "grid"],
+                    help="execution path of the mixed form for the batch (the double form "
+                         "always runs one CTA per matrix)")
     args = ap.parse_args()
     if args.workload != "batch":
         return run_single(args)
@@ -401,7 +404,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(prec, out):
-        return fm.expm_batched(P, t_dev, cs, precision=prec, out=out)
+        path = args.path if prec == "mixed" else "cta"
+        return fm.expm_batched(P, t_dev, cs, precision=prec, out=out, path=path)
 
     def timed(prec, out, steps, warmup):
         for _ in range(warmup):
@@ -423,6 +427,7 @@ def main():
     clocks.start()
     per, info, s = timed(args.precision, F, args.steps, args.warmup)
     clk = clocks.stop()
+    st = fm.last_stats()  # the last timed call
     ms = max_over_ranks(sum(per) / len(per))
     bad = int((info != 0).sum().item())
     s_host = s.cpu().numpy()
@@ -448,26 +453,52 @@ def main():
         e2e = run_e2e(args, fm, torch, flat, dims, cs, stream, barrier, max_over_ranks, world,
                       dev)
 
-    # roofline of the dominant kernel (the persistent per-matrix kernel: every
-    # launch but the microsecond ordering kernel), from the per-step event time
+    # roofline.  Grid path (the automatic choice for this batch): every product
+    # of the step is tensor-core digit work, counted by the library
+    # (fm_last_stats); the rate is taken over the whole step, so it bounds the
+    # tile kernel's own rate from below.  One-CTA path: the per-pipe model of
+    # the persistent kernel.
     peaks = load_peaks()
     achieved = method_flops(dims, s_host) / (ms / 1000.0) / 1e12
-    roofline = roofline_of(pipe_work(dims, s_host, args.precision), ms, peaks)
-    roofline["traffic"] = TRAFFIC.get(args.precision) if BATCH == 4096 and not args.dims else None
+    grid_path = st["products"] > 0
+    if grid_path:
+        pk = pipe_peaks(peaks)["tensor_bf16"]
+        ach = st["digit_flops"] / (ms / 1000.0) / 1e12
+        roofline = {"bound": "tensor", "pipe": "tensor_bf16", "achieved": ach, "peak": pk[0],
+                    "peak_source": pk[1], "unit": "TFLOP/s", "frac": ach / pk[0], "traffic": None,
+                    "flops_per_step": st["digit_flops"], "products_per_step": st["products"],
+                    "note": "digit-pair flops of every product in the step (28 per product "
+                            "flop) over the step's event time"}
+    else:
+        roofline = roofline_of(pipe_work(dims, s_host, args.precision), ms, peaks)
+        roofline["traffic"] = TRAFFIC.get(args.precision) if BATCH == 4096 and not args.dims else None
     fp64_roofline = (roofline_of(pipe_work(dims, s_host, "fp64"), fp64_ms, peaks)
                      if fp64_ms else None)
+    # the mixed form on the one-CTA path, for context
+    cta_value = None
+    if grid_path and not args.no_fp64:
+        Fc = torch.empty_like(P.flat)
+        old = args.path
+        args.path = "cta"
+        perc, _, _ = timed("mixed", Fc, max(1, min(args.steps, 2)), 1)
+        args.path = old
+        cta_value = world * BATCH / (max_over_ranks(sum(perc) / len(perc)) / 1000.0)
 
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "dtype": ("bf16 digits+f64" if grid_path else "f32+f64") if args.precision == "mixed"
+                     else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch": BATCH, "precision": args.precision,
                        "coeffs": "R8", "l2": "inputs (784 MB) larger than L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
-            "gpu_launches_note": "per step: the batch-ordering kernel and the persistent kernel",
+            "gpu_launches": (st["launches"] if grid_path else 2) * args.steps,
+            "gpu_launches_note": ("per step: the grid path's launches (splits, tile products, "
+                                  "epilogues, elementwise), as counted by the library"
+                                  if grid_path else
+                                  "per step: the batch-ordering kernel and the persistent kernel"),
             "status_nonzero": bad,
             "fp64_value": (world * BATCH / (fp64_ms / 1000.0)) if fp64_ms else None,
             "fp64_ms_per_step": fp64_ms,
@@ -475,6 +506,8 @@ def main():
             "max_rel_diff_vs_fp64": maxdiff,
             "method_tflops": achieved,
             "fp64_roofline": fp64_roofline,
+            "path": "grid" if grid_path else "cta",
+            "mixed_cta_path_value": cta_value,
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(dims, norms, args.cpu_sample, F, P)

@@ -113,19 +113,22 @@ enum { FM_FP64 = 0, FM_FP32_IR = 1 };   /* precision of the shifted solves      
 enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       */
 /* Execution path.  FM_PATH_CTA: one thread block per matrix, every step in it
  * (LU with partial pivoting of each shifted matrix; d <= fm_max_dim()).
- * FM_PATH_GRID (single-matrix calls only): the matrix is spread over every SM;
- * each shifted system (I - c_i B) Y_i = c_i B is solved by the residual-
- * correction (Newton-Schulz) iteration Y <- Y + (I + Y)(C - (I - C) Y),
- * C = c_i B, whose only heavy steps are matrix products, until the largest
- * residual entry times d is below 2^-30 (then one more correction); it needs
- * the spectral radius of c_i B well below 1, as every set here gives with
- * ||B||_1 <= theta (||c_i B||_1 <= 0.05).  Products run on the FP64 pipe
- * (FM_FP64) or as BF16 digit products on the tensor cores with exact
- * accumulation (FM_FP32_IR), both accurate to double.  The action forms the
- * matrix r(B) once and applies it N times.  The call synchronizes its stream
- * (s or N and the iteration counts are chosen on the host).
- * FM_PATH_AUTO: single-matrix calls with d > fm_max_dim() take the grid path,
- * everything else the one-CTA kernels. */
+ * FM_PATH_GRID: every step is one launch over the whole GPU -- one matrix of
+ * any order (single-matrix calls), or a whole batch of exp (batched exp,
+ * dmax <= fm_max_dim()); each shifted system (I - c_i B) Y_i = c_i B is solved
+ * by the residual-correction (Newton-Schulz) iteration
+ * Y <- Y + (I + Y)(C - (I - C) Y), C = c_i B, whose only heavy steps are matrix
+ * products, until the largest residual entry times d is below 2^-30 (then one
+ * more correction); it needs the spectral radius of c_i B well below 1, as
+ * every set here gives with ||B||_1 <= theta (||c_i B||_1 <= 0.05).  Products
+ * run on the FP64 pipe (FM_FP64) or as BF16 digit products on the tensor cores
+ * with exact accumulation (FM_FP32_IR), both accurate to double.  The action
+ * forms the matrix r(B) once and applies it N times.  Calls on this path
+ * synchronize their stream (s or N, the batch orders and the iteration counts
+ * are read on the host).
+ * FM_PATH_AUTO: single-matrix calls with d > fm_max_dim() and batched exp in
+ * FM_FP32_IR with dmax >= 64 take the grid path, everything else the one-CTA
+ * kernels. */
 enum { FM_PATH_AUTO = 0, FM_PATH_CTA = 1, FM_PATH_GRID = 2 };
 
 typedef struct {
@@ -273,13 +276,15 @@ const char* fm_last_error(void);
  * call on the one-CTA path): matrix products, their algorithmic flops (2MNK
  * real, 8MNK complex), the tensor-core flops of their digit products (28
  * digit-pair products per product flop; 0 on the FP64 pipe), and the largest
- * number of correction steps one shifted system took.  The library has no
+ * number of correction steps one shifted system took, and the number of kernel
+ * launches of the call.  The library has no
  * counterpart in the paper; it serves measurement. */
 typedef struct {
   long long products;
   double product_flops;
   double digit_flops;
   int corrections;
+  long long launches;  /* kernels the call launched */
 } fm_stats;
 void fm_last_stats(fm_stats* out);
 

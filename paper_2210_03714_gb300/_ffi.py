@@ -38,7 +38,8 @@ class fm_opts(C.Structure):
 
 class fm_stats(C.Structure):
     _fields_ = [("products", C.c_longlong), ("product_flops", C.c_double),
-                ("digit_flops", C.c_double), ("corrections", C.c_int)]
+                ("digit_flops", C.c_double), ("corrections", C.c_int),
+                ("launches", C.c_longlong)]
 
 
 def last_stats():

@@ -1,0 +1,384 @@
+// bgrid.cuh -- the grid path over a batch of matrices: one launch per step
+// for every matrix of the batch (one thread block per matrix for the
+// elementwise and split steps, one CTA per 128 x 64 output tile for the
+// tensor-core products), masked per matrix.
+//
+// Same method as the single-matrix grid path (fm_grid.cu): s from the norm
+// (Sec. 1, 3), each shifted system (I - C) Y = C, C = c_i B, solved by the
+// residual-correction iteration Y <- Y + (I + Y)(C - (I - C) Y) until the
+// largest residual entry times d falls below 2^-30 (then one more
+// correction), F = a0 I + sum_i b_i Y_i (Eq. ParallRoundOff), and s
+// squarings of F = I + E as E <- 2E + E E.
+#pragma once
+#include "grid.cuh"
+
+namespace fmk {
+namespace grid {
+
+template <class T>
+__device__ __forceinline__ double max_re_im(T v) {
+  return fmax(fabs(El<T>::re(v)), fabs(El<T>::im(v)));
+}
+
+// block-wide maximum with NaN propagation; red: 32 doubles of shared memory
+__device__ __forceinline__ double block_max(double m, double* red) {
+  for (int o = 16; o; o >>= 1) {
+    const double v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (v > m || isnan(v)) ? v : m;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double r = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = (red[w] > r || isnan(red[w])) ? red[w] : r;
+  return r;
+}
+
+// a1/a2, one block per matrix: B = t A (one rounding), eta = ||tA||_1 (column
+// sums, rows ascending, as the one-CTA kernels), s, B <- B / 2^s; info -2 for
+// a non-finite entry or t.  alive[b] = 1 unless info = -2.
+template <class T>
+__global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, double anorm,
+                           double theta, int s_fixed, int* s_out, int* info, int* alive) {
+  __shared__ double red[32];
+  const BMat M = mats[blockIdx.x];
+  const int n = M.d, tid = threadIdx.x;
+  const T* Ab = A + M.uoff;
+  T* Bb = B + M.off;
+  const double tb = t[blockIdx.x];
+  int bad = !isfinite(tb);
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const T a = Ab[e];
+    bad |= !Tr<T>::finite(a);
+    Bb[e] = Tr<T>::rscale(a, tb);
+  }
+  bad = __syncthreads_or(bad);
+  double cmax = 0;
+  for (int c = tid; c < n; c += blockDim.x) {
+    double sc = 0;
+    for (int r = 0; r < n; ++r) sc += Tr<T>::mag(Bb[(size_t)r * n + c]);
+    cmax = (sc > cmax || isnan(sc)) ? sc : cmax;
+  }
+  cmax = block_max(cmax, red);
+  const double eta = anorm > 0 ? anorm * fabs(tb) : cmax;
+  int s = s_fixed;
+  if (s < 0) {
+    s = 0;
+    while (eta > ldexp(theta, s) && s < 1023) ++s;
+  }
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const T v = Bb[e];
+    Bb[e] = El<T>::make(ldexp(El<T>::re(v), -s), ldexp(El<T>::im(v), -s));
+  }
+  if (tid == 0) {
+    if (s_out) s_out[blockIdx.x] = s;
+    info[blockIdx.x] = bad ? -2 : 0;
+    alive[blockIdx.x] = !bad;
+  }
+}
+
+// Elementwise and split kernels run on a grid (batch, parts): block (b, y)
+// takes the y-th slice of matrix b (BE elements, or RB rows, or CB columns);
+// slices past the end of a small matrix return at once.
+constexpr int BE = 4096;  // elements per block
+constexpr int RB = 32;    // rows per block (row planes, epilogue)
+constexpr int CB = 32;    // columns per block (column planes)
+
+#define FM_SLICE(M, count)                                       \
+  if (!mask[blockIdx.x]) return;                                 \
+  const BMat M = mats[blockIdx.x];                               \
+  const size_t e0 = (size_t)blockIdx.y * BE;                     \
+  if (e0 >= (count)) return;                                     \
+  const size_t e1 = e0 + BE < (count) ? e0 + BE : (count);
+
+// C = c B, Y = C
+template <class T>
+__global__ void b_build_shift(const BMat* mats, const int* mask, const T* B, double cr,
+                              double ci, T* C, T* Y) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const T v = cmul<T>(cr, ci, B[M.off + e]);
+    C[M.off + e] = v;
+    Y[M.off + e] = v;
+  }
+}
+
+// F = base I
+template <class T>
+__global__ void b_init_f(const BMat* mats, const int* mask, double base, T* F) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+  const int n = M.d;
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+    F[M.off + e] = Tr<T>::rscale((e / n == e % n) ? Tr<T>::one() : Tr<T>::zero(), base);
+}
+
+// F += d1 B + d2 B2 (B2 nullable when d2 == 0)
+template <class T>
+__global__ void b_hybrid(const BMat* mats, const int* mask, double d1, const T* B, double d2,
+                         const T* B2, T* F) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    T v = F[M.off + e];
+    if (d1 != 0) v = Tr<T>::add(v, Tr<T>::rscale(B[M.off + e], d1));
+    if (d2 != 0) v = Tr<T>::add(v, Tr<T>::rscale(B2[M.off + e], d2));
+    F[M.off + e] = v;
+  }
+}
+
+// F += b Y (roundoff form) or b (I + Y) (plain form)
+template <class T>
+__global__ void b_accumulate(const BMat* mats, const int* mask, double br, double bi, const T* Y,
+                             int plain, T* F) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+  const int n = M.d;
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    T y = Y[M.off + e];
+    if (plain && e / n == e % n) y = Tr<T>::add(y, Tr<T>::one());
+    F[M.off + e] = Tr<T>::add(F[M.off + e], cmul<T>(br, bi, y));
+  }
+}
+
+// out = in + g I; user_out: out uses the caller's offsets
+template <class T>
+__global__ void b_add_identity(const BMat* mats, const int* mask, const T* in, double g, T* out,
+                               int user_out) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+  const int n = M.d;
+  T* o = out + (user_out ? M.uoff : M.off);
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    T v = in[M.off + e];
+    if (e / n == e % n) v = Tr<T>::add(v, Tr<T>::rscale(Tr<T>::one(), g));
+    o[e] = v;
+  }
+}
+
+// Row digit planes of rows [RB y, RB y + RB) of X_b (d x d) and their exponents
+// ex[eo + r].  Only real rows and the 8-value groups holding real columns are
+// written; the rest of the planes stays zero from the reset at the start of
+// the call.
+template <class T>
+__global__ void b_split_rows(const BMat* mats, const int* mask, const T* X, unsigned char* px,
+                             int* ex) {
+  __shared__ int s_e[RB];
+  if (!mask[blockIdx.x]) return;
+  const BMat M = mats[blockIdx.x];
+  const int n = M.d, kc = M.kc;
+  const int r0 = blockIdx.y * RB;
+  if (r0 >= n) return;
+  const int nr = min(RB, n - r0);
+  const T* Xb = X + M.off;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int rr = w; rr < nr; rr += nw) {
+    const int r = r0 + rr;
+    double mx = 0;
+    for (int k = lane; k < n; k += 32) mx = fmax(mx, max_re_im(Xb[(size_t)r * n + k]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      s_e[rr] = oz::exp_above(mx);
+      ex[M.eo + r] = s_e[rr];
+    }
+  }
+  __syncthreads();
+  unsigned char* pb = px + M.px;
+  const size_t pxs = (size_t)M.mtn * kc * GXST;
+  const int g8 = (n + 7) / 8;  // 8-value groups holding real columns
+  const int items = nr * g8;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int k8 = it % g8;
+    const int rr = it / g8, r = r0 + rr;
+    const int e = s_e[rr];
+    __align__(16) __nv_bfloat16 dr[oz::S][8], di[oz::S][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k8 * 8 + j;
+      const T v = k < n ? Xb[(size_t)r * n + k] : El<T>::make(0.0, 0.0);
+      __nv_bfloat16 t[oz::S];
+      oz::digits(El<T>::re(v), e, t);
+#pragma unroll
+      for (int p = 0; p < oz::S; ++p) dr[p][j] = t[p];
+      if (El<T>::parts == 2) {
+        oz::digits(El<T>::im(v), e, t);
+#pragma unroll
+        for (int p = 0; p < oz::S; ++p) di[p][j] = t[p];
+      }
+    }
+    const size_t blk = ((size_t)(r / oz::TM) * kc + (k8 * 8) / GKC) * GXST;
+    const uint32_t off = plane_off16(r % oz::TM, (k8 * 8) % GKC);
+#pragma unroll
+    for (int p = 0; p < oz::S; ++p) *(uint4*)(pb + blk + p * GXB + off) = *(const uint4*)dr[p];
+    if (El<T>::parts == 2) {
+#pragma unroll
+      for (int p = 0; p < oz::S; ++p) *(uint4*)(pb + pxs + blk + p * GXB + off) = *(const uint4*)di[p];
+    }
+  }
+}
+
+// Column digit planes of columns [CB y, CB y + CB) of Y_b (N-major) and their
+// exponents fy[fo + j]; only real columns and real 8-value groups of rows.
+template <class T>
+__global__ void b_split_cols(const BMat* mats, const int* mask, const T* Y, unsigned char* py,
+                             int* fy) {
+  __shared__ double red[8][CB + 1];
+  __shared__ int s_f[CB];
+  if (!mask[blockIdx.x]) return;
+  const BMat M = mats[blockIdx.x];
+  const int n = M.d, kc = M.kc;
+  const int c0 = blockIdx.y * CB;
+  if (c0 >= n) return;
+  const int nc = min(CB, n - c0);
+  const T* Yb = Y + M.off;
+  {
+    const int cx = threadIdx.x % CB, ry = threadIdx.x / CB;  // 8 row lanes x 32 columns
+    double mx = 0;
+    if (cx < nc)
+      for (int k = ry; k < n; k += 8) mx = fmax(mx, max_re_im(Yb[(size_t)k * n + c0 + cx]));
+    red[ry][cx] = mx;
+    __syncthreads();
+    if (ry == 0) {
+      for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][cx]);
+      if (cx < nc) {
+        s_f[cx] = oz::exp_above(mx);
+        fy[M.fo + c0 + cx] = s_f[cx];
+      }
+    }
+    __syncthreads();
+  }
+  unsigned char* pb = py + M.py;
+  const size_t pys = (size_t)M.ntn * kc * GYST;
+  const int g8 = (n + 7) / 8;
+  const int items = nc * g8;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int jj = it % nc, j = c0 + jj;
+    const int k8 = it / nc;
+    const int e = s_f[jj];
+    __align__(16) __nv_bfloat16 dr[oz::S][8], di[oz::S][8], dn[oz::S][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k8 * 8 + q;
+      const T v = k < n ? Yb[(size_t)k * n + j] : El<T>::make(0.0, 0.0);
+      __nv_bfloat16 t[oz::S];
+      oz::digits(El<T>::re(v), e, t);
+#pragma unroll
+      for (int p = 0; p < oz::S; ++p) dr[p][q] = t[p];
+      if (El<T>::parts == 2) {
+        oz::digits(El<T>::im(v), e, t);
+#pragma unroll
+        for (int p = 0; p < oz::S; ++p) {
+          di[p][q] = t[p];
+          dn[p][q] = __hneg(t[p]);
+        }
+      }
+    }
+    const size_t blk = ((size_t)(j / oz::TN) * kc + (k8 * 8) / GKC) * GYST;
+    const uint32_t off = plane_off16(j % oz::TN, (k8 * 8) % GKC);
+#pragma unroll
+    for (int p = 0; p < oz::S; ++p) *(uint4*)(pb + blk + p * GYB + off) = *(const uint4*)dr[p];
+    if (El<T>::parts == 2) {
+#pragma unroll
+      for (int p = 0; p < oz::S; ++p) {
+        *(uint4*)(pb + pys + blk + p * GYB + off) = *(const uint4*)di[p];
+        *(uint4*)(pb + 2 * pys + blk + p * GYB + off) = *(const uint4*)dn[p];
+      }
+    }
+  }
+}
+
+// rows [RB y, RB y + RB) of out_b = alpha P_b + b1 Z1_b + b2 Z2_b + g I, P_b
+// from the exact sums; emax[b] (bits, zeroed by the caller, nullable) =
+// largest |re|, |im| of out_b
+template <class T>
+__global__ void b_epilogue(const BMat* mats, const int* mask, const long long* acc, const int* ex,
+                           const int* fy, Epi e, T* out, unsigned long long* emax, double* flops) {
+  if (!mask[blockIdx.x]) return;
+  const BMat M = mats[blockIdx.x];
+  const int n = M.d, parts = El<T>::parts;
+  const int r0 = blockIdx.y * RB;
+  if (r0 >= n) return;
+  const int nr = min(RB, n - r0);
+  if (flops && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(flops, (parts == 2 ? 8.0 : 2.0) * n * (double)n * n);
+  const int Mp = M.mtn * oz::TM, Np = M.ntn * oz::TN;
+  const long long* ab = acc + M.acc * 2;
+  const T* Z1 = (const T*)e.Z1;
+  const T* Z2 = (const T*)e.Z2;
+  const bool scale = e.ar != 1.0 || e.ai != 0;
+  unsigned long long mx = 0;
+  const int cnt = nr * n;
+#pragma unroll 2
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const int i = r0 + k / n, j = k % n;
+    const size_t el = (size_t)i * n + j;
+    const int e2 = ex[M.eo + i] + fy[M.fo + j] - 64;
+    const longlong2 a0 = *(const longlong2*)(ab + ((size_t)i * Np + j) * 2);
+    const double pr = oz::combine_scaled(a0.x, a0.y, e2);
+    double pi = 0;
+    if (parts == 2) {
+      const longlong2 a1 = *(const longlong2*)(ab + ((size_t)Mp * Np + (size_t)i * Np + j) * 2);
+      pi = oz::combine_scaled(a1.x, a1.y, e2);
+    }
+    T v = El<T>::make(pr, pi);
+    if (scale) v = cmul<T>(e.ar, e.ai, v);
+    if (Z1) v = axpy1<T>(v, e.b1r, e.b1i, Z1[M.off + el]);
+    if (Z2) v = axpy1<T>(v, e.b2r, e.b2i, Z2[M.off + el]);
+    if (i == j && (e.gr != 0 || e.gi != 0)) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
+    out[M.off + el] = v;
+    const unsigned long long bb = abs_bits<T>(v);
+    mx = bb > mx ? bb : mx;
+  }
+  if (emax) {
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = v > mx ? v : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(emax + blockIdx.x, mx);
+  }
+}
+
+// One correction step's decision per matrix (the single-matrix rule):
+// residual zero -> done; non-finite, too many steps or growing after 3 ->
+// info -1, done; otherwise correct, and stop after that when em d <= 2^-30.
+static __global__ void b_flags(int batch, const BMat* mats, const unsigned long long* emax, double* prev, int it,
+                        int max_iters, int* mask_e, int* mask_u, int* info, int* active,
+                        int* corrections) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  if (!mask_e[b]) {
+    mask_u[b] = 0;
+    return;
+  }
+  const double em = __longlong_as_double((long long)emax[b]);
+  if (em == 0.0) {
+    mask_e[b] = 0;
+    mask_u[b] = 0;
+  } else if (!(em < INFINITY) || it >= max_iters || (it >= 3 && em >= prev[b])) {
+    if (info[b] == 0) info[b] = -1;
+    mask_e[b] = 0;
+    mask_u[b] = 0;
+  } else {
+    prev[b] = em;
+    mask_u[b] = 1;
+    atomicMax(corrections, it + 1);
+    if (em * mats[b].d <= 9.313225746154785e-10 /* 2^-30 */) mask_e[b] = 0;
+  }
+  if (mask_e[b]) atomicAdd(active, 1);
+}
+
+// info[b] = code for every live matrix
+static __global__ void b_set_info(int batch, const int* alive, int code, int* info) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch && alive[b]) info[b] = code;
+}
+
+// mask[b] = matrix b is alive and still has squaring q to do
+static __global__ void b_square_mask(int batch, const int* alive, const int* s, int q, int* mask) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < batch) mask[b] = alive[b] && q < s[b];
+}
+
+}  // namespace grid
+}  // namespace fmk

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/fm.h"
+#include "fm_bgrid.h"
 #include "fm_grid.h"
 #include "fm_job.h"
 #include "fm_launch.h"
@@ -272,6 +273,47 @@ fm_status run_grid(const Call& c, const fm_opts& o, cudaStream_t st) {
   return (fm_status)grid_run(g, g_err, sizeof g_err);
 }
 
+// a batch of exp over the whole GPU (fm_bgrid.cu)
+fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
+  if (c.kind != JOB_EXPM)
+    return fail(FM_EINVAL, "the grid path takes batches of exp only (other batched jobs: FM_PATH_CTA)");
+  if (!c.A || !c.F || !c.d_dev || !c.off || !c.t_dev || !c.info_dev)
+    return fail(FM_EINVAL, "batched calls need A, F, d_dev, off_dev, t_dev and info_dev");
+  if (c.dmax < 1 || c.dmax > fm_max_dim()) return fail(FM_ESHAPE, "dmax must be in [1, fm_max_dim()]");
+  BGridJob j;
+  memset(&j, 0, sizeof j);
+  fm_status s = pack(c.ce, c.cp, c.cplx, o.form, j.cf);
+  if (s) return s;
+  std::vector<int> d(c.batch);
+  std::vector<int64_t> off(c.batch);
+  cudaError_t e = cudaMemcpyAsync(d.data(), c.d_dev, (size_t)c.batch * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(off.data(), c.off, (size_t)c.batch * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the batch orders");
+  for (int b = 0; b < c.batch; ++b)
+    if (d[b] < 1 || d[b] > c.dmax) return fail(FM_ESHAPE, "a batch order is outside [1, dmax]");
+  j.cplx = c.cplx;
+  j.form = o.form;
+  j.batch = c.batch;
+  j.d_host = d.data();
+  j.off_host = off.data();
+  j.A = c.A;
+  j.t_dev = c.t_dev;
+  j.F = c.F;
+  j.info_dev = c.info_dev;
+  j.s_dev = c.s_dev;
+  j.anorm = o.anorm;
+  j.s_fixed = o.s_fixed;
+  j.max_iters = 40;
+  j.st = st;
+  j.stats = &g_stats;
+  j.ws_bytes = bgrid_ws_bytes(c.cplx, c.batch, d.data());
+  s = get_scratch(j.ws_bytes, &o, &j.ws, st);
+  if (s) return s;
+  return (fm_status)bgrid_run(j, g_err, sizeof g_err);
+}
+
 fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   memset(&g_stats, 0, sizeof g_stats);
   fm_opts o = resolve_opts(optsp);
@@ -280,8 +322,12 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   if (c.kind == JOB_ADJ) o.precision = FM_FP64;
   if (c.batch < 1) return fail(FM_ESHAPE, "batch must be >= 1");
   const bool single = c.d_dev == nullptr && c.kind != JOB_ADJ;
-  if (o.path == FM_PATH_GRID && !single)
-    return fail(FM_EINVAL, "opts.path = FM_PATH_GRID is for single-matrix calls");
+  if (o.path == FM_PATH_GRID && !single) return run_bgrid(c, o, st);
+  // batches of exp in mixed precision with matrices of order 64 and up: the
+  // grid path (tensor-core products over the whole batch) is the faster one
+  if (o.path == FM_PATH_AUTO && !single && c.kind == JOB_EXPM && o.precision != FM_FP64 &&
+      c.dmax >= 64 && c.dmax <= fm_max_dim())
+    return run_bgrid(c, o, st);
   if (single && c.dmax >= 1 &&
       (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && c.dmax > fm_max_dim())))
     return run_grid(c, o, st);
@@ -416,6 +462,13 @@ size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_op
   if (batch == 1 && kind != JOB_ADJ &&
       (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && dmax > fm_max_dim())))
     return grid_ws_bytes(kind, cplx, o.precision, dmax, m);
+  if (batch > 1 && (o.path == FM_PATH_GRID ||
+                    (o.path == FM_PATH_AUTO && kind == JOB_EXPM && o.precision != FM_FP64 &&
+                     dmax >= 64))) {
+    if (kind != JOB_EXPM || dmax > fm_max_dim()) return 0;
+    std::vector<int> d(batch, dmax);
+    return bgrid_ws_bytes(cplx, batch, d.data());
+  }
   if (dmax > fm_max_dim()) return 0;
   return make_plan(kind, cplx, o.precision, batch, dmax, m, k, nmax).total;
 }

@@ -1,0 +1,380 @@
+// fm_bgrid.cu -- host side of the grid path over a batch: exp(t_b A_b) for
+// every matrix of the batch, each step one launch over the whole batch
+// (bgrid.cuh), the tensor-core products as one CTA per 128 x 64 output tile
+// of every matrix (oz_tiles in batch mode).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/fm.h"
+#include "bgrid.cuh"
+#include "fm_bgrid.h"
+
+namespace fmk {
+namespace {
+
+size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Geo {
+  std::vector<grid::BMat> mats;
+  std::vector<int4> items;
+  long long elems = 0;       // sum of d^2
+  long long pxb = 0, pyb = 0;  // plane bytes (all sets)
+  long long accp = 0;        // accumulator pairs
+  long long rows = 0, cols = 0;
+};
+
+Geo geometry(bool cplx, int batch, const int* d, const int64_t* off) {
+  Geo g;
+  g.mats.resize(batch);
+  const int parts = cplx ? 2 : 1;
+  for (int b = 0; b < batch; ++b) {
+    grid::BMat& M = g.mats[b];
+    const int n = d[b];
+    M.d = n;
+    M.mtn = (n + oz::TM - 1) / oz::TM;
+    M.ntn = (n + oz::TN - 1) / oz::TN;
+    M.kc = (n + grid::GKC - 1) / grid::GKC;
+    M.off = g.elems;
+    M.uoff = off ? off[b] : 0;
+    M.px = g.pxb;
+    M.py = g.pyb;
+    M.acc = g.accp;
+    M.eo = (int)g.rows;
+    M.fo = (int)g.cols;
+    g.elems += (long long)n * n;
+    g.pxb += (long long)parts * M.mtn * M.kc * grid::GXST;
+    g.pyb += (long long)(cplx ? 3 : 1) * M.ntn * M.kc * grid::GYST;
+    g.accp += (long long)parts * M.mtn * oz::TM * M.ntn * oz::TN;
+    g.rows += (long long)M.mtn * oz::TM;
+    g.cols += (long long)M.ntn * oz::TN;
+    for (int p = 0; p < parts; ++p)
+      for (int mt = 0; mt < M.mtn; ++mt)
+        for (int nt = 0; nt < M.ntn; ++nt) g.items.push_back(make_int4(b, p, mt, nt));
+  }
+  return g;
+}
+
+struct Lay {
+  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, C, Y, E, F, pxC, pxG, py,
+      acc, exC, exG, fy, total;
+};
+
+Lay carve(const Geo& g, bool cplx, int batch) {
+  Lay L;
+  const size_t elt = cplx ? 16 : 8;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t at = o;
+    o += up(b);
+    return at;
+  };
+  L.mats = take(g.mats.size() * sizeof(grid::BMat));
+  L.items = take(g.items.size() * sizeof(int4));
+  L.alive = take((size_t)batch * 4);
+  L.mask_e = take((size_t)batch * 4);
+  L.mask_u = take((size_t)batch * 4);
+  L.mask_s = take((size_t)batch * 4);
+  L.sbuf = take((size_t)batch * 4);
+  L.emax = take((size_t)batch * 8);
+  L.prev = take((size_t)batch * 8);
+  L.ctr = take(64);
+  L.B = take((size_t)g.elems * elt);
+  L.C = take((size_t)g.elems * elt);
+  L.Y = take((size_t)g.elems * elt);
+  L.E = take((size_t)g.elems * elt);
+  L.F = take((size_t)g.elems * elt);
+  L.pxC = take((size_t)g.pxb);
+  L.pxG = take((size_t)g.pxb);
+  L.py = take((size_t)g.pyb);
+  L.acc = take((size_t)g.accp * 16);
+  L.exC = take((size_t)g.rows * 4);
+  L.exG = take((size_t)g.rows * 4);
+  L.fy = take((size_t)g.cols * 4);
+  L.total = o;
+  return L;
+}
+
+// device counters
+struct Ctr {
+  int active;
+  int corrections;
+  int err;
+  int pad;
+  double flops;
+};
+
+template <class T>
+class BRunner {
+ public:
+  BRunner(const BGridJob& j, char* msg, size_t len) : j_(j), msg_(msg), len_(len) {}
+  int run();
+
+ private:
+  const BGridJob& j_;
+  char* msg_;
+  size_t len_;
+  cudaStream_t st_ = nullptr;
+  cudaError_t err_ = cudaSuccess;
+  Geo g_;
+  Lay L_;
+  char* base_ = nullptr;
+  grid::BMat* mats_ = nullptr;
+  int4* items_ = nullptr;
+  int *alive_ = nullptr, *mask_e_ = nullptr, *mask_u_ = nullptr, *mask_s_ = nullptr, *s_ = nullptr;
+  unsigned long long* emax_ = nullptr;
+  double* prev_ = nullptr;
+  dim3 gE_, gR_, gC_;  // grids: element slices, row slices, column slices
+  Ctr* ctr_ = nullptr;
+  T *B_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr;
+  unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
+  long long* acc_ = nullptr;
+  int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
+  long long products_ = 0;
+
+  long long launches_ = 0;
+  void check(const char* where) {
+    ++launches_;
+    if (err_ != cudaSuccess) return;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      err_ = e;
+      snprintf(msg_, len_, "%s: %s", where, cudaGetErrorString(e));
+    }
+  }
+  void api(cudaError_t e, const char* where) {
+    if (err_ == cudaSuccess && e != cudaSuccess) {
+      err_ = e;
+      snprintf(msg_, len_, "%s: %s", where, cudaGetErrorString(e));
+    }
+  }
+  Ctr read_ctr() {
+    Ctr h;
+    memset(&h, 0, sizeof h);
+    api(cudaMemcpyAsync(&h, ctr_, sizeof h, cudaMemcpyDeviceToHost, st_), "reading counters");
+    api(cudaStreamSynchronize(st_), "stream synchronize");
+    return h;
+  }
+
+  // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
+  // row planes of X into px (else reuse those already there)
+  void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp, const grid::Epi& e,
+            T* out, const int* mask, unsigned long long* emax) {
+    if (err_ != cudaSuccess) return;
+    const int batch = j_.batch;
+    const int parts = grid::El<T>::parts;
+    if (split_x) {
+      grid::b_split_rows<T><<<gR_, NT, 0, st_>>>(mats_, mask, X, px, ex);
+      check("row digit planes");
+    }
+    grid::b_split_cols<T><<<gC_, NT, 0, st_>>>(mats_, mask, Yp, py_, fy_);
+    check("column digit planes");
+    grid::OzTiles a;
+    memset(&a, 0, sizeof a);
+    a.px = px;
+    a.py = py_;
+    a.nparts = parts;
+    a.nseg = parts;
+    if (parts == 2) {
+      a.sx[0][1] = 1; a.sy[0][1] = 2;
+      a.sx[1][0] = 0; a.sy[1][0] = 1;
+      a.sx[1][1] = 1; a.sy[1][1] = 0;
+    }
+    a.ksplit = 1;
+    a.acc = acc_;
+    a.err = &ctr_->err;
+    a.items = items_;
+    a.mats = mats_;
+    a.mask = mask;
+    a.store = 1;
+    a.flops = &ctr_->flops;
+    grid::oz_tiles<<<(unsigned)g_.items.size(), grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
+    check("tensor-core products");
+    if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
+    grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy_, e, out, emax, nullptr);
+    check("product epilogue");
+    ++products_;
+  }
+};
+
+template <class T>
+int BRunner<T>::run() {
+  const BGridJob& j = j_;
+  st_ = j.st;
+  const int batch = j.batch;
+  g_ = geometry(j.cplx, batch, j.d_host, j.off_host);
+  L_ = carve(g_, j.cplx, batch);
+  if (j.ws_bytes < L_.total) {
+    snprintf(msg_, len_, "batched grid path: workspace too small");
+    return FM_ENOMEM;
+  }
+  base_ = (char*)j.ws;
+  mats_ = (grid::BMat*)(base_ + L_.mats);
+  items_ = (int4*)(base_ + L_.items);
+  alive_ = (int*)(base_ + L_.alive);
+  mask_e_ = (int*)(base_ + L_.mask_e);
+  mask_u_ = (int*)(base_ + L_.mask_u);
+  mask_s_ = (int*)(base_ + L_.mask_s);
+  s_ = j.s_dev ? j.s_dev : (int*)(base_ + L_.sbuf);
+  emax_ = (unsigned long long*)(base_ + L_.emax);
+  prev_ = (double*)(base_ + L_.prev);
+  ctr_ = (Ctr*)(base_ + L_.ctr);
+  B_ = (T*)(base_ + L_.B);
+  C_ = (T*)(base_ + L_.C);
+  Y_ = (T*)(base_ + L_.Y);
+  E_ = (T*)(base_ + L_.E);
+  F_ = (T*)(base_ + L_.F);
+  pxC_ = (unsigned char*)(base_ + L_.pxC);
+  pxG_ = (unsigned char*)(base_ + L_.pxG);
+  py_ = (unsigned char*)(base_ + L_.py);
+  acc_ = (long long*)(base_ + L_.acc);
+  exC_ = (int*)(base_ + L_.exC);
+  exG_ = (int*)(base_ + L_.exG);
+  fy_ = (int*)(base_ + L_.fy);
+  {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+      api(cudaFuncSetAttribute(grid::oz_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               grid::GSMEM + 1024),
+          "cudaFuncSetAttribute");
+      attr_set[dev] = err_ == cudaSuccess;
+    }
+  }
+  api(cudaMemcpyAsync(mats_, g_.mats.data(), g_.mats.size() * sizeof(grid::BMat),
+                      cudaMemcpyHostToDevice, st_),
+      "copying the matrix table");
+  api(cudaMemcpyAsync(items_, g_.items.data(), g_.items.size() * sizeof(int4),
+                      cudaMemcpyHostToDevice, st_),
+      "copying the tile table");
+  api(cudaMemsetAsync(ctr_, 0, sizeof(Ctr), st_), "counter reset");
+  const FmCoef& cf = j.cf;
+  const int nb = (batch + 255) / 256;
+  int dmax = 1;
+  for (int b = 0; b < batch; ++b) dmax = j.d_host[b] > dmax ? j.d_host[b] : dmax;
+  gE_ = dim3(batch, (unsigned)(((long long)dmax * dmax + grid::BE - 1) / grid::BE));
+  gR_ = dim3(batch, (unsigned)((dmax + grid::RB - 1) / grid::RB));
+  gC_ = dim3(batch, (unsigned)((dmax + grid::CB - 1) / grid::CB));
+  // the digit planes outside real rows, columns and 8-value groups stay zero
+  api(cudaMemsetAsync(pxC_, 0, (size_t)g_.pxb, st_), "plane reset");
+  api(cudaMemsetAsync(pxG_, 0, (size_t)g_.pxb, st_), "plane reset");
+  api(cudaMemsetAsync(py_, 0, (size_t)g_.pyb, st_), "plane reset");
+
+  // a1/a2
+  grid::b_prologue<T><<<batch, NT, 0, st_>>>(mats_, (const T*)j.A, j.t_dev, B_, j.anorm, cf.theta,
+                                            j.s_fixed, s_, j.info_dev, alive_);
+  check("prologue");
+  std::vector<int> s_host(batch);
+  api(cudaMemcpyAsync(s_host.data(), s_, (size_t)batch * 4, cudaMemcpyDeviceToHost, st_),
+      "reading s");
+  api(cudaStreamSynchronize(st_), "stream synchronize");
+  if (err_ != cudaSuccess) return FM_ECUDA;
+  int s_max = 0;
+  for (int v : s_host) s_max = v > s_max ? v : s_max;
+
+  // a6 (first part): F = base I + d1 B + d2 B^2
+  double base = cf.a0[0];
+  if (j.form == 1)
+    for (int i = 0; i < cf.k; ++i)
+      if (!(cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) base -= cf.b_re[0][i];
+  grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base, F_);
+  check("initial combination");
+  if (cf.d1[0] != 0 || cf.d2[0] != 0) {
+    if (cf.d2[0] != 0) {
+      grid::Epi e;
+      prod(B_, pxG_, exG_, true, B_, e, E_, alive_, nullptr);
+    }
+    grid::b_hybrid<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.d1[0], B_, cf.d2[0],
+                                            cf.d2[0] != 0 ? E_ : nullptr, F_);
+    check("hybrid terms");
+  }
+
+  // a3-a6: the shifted systems, ascending i
+  for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
+    const double cr = cf.c_re[i], ci = cf.c_im[i];
+    if (cr == 0.0 && ci == 0.0) continue;
+    grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, cr, ci, C_, Y_);
+    check("shift");
+    api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
+        "mask copy");
+    for (int it = 0; err_ == cudaSuccess; ++it) {
+      api(cudaMemsetAsync(&ctr_->active, 0, 4, st_), "counter reset");
+      // E = C Y + C - Y, largest entry per matrix
+      grid::Epi e1;
+      e1.Z1 = C_;
+      e1.b1r = 1.0;
+      e1.Z2 = Y_;
+      e1.b2r = -1.0;
+      prod(C_, pxC_, exC_, it == 0, Y_, e1, E_, mask_e_, emax_);
+      grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, it, j.max_iters, mask_e_,
+                                         mask_u_, j.info_dev, &ctr_->active, &ctr_->corrections);
+      check("correction flags");
+      // Y = Y E + Y + E
+      grid::Epi e2;
+      e2.Z1 = Y_;
+      e2.b1r = 1.0;
+      e2.Z2 = E_;
+      e2.b2r = 1.0;
+      prod(Y_, pxG_, exG_, true, E_, e2, Y_, mask_u_, nullptr);
+      const Ctr h = read_ctr();
+      if (h.active == 0) break;
+    }
+    grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[0][i], cf.b_im[0][i], Y_,
+                                                j.form == 1, F_);
+    check("combination");
+  }
+  if (err_ != cudaSuccess) return FM_ECUDA;
+
+  // a7: s squarings of F = I + E
+  grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F_, -1.0, E_, 0);
+  check("deviation");
+  for (int q = 0; q < s_max; ++q) {
+    grid::b_square_mask<<<nb, 256, 0, st_>>>(batch, alive_, s_, q, mask_s_);
+    check("squaring mask");
+    grid::Epi e;
+    e.Z1 = E_;
+    e.b1r = 2.0;
+    prod(E_, pxG_, exG_, true, E_, e, E_, mask_s_, nullptr);
+  }
+  grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.F, 1);
+  check("output");
+  const Ctr h = read_ctr();
+  if (err_ != cudaSuccess) return FM_ECUDA;
+  if (h.err) {  // a tensor-core wait timed out: every result of the call is invalid
+    grid::b_set_info<<<nb, 256, 0, st_>>>(batch, alive_, -7, j.info_dev);
+    check("status");
+    api(cudaStreamSynchronize(st_), "stream synchronize");
+    if (err_ != cudaSuccess) return FM_ECUDA;
+  }
+  if (j.stats) {
+    fm_stats* st = (fm_stats*)j.stats;
+    st->products = products_;
+    st->product_flops = h.flops;
+    st->digit_flops = 28.0 * h.flops;
+    st->corrections = h.corrections;
+    st->launches = launches_;
+  }
+  return FM_OK;
+}
+
+}  // namespace
+
+size_t bgrid_ws_bytes(bool cplx, int batch, const int* d_host) {
+  Geo g = geometry(cplx, batch, d_host, nullptr);
+  return carve(g, cplx, batch).total;
+}
+
+int bgrid_run(const BGridJob& j, char* msg, size_t len) {
+  if (j.cplx) {
+    BRunner<zd> r(j, msg, len);
+    return r.run();
+  }
+  BRunner<double> r(j, msg, len);
+  return r.run();
+}
+
+}  // namespace fmk

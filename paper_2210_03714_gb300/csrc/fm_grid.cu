@@ -124,7 +124,9 @@ class Runner {
     if (b > cap) b = cap;
     return b < 1 ? 1 : (int)b;
   }
+  long long launches_ = 0;
   void check(const char* where) {
+    ++launches_;
     if (err_ != cudaSuccess) return;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -201,7 +203,6 @@ class Runner {
       grid::split_cols<T><<<blocks(items), kThreads, 0, st_>>>(K, N, Yp, ldy, cmax_, py_, pys, kc, fy_);
       check("column digit planes");
     }
-    memset0(acc_, (size_t)parts * Mp * Np * 16, "accumulator reset");
     grid::OzTiles a;
     memset(&a, 0, sizeof a);
     a.px = px_;
@@ -241,6 +242,7 @@ class Runner {
     a.ksplit = ksplit;
     a.acc = acc_;
     a.err = &misc_->tc_err;
+    memset0(acc_, (size_t)parts * Mp * Np * 16, "accumulator reset");
     grid::oz_tiles<<<tiles * ksplit, grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
     check("tensor-core product");
     grid::epilogue<T><<<blocks((size_t)M * N), kThreads, 0, st_>>>(
@@ -490,6 +492,7 @@ int Runner<T>::run() {
   Misc hf = read_misc();
   if (err_ != cudaSuccess) return FM_ECUDA;
   if (hf.tc_err) info = -7;
+  if (stats_) stats_->launches = launches_;
   return finish(info);
 }
 

@@ -41,6 +41,10 @@ template <> struct El<zd> {
   static __device__ __forceinline__ zd make(double r, double i) { return {r, i}; }
 };
 
+// largest |re|, |im| as the bit pattern of a non-negative double (integer ops)
+template <class T>
+__device__ __forceinline__ unsigned long long abs_bits(T v);
+
 // (cr + i ci) * a with one rounding per real operation (real: cr * a)
 template <class T> __device__ __forceinline__ T cmul(double cr, double ci, T a);
 template <> __device__ __forceinline__ double cmul<double>(double cr, double, double a) {
@@ -48,6 +52,25 @@ template <> __device__ __forceinline__ double cmul<double>(double cr, double, do
 }
 template <> __device__ __forceinline__ zd cmul<zd>(double cr, double ci, zd a) {
   return Tr<zd>::mul(zd{cr, ci}, a);
+}
+
+// a + (cr + i ci) z: an add or a subtract when the coefficient is +-1
+template <class T>
+__device__ __forceinline__ T axpy1(T a, double cr, double ci, T z) {
+  if (ci == 0 && cr == 1.0) return Tr<T>::add(a, z);
+  if (ci == 0 && cr == -1.0) return Tr<T>::sub(a, z);
+  return Tr<T>::add(a, cmul<T>(cr, ci, z));
+}
+
+template <>
+__device__ __forceinline__ unsigned long long abs_bits<double>(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+}
+template <>
+__device__ __forceinline__ unsigned long long abs_bits<zd>(zd v) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFULL;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFULL;
+  return a > b ? a : b;
 }
 
 __device__ __forceinline__ void max_bits(unsigned long long* dst, double v) {
@@ -77,7 +100,7 @@ __global__ void colsum_scale(int n, const T* A, int lda, double t, T* B, double*
 }
 
 // eta = max column sum (NaN propagates, as in the one-CTA kernels)
-__global__ void colsum_max(int n, const double* colsum, double* eta) {
+static __global__ void colsum_max(int n, const double* colsum, double* eta) {
   __shared__ double red[32];
   double m = 0;
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
@@ -207,7 +230,7 @@ __global__ void epilogue(int M, int N, const long long* acc, int parts, int Mp, 
                          const int* ex, const int* fy, const T* Pd, int ldp, Epi e, T* out,
                          int ldo) {
   const size_t count = (size_t)M * N;
-  double mx = 0;
+  unsigned long long mx = 0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count;
        k += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(k / N), j = (int)(k % N);
@@ -225,16 +248,21 @@ __global__ void epilogue(int M, int N, const long long* acc, int parts, int Mp, 
       pr = El<T>::re(p);
       pi = El<T>::im(p);
     }
-    T v = cmul<T>(e.ar, e.ai, El<T>::make(pr, pi));
-    if (e.Z1) v = Tr<T>::add(v, cmul<T>(e.b1r, e.b1i, ((const T*)e.Z1)[(size_t)i * e.ld1 + j]));
-    if (e.Z2) v = Tr<T>::add(v, cmul<T>(e.b2r, e.b2i, ((const T*)e.Z2)[(size_t)i * e.ld2 + j]));
+    T v = El<T>::make(pr, pi);
+    if (e.ar != 1.0 || e.ai != 0) v = cmul<T>(e.ar, e.ai, v);
+    if (e.Z1) v = axpy1<T>(v, e.b1r, e.b1i, ((const T*)e.Z1)[(size_t)i * e.ld1 + j]);
+    if (e.Z2) v = axpy1<T>(v, e.b2r, e.b2i, ((const T*)e.Z2)[(size_t)i * e.ld2 + j]);
     if (i == j && (e.gr != 0 || e.gi != 0)) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
     out[(size_t)i * ldo + j] = v;
-    mx = fmax(mx, fmax(fabs(El<T>::re(v)), fabs(El<T>::im(v))));
+    const unsigned long long ab = abs_bits<T>(v);
+    mx = ab > mx ? ab : mx;
   }
   if (e.maxabs) {
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) max_bits(e.maxabs, mx);
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = v > mx ? v : mx;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(e.maxabs, mx);
   }
 }
 
@@ -418,6 +446,18 @@ __global__ void split_cols(int K, int N, const T* Y, int ldy, const unsigned lon
 // filled by bulk copies and issues the MMAs.  mbarriers: full[s] (copies
 // landed), empty[s] (the stage's MMAs finished), accf (a group's MMAs
 // finished), accr (the 8 readout warps released the accumulators).
+// One matrix of a batch on the tensor-core product path: its geometry and
+// where its data sits in the batch-wide buffers.
+struct BMat {
+  int d, mtn, ntn, kc;  // order, 128-row tiles, 64-column tiles, 16-value K chunks
+  long long off;        // element offset in the packed work matrices (leading dimension d)
+  long long uoff;       // element offset of the caller's matrix (A in, F out)
+  long long px, py;     // byte offsets of its X and Y digit planes
+  long long acc;        // offset, in (hi, lo) pairs, of its accumulators
+  int eo, fo;           // offsets of its rows (mtn*128) and columns (ntn*64) in the
+                        // exponent and maximum arrays
+};
+
 struct OzTiles {
   const unsigned char* px;
   const unsigned char* py;
@@ -428,25 +468,67 @@ struct OzTiles {
   int ksplit;
   long long* acc;  // [part][mtn*128][ntn*64][2]: hi (2^-40 units), lo (2^-64 units)
   int* err;
+  // batch mode (items != nullptr): CTA i computes tile items[i] = (b, part, mt,
+  // nt) of matrix b over its whole K (ksplit 1), with the geometry and offsets
+  // of mats[b]; CTAs of matrices with mask[b] == 0 do nothing
+  const int4* items;
+  const BMat* mats;
+  const int* mask;
+  int store;       // 1: plain stores into acc (one CTA per tile), 0: atomic adds
+  double* flops;             // batch mode: product flops (2d^3, complex 8d^3) added, nullable
 };
 
-__global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
+static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
   extern __shared__ unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[GNST], empty[GNST], accf, accr;
   __shared__ uint32_t tslot;
   __shared__ int s_err;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned char* smem = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
-  int item = blockIdx.x;
-  const int ks = item % a.ksplit;
-  item /= a.ksplit;
-  const int nt = item % a.ntn;
-  item /= a.ntn;
-  const int mt = item % a.mtn;
-  const int part = item / a.mtn;
-  const int nch = a.nseg * a.kc;
+  int ks, nt, mt, part, mtn, ntn, kc, ksplit;
+  const unsigned char *px, *py;
+  size_t pxs, pys;
+  long long* acc;
+  if (a.items) {
+    const int4 it = a.items[blockIdx.x];
+    if (!a.mask[it.x]) return;  // uniform: the whole CTA leaves
+    const BMat& M = a.mats[it.x];
+    if (a.flops && threadIdx.x == 0 && it.y == 0 && it.z == 0 && it.w == 0)
+      atomicAdd(a.flops, (a.nparts == 2 ? 8.0 : 2.0) * M.d * (double)M.d * M.d);
+    part = it.y;
+    mt = it.z;
+    nt = it.w;
+    ks = 0;
+    ksplit = 1;
+    mtn = M.mtn;
+    ntn = M.ntn;
+    kc = M.kc;
+    px = a.px + M.px;
+    py = a.py + M.py;
+    pxs = (size_t)mtn * kc * GXST;
+    pys = (size_t)ntn * kc * GYST;
+    acc = a.acc + M.acc * 2;
+  } else {
+    int item = blockIdx.x;
+    ks = item % a.ksplit;
+    item /= a.ksplit;
+    nt = item % a.ntn;
+    item /= a.ntn;
+    mt = item % a.mtn;
+    part = item / a.mtn;
+    mtn = a.mtn;
+    ntn = a.ntn;
+    kc = a.kc;
+    ksplit = a.ksplit;
+    px = a.px;
+    py = a.py;
+    pxs = a.pxs;
+    pys = a.pys;
+    acc = a.acc;
+  }
+  const int nch = a.nseg * kc;
   const int groups = (nch + GSTEPS - 1) / GSTEPS;
-  const int gpb = (groups + a.ksplit - 1) / a.ksplit;
+  const int gpb = (groups + ksplit - 1) / ksplit;
   const int g0 = ks * gpb, g1 = min(groups, g0 + gpb);
   if (g0 >= g1) return;  // the whole CTA leaves before any barrier or allocation
   const int c0 = g0 * GSTEPS, c1 = min(nch, g1 * GSTEPS);
@@ -475,11 +557,9 @@ __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
       int mma_chunks = 0;       // chunks whose MMAs were issued
       auto load = [&](int ch) {
         const int s = (ch - c0) % GNST;
-        const int seg = ch / a.kc, c = ch % a.kc;
-        const unsigned char* xs =
-            a.px + (size_t)a.sx[part][seg] * a.pxs + ((size_t)mt * a.kc + c) * GXST;
-        const unsigned char* ys =
-            a.py + (size_t)a.sy[part][seg] * a.pys + ((size_t)nt * a.kc + c) * GYST;
+        const int seg = ch / kc, c = ch % kc;
+        const unsigned char* xs = px + (size_t)a.sx[part][seg] * pxs + ((size_t)mt * kc + c) * GXST;
+        const unsigned char* ys = py + (size_t)a.sy[part][seg] * pys + ((size_t)nt * kc + c) * GYST;
         unsigned char* dst = smem + s * GST;
         tc::mbar_arrive_expect_tx(&full[s], GST);
         tc::bulk_g2s(dst, xs, GXST, &full[s]);
@@ -580,14 +660,20 @@ __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
       if (lane == 0) tc::mbar_arrive(&accr);
     }
     if (ok && !s_err) {
-      const int Mp = a.mtn * oz::TM, Np = a.ntn * oz::TN;
+      const int Mp = mtn * oz::TM, Np = ntn * oz::TN;
       const int row = mt * oz::TM + 32 * (warp & 3) + lane;
       unsigned long long* dst =
-          (unsigned long long*)a.acc + (((size_t)part * Mp + row) * Np + nt * oz::TN + colh) * 2;
+          (unsigned long long*)acc + (((size_t)part * Mp + row) * Np + nt * oz::TN + colh) * 2;
+      if (a.store) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (ahi[j]) atomicAdd(dst + 2 * j, (unsigned long long)ahi[j]);
-        if (alo[j]) atomicAdd(dst + 2 * j + 1, (unsigned long long)alo[j]);
+        for (int j = 0; j < 32; ++j)
+          *(ulonglong2*)(dst + 2 * j) = make_ulonglong2(ahi[j], alo[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (ahi[j]) atomicAdd(dst + 2 * j, (unsigned long long)ahi[j]);
+          if (alo[j]) atomicAdd(dst + 2 * j + 1, (unsigned long long)alo[j]);
+        }
       }
     } else if (!ok && lane == 0) {
       atomicOr(a.err, 1);

@@ -106,16 +106,21 @@ __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out) {
     q = (q - v) >> 8;
   }
   d[0] = (int)q;
+  // d_p 2^(-8p) without conversion instructions: 1.5 2^23 + d_p is exact in
+  // FP32 (|d_p| <= 256), one FMA scales it by 2^(-8p) and removes the 1.5 2^23
+  // exactly, and the value (at most 8 significant bits) is its own BF16
+  // truncation: the top 16 bits of the FP32 word.
 #pragma unroll
   for (int p = 0; p < S; ++p) {
-    float f = (float)(neg ? -d[p] : d[p]) * __int_as_float((127 - 8 * (p + 1)) << 23);
-    out[p] = __float2bfloat16_rn(f);  // exact: |d_p| <= 256 has at most 8 significant bits
+    const float sc = __int_as_float((127 - 8 * (p + 1)) << 23);  // 2^(-8(p+1))
+    const float m = __int_as_float(0x4B400000 + (neg ? -d[p] : d[p]));
+    const float f = __fmaf_rn(m, sc, -12582912.0f * sc);
+    out[p] = __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
   }
 }
 
-// round-to-nearest double of (hi 2^24 + lo) 2^e2, hi and lo exact integers
-__device__ __forceinline__ double combine_scaled(long long hi, long long lo, int e2) {
-  __int128 v = ((__int128)hi << 24) + (__int128)lo;
+// round-to-nearest double of v 2^e2, v an exact 128-bit integer
+__device__ __forceinline__ double round_i128(__int128 v, int e2) {
   if (v == 0) return 0.0;
   const bool neg = v < 0;
   unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
@@ -146,6 +151,12 @@ __device__ __forceinline__ double combine_scaled(long long hi, long long lo, int
   const double r = ldexp((double)m, e);  // outside the normal range
   return neg ? -r : r;
 }
+
+// round-to-nearest double of (hi 2^24 + lo) 2^e2, hi and lo exact integers
+__device__ __forceinline__ double combine_scaled(long long hi, long long lo, int e2) {
+  return round_i128(((__int128)hi << 24) + (__int128)lo, e2);
+}
+
 
 // exponent e with |x| < 2^e for the largest |x| (0 for an all-zero set)
 __device__ __forceinline__ int exp_above(double mx) {

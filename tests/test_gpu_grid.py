@@ -164,12 +164,13 @@ def test_grid_nonfinite_and_zero(fm):
     assert np.array_equal(F.cpu().numpy(), np.eye(90))
 
 
-def test_grid_rejects_batched(fm):
+def test_grid_rejects_batched_actions(fm):
+    """Batches on the grid path take exp only; batched actions stay on the one-CTA kernels."""
     import torch
     P = fm.Packed([T(wl.dense_scaled(8, 1.0, 1))])
+    V = torch.ones(8, dtype=torch.float64, device="cuda")
     with pytest.raises(fm.FmError):
-        fm.expm_batched(P, torch.ones(1, dtype=torch.float64, device="cuda"), "R8",
-                        path="grid")
+        fm.expmv_batched(P, V, 1, 1.0, "R8", path="grid")
 
 
 def test_hermitian_action_d4096(fm):

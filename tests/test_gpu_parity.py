@@ -73,15 +73,20 @@ def test_builtin_coeffs_match(fm):
 RAGGED = [1, 2, 5, 16, 17, 31, 48, 63, 64, 65, 100, 129, 200, 256]
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_batched_expm_ragged(fm, prec):
+# the double form runs one CTA per matrix; the mixed form on both paths
+# (automatic selection takes the grid path for these batches)
+PREC_PATH = [("fp64", "auto"), ("mixed", "cta"), ("mixed", "auto")]
+
+
+@pytest.mark.parametrize("prec,path", PREC_PATH)
+def test_batched_expm_ragged(fm, prec, path):
     rng = np.random.default_rng(7)
     norms = rng.uniform(0.5, 8.0, len(RAGGED))
     mats = [wl.dense_scaled(d, n, 100 + i, scale_sqrt=True) for i, (d, n) in enumerate(zip(RAGGED, norms))]
     ts = rng.uniform(0.5, 1.5, len(RAGGED))
     cs = oracle_set("R8")
     P = fm.Packed([T(m) for m in mats])
-    F, info, s = fm.expm_batched(P, T(ts), fm.Coeffs(cs), precision=prec)
+    F, info, s = fm.expm_batched(P, T(ts), fm.Coeffs(cs), precision=prec, path=path)
     F = F.cpu().numpy()
     info, s = info.cpu().numpy(), s.cpu().numpy()
     for b, (M, t) in enumerate(zip(mats, ts)):
@@ -90,15 +95,15 @@ def test_batched_expm_ragged(fm, prec):
         assert relerr(P.get(F, b), ref) <= TOL_FP64, (b, RAGGED[b])
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_batched_expm_mixed_d_full_size_sampled(fm, prec):
+@pytest.mark.parametrize("prec,path", PREC_PATH)
+def test_batched_expm_mixed_d_full_size_sampled(fm, prec, path):
     """The 4096-matrix batch (d uniform over {16..256}, ||A||_1 in [0.5, 8], R8)
     in the launch configuration the benchmark times; 16 sampled results are
     recomputed by the oracle one by one; every status must be 0."""
     import torch
     dims, mats, norms = wl.batch_mixed_d(4096)
     P = fm.Packed([torch.from_numpy(m) for m in mats], device="cuda")
-    F, info, s = fm.expm_batched(P, 1.0, "R8", precision=prec)
+    F, info, s = fm.expm_batched(P, 1.0, "R8", precision=prec, path=path)
     torch.cuda.synchronize()
     assert int((info != 0).sum().item()) == 0
     s = s.cpu().numpy()
