@@ -665,9 +665,14 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
       unsigned long long* dst =
           (unsigned long long*)acc + (((size_t)part * Mp + row) * Np + nt * oz::TN + colh) * 2;
       if (a.store) {
+        // only the matrix's own rows and columns: the epilogue reads no others
+        const int dm = a.items ? a.mats[a.items[blockIdx.x].x].d : mtn * oz::TM;
+        const int col0 = nt * oz::TN + colh;
+        if (row < dm) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          *(ulonglong2*)(dst + 2 * j) = make_ulonglong2(ahi[j], alo[j]);
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < dm) *(ulonglong2*)(dst + 2 * j) = make_ulonglong2(ahi[j], alo[j]);
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
