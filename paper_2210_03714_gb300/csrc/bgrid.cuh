@@ -175,11 +175,17 @@ __global__ void b_split_rows(const BMat* mats, const int* mask, const T* X, unsi
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int rr = w; rr < nr; rr += nw) {
     const int r = r0 + rr;
-    double mx = 0;
-    for (int k = lane; k < n; k += 32) mx = fmax(mx, max_re_im(Xb[(size_t)r * n + k]));
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    unsigned long long mx = 0;  // largest |re|, |im| as bits: integer operations only
+    for (int k = lane; k < n; k += 32) {
+      const unsigned long long b = abs_bits<T>(Xb[(size_t)r * n + k]);
+      mx = b > mx ? b : mx;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = b > mx ? b : mx;
+    }
     if (lane == 0) {
-      s_e[rr] = oz::exp_above(mx);
+      s_e[rr] = oz::exp_above_bits(mx);
       ex[M.eo + r] = s_e[rr];
     }
   }
@@ -223,7 +229,7 @@ __global__ void b_split_rows(const BMat* mats, const int* mask, const T* X, unsi
 template <class T>
 __global__ void b_split_cols(const BMat* mats, const int* mask, const T* Y, unsigned char* py,
                              int* fy) {
-  __shared__ double red[8][CB + 1];
+  __shared__ unsigned long long red[8][CB + 1];
   __shared__ int s_f[CB];
   if (!mask[blockIdx.x]) return;
   const BMat M = mats[blockIdx.x];
@@ -234,15 +240,18 @@ __global__ void b_split_cols(const BMat* mats, const int* mask, const T* Y, unsi
   const T* Yb = Y + M.off;
   {
     const int cx = threadIdx.x % CB, ry = threadIdx.x / CB;  // 8 row lanes x 32 columns
-    double mx = 0;
+    unsigned long long mx = 0;
     if (cx < nc)
-      for (int k = ry; k < n; k += 8) mx = fmax(mx, max_re_im(Yb[(size_t)k * n + c0 + cx]));
+      for (int k = ry; k < n; k += 8) {
+        const unsigned long long b = abs_bits<T>(Yb[(size_t)k * n + c0 + cx]);
+        mx = b > mx ? b : mx;
+      }
     red[ry][cx] = mx;
     __syncthreads();
     if (ry == 0) {
-      for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][cx]);
+      for (int q = 1; q < 8; ++q) mx = red[q][cx] > mx ? red[q][cx] : mx;
       if (cx < nc) {
-        s_f[cx] = oz::exp_above(mx);
+        s_f[cx] = oz::exp_above_bits(mx);
         fy[M.fo + c0 + cx] = s_f[cx];
       }
     }
@@ -315,17 +324,30 @@ __global__ void b_epilogue(const BMat* mats, const int* mask, const long long* a
     const size_t el = (size_t)i * n + j;
     const int e2 = ex[M.eo + i] + fy[M.fo + j] - 64;
     const longlong2 a0 = *(const longlong2*)(ab + ((size_t)i * Np + j) * 2);
-    const double pr = oz::combine_scaled(a0.x, a0.y, e2);
-    double pi = 0;
-    if (parts == 2) {
-      const longlong2 a1 = *(const longlong2*)(ab + ((size_t)Mp * Np + (size_t)i * Np + j) * 2);
-      pi = oz::combine_scaled(a1.x, a1.y, e2);
+    T v;
+    if (e.fx) {
+      const T z1 = Z1 ? Z1[M.off + el] : El<T>::make(0.0, 0.0);
+      const T z2 = Z2 ? Z2[M.off + el] : El<T>::make(0.0, 0.0);
+      const double re = epi_part(e, a0.x, a0.y, e2, Z1, El<T>::re(z1), Z2, El<T>::re(z2), i == j, e.gr);
+      double im = 0;
+      if (parts == 2) {
+        const longlong2 a1 = *(const longlong2*)(ab + ((size_t)Mp * Np + (size_t)i * Np + j) * 2);
+        im = epi_part(e, a1.x, a1.y, e2, Z1, El<T>::im(z1), Z2, El<T>::im(z2), i == j, e.gi);
+      }
+      v = El<T>::make(re, im);
+    } else {
+      const double pr = oz::combine_scaled(a0.x, a0.y, e2);
+      double pi = 0;
+      if (parts == 2) {
+        const longlong2 a1 = *(const longlong2*)(ab + ((size_t)Mp * Np + (size_t)i * Np + j) * 2);
+        pi = oz::combine_scaled(a1.x, a1.y, e2);
+      }
+      v = El<T>::make(pr, pi);
+      if (scale) v = cmul<T>(e.ar, e.ai, v);
+      if (Z1) v = axpy1<T>(v, e.b1r, e.b1i, Z1[M.off + el]);
+      if (Z2) v = axpy1<T>(v, e.b2r, e.b2i, Z2[M.off + el]);
+      if (i == j && (e.gr != 0 || e.gi != 0)) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
     }
-    T v = El<T>::make(pr, pi);
-    if (scale) v = cmul<T>(e.ar, e.ai, v);
-    if (Z1) v = axpy1<T>(v, e.b1r, e.b1i, Z1[M.off + el]);
-    if (Z2) v = axpy1<T>(v, e.b2r, e.b2i, Z2[M.off + el]);
-    if (i == j && (e.gr != 0 || e.gi != 0)) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
     out[M.off + el] = v;
     const unsigned long long bb = abs_bits<T>(v);
     mx = bb > mx ? bb : mx;

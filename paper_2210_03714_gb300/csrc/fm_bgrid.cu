@@ -161,9 +161,11 @@ class BRunner {
 
   // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
   // row planes of X into px (else reuse those already there)
-  void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp, const grid::Epi& e,
-            T* out, const int* mask, unsigned long long* emax) {
+  void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp,
+            const grid::Epi& e_in, T* out, const int* mask, unsigned long long* emax) {
     if (err_ != cudaSuccess) return;
+    grid::Epi e = e_in;
+    grid::fixed_form(e);
     const int batch = j_.batch;
     const int parts = grid::El<T>::parts;
     if (split_x) {

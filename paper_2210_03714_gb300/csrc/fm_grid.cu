@@ -158,8 +158,10 @@ class Runner {
   // out (M x N, ldo) = epilogue(X (M x K) Y (K x N)); split_x = false reuses
   // the row digit planes of the previous product's X (same matrix, same M, K)
   void prod(int M, int N, int K, const T* X, int ldx, bool split_x, const T* Yp, int ldy,
-            const grid::Epi& e, T* out, int ldo) {
+            const grid::Epi& e_in, T* out, int ldo) {
     if (err_ != cudaSuccess) return;
+    grid::Epi e = e_in;
+    grid::fixed_form(e);
     if (stats_) {
       const double f = (grid::El<T>::parts == 2 ? 8.0 : 2.0) * M * (double)N * K;
       stats_->products += 1;

@@ -223,7 +223,67 @@ struct Epi {
   double b2r = 0, b2i = 0;
   double gr = 0, gi = 0;
   unsigned long long* maxabs = nullptr;  // max |re|, |im| of out (bits), nullable
+  // integer form (fx = 1, set by fixed_form): alpha, b1, b2 are real powers of
+  // two (sign s*, exponent k*), and each output is summed exactly in 128-bit
+  // fixed point and rounded once, without the FP64 unit
+  int fx = 0, ka = 0, sa = 0, k1 = 0, s1 = 0, k2 = 0, s2 = 0;
 };
+
+// c = +-2^k
+inline bool epi_pow2(double c, int* neg, int* k) {
+  if (!(c != 0) || !(c - c == 0)) return false;
+  int e;
+  const double m = frexp(c < 0 ? -c : c, &e);
+  if (m != 0.5) return false;
+  *neg = c < 0;
+  *k = e - 1;
+  return true;
+}
+
+// select the integer form when every coefficient allows it (host)
+inline void fixed_form(Epi& e) {
+  e.fx = 0;
+  if (e.ai != 0 || e.b1i != 0 || e.b2i != 0) return;
+  if (!epi_pow2(e.ar, &e.sa, &e.ka) || e.ka < -2) return;
+  if (e.Z1 && !epi_pow2(e.b1r, &e.s1, &e.k1)) return;
+  if (e.Z2 && !epi_pow2(e.b2r, &e.s2, &e.k2)) return;
+  e.fx = 1;
+}
+
+// one component of alpha P + b1 z1 + b2 z2 + g, P = (hi 2^24 + lo) 2^e2: exact
+// 128-bit sum rounded once (integer form), else in double
+__device__ __forceinline__ double epi_part(const Epi& e, long long hi, long long lo, int e2,
+                                           bool h1, double z1, bool h2, double z2, bool diag,
+                                           double g) {
+  if (e.fx) {
+    const int u = e2 - 2;  // two fraction bits below the product's unit (alpha >= 1/4)
+    __int128 S = (((__int128)hi << 24) + (__int128)lo) << 2;
+    S = e.ka >= 0 ? (S << e.ka) : (S >> (-e.ka));
+    if (e.sa) S = -S;
+    bool ok = true;
+    __int128 t;
+    if (h1) {
+      ok &= oz::to_fixed(z1, e.k1, e.s1, u, t);
+      S += t;
+    }
+    if (h2) {
+      ok &= oz::to_fixed(z2, e.k2, e.s2, u, t);
+      S += t;
+    }
+    if (diag && g != 0) {
+      ok &= oz::to_fixed(g, 0, false, u, t);
+      S += t;
+    }
+    if (ok) return oz::round_i128(S, u);
+  }
+  // a term too far above the product's scale, not finite, or general weights
+  double v = oz::combine_scaled(hi, lo, e2);
+  if (e.ar != 1.0) v = __dmul_rn(e.ar, v);
+  if (h1) v = __dadd_rn(v, __dmul_rn(e.b1r, z1));
+  if (h2) v = __dadd_rn(v, __dmul_rn(e.b2r, z2));
+  if (diag && g != 0) v = __dadd_rn(v, g);
+  return v;
+}
 
 template <class T>
 __global__ void epilogue(int M, int N, const long long* acc, int parts, int Mp, int Np,
@@ -234,25 +294,42 @@ __global__ void epilogue(int M, int N, const long long* acc, int parts, int Mp, 
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count;
        k += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(k / N), j = (int)(k % N);
-    double pr, pi = 0;
-    if (acc) {
+    T v;
+    if (acc && e.fx) {
       const int e2 = ex[i] + fy[j] - 64;
       const long long* a0 = acc + ((size_t)i * Np + j) * 2;
-      pr = oz::combine_scaled(a0[0], a0[1], e2);
+      const T z1 = e.Z1 ? ((const T*)e.Z1)[(size_t)i * e.ld1 + j] : El<T>::make(0.0, 0.0);
+      const T z2 = e.Z2 ? ((const T*)e.Z2)[(size_t)i * e.ld2 + j] : El<T>::make(0.0, 0.0);
+      const double re = epi_part(e, a0[0], a0[1], e2, e.Z1, El<T>::re(z1), e.Z2, El<T>::re(z2),
+                                 i == j, e.gr);
+      double im = 0;
       if (parts == 2) {
         const long long* a1 = acc + ((size_t)Mp * Np + (size_t)i * Np + j) * 2;
-        pi = oz::combine_scaled(a1[0], a1[1], e2);
+        im = epi_part(e, a1[0], a1[1], e2, e.Z1, El<T>::im(z1), e.Z2, El<T>::im(z2), i == j,
+                      e.gi);
       }
+      v = El<T>::make(re, im);
     } else {
-      const T p = Pd[(size_t)i * ldp + j];
-      pr = El<T>::re(p);
-      pi = El<T>::im(p);
+      double pr, pi = 0;
+      if (acc) {
+        const int e2 = ex[i] + fy[j] - 64;
+        const long long* a0 = acc + ((size_t)i * Np + j) * 2;
+        pr = oz::combine_scaled(a0[0], a0[1], e2);
+        if (parts == 2) {
+          const long long* a1 = acc + ((size_t)Mp * Np + (size_t)i * Np + j) * 2;
+          pi = oz::combine_scaled(a1[0], a1[1], e2);
+        }
+      } else {
+        const T p = Pd[(size_t)i * ldp + j];
+        pr = El<T>::re(p);
+        pi = El<T>::im(p);
+      }
+      v = El<T>::make(pr, pi);
+      if (e.ar != 1.0 || e.ai != 0) v = cmul<T>(e.ar, e.ai, v);
+      if (e.Z1) v = axpy1<T>(v, e.b1r, e.b1i, ((const T*)e.Z1)[(size_t)i * e.ld1 + j]);
+      if (e.Z2) v = axpy1<T>(v, e.b2r, e.b2i, ((const T*)e.Z2)[(size_t)i * e.ld2 + j]);
+      if (i == j && (e.gr != 0 || e.gi != 0)) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
     }
-    T v = El<T>::make(pr, pi);
-    if (e.ar != 1.0 || e.ai != 0) v = cmul<T>(e.ar, e.ai, v);
-    if (e.Z1) v = axpy1<T>(v, e.b1r, e.b1i, ((const T*)e.Z1)[(size_t)i * e.ld1 + j]);
-    if (e.Z2) v = axpy1<T>(v, e.b2r, e.b2i, ((const T*)e.Z2)[(size_t)i * e.ld2 + j]);
-    if (i == j && (e.gr != 0 || e.gi != 0)) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
     out[(size_t)i * ldo + j] = v;
     const unsigned long long ab = abs_bits<T>(v);
     mx = ab > mx ? ab : mx;
@@ -307,39 +384,40 @@ __global__ void row_max(int M, int K, const T* X, int ldx, unsigned long long* r
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int r = w; r < M; r += nw) {
-    double mx = 0;
+    unsigned long long mx = 0;  // as bits: integer operations only
     for (int k = lane; k < K; k += 32) {
-      const T v = X[(size_t)r * ldx + k];
-      mx = fmax(mx, fmax(fabs(El<T>::re(v)), fabs(El<T>::im(v))));
+      const unsigned long long b = abs_bits<T>(X[(size_t)r * ldx + k]);
+      mx = b > mx ? b : mx;
     }
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) rmax[r] = (unsigned long long)__double_as_longlong(mx);
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) rmax[r] = mx;
   }
 }
 
 // largest |re|, |im| of every column of Y: blocks of 32 columns x 8 row lanes
 template <class T>
 __global__ void col_max(int K, int N, const T* Y, int ldy, unsigned long long* cmax) {
-  __shared__ double red[8][33];
+  __shared__ unsigned long long red[8][33];
   const int cx = threadIdx.x & 31, ry = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + cx;
-  double mx = 0;
+  unsigned long long mx = 0;
   if (j < N)
     for (int k = blockIdx.y * 8 + ry; k < K; k += 8 * gridDim.y) {
-      const T v = Y[(size_t)k * ldy + j];
-      mx = fmax(mx, fmax(fabs(El<T>::re(v)), fabs(El<T>::im(v))));
+      const unsigned long long b = abs_bits<T>(Y[(size_t)k * ldy + j]);
+      mx = b > mx ? b : mx;
     }
   red[ry][cx] = mx;
   __syncthreads();
   if (ry == 0 && j < N) {
-    for (int q = 1; q < 8; ++q) mx = fmax(mx, red[q][cx]);
-    max_bits(cmax + j, mx);
+    for (int q = 1; q < 8; ++q) mx = red[q][cx] > mx ? red[q][cx] : mx;
+    atomicMax(cmax + j, mx);
   }
 }
 
-__device__ __forceinline__ int exp_of_bits(unsigned long long b) {
-  return oz::exp_above(__longlong_as_double((long long)b));
-}
+__device__ __forceinline__ int exp_of_bits(unsigned long long b) { return oz::exp_above_bits(b); }
 
 // X (M x K) -> row digit planes; item = (row, 8 consecutive k)
 template <class T>

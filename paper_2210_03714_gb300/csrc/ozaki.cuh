@@ -148,8 +148,40 @@ __device__ __forceinline__ double round_i128(__int128 v, int e2) {
                                     (neg ? 0x8000000000000000ULL : 0ULL);
     return __longlong_as_double((long long)bits);
   }
-  const double r = ldexp((double)m, e);  // outside the normal range
-  return neg ? -r : r;
+  // outside the normal range, with integer operations only (no FP64 unit):
+  // overflow to infinity; below 2^-1022 the 53-bit mantissa is shifted into
+  // the subnormal field (truncated: such values are far below any result here)
+  const unsigned long long sgn = neg ? 0x8000000000000000ULL : 0ULL;
+  if (ef > 2046) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ULL));
+  const unsigned long long mant = nbm <= 53 ? (m << (53 - nbm)) : (m >> (nbm - 53));
+  const int sh = 1 - ef;
+  return __longlong_as_double((long long)(sgn | (sh < 64 ? (mant >> sh) : 0ULL)));
+}
+
+// s 2^k z as an exact multiple of 2^e (z double, s = +-1): false when z is not
+// finite or the value would need more than 126 bits; bits of z below 2^e are
+// rounded to nearest (at most half a unit 2^e)
+__device__ __forceinline__ bool to_fixed(double z, int k, bool neg, int e, __int128& out) {
+  const long long bits = __double_as_longlong(z);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0x7FF) return false;
+  if (E == 0) {  // zero or subnormal: below every unit these sums use
+    out = 0;
+    return true;
+  }
+  const long long m = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const int sh = E - 1075 + k - e;  // s 2^k z = +-m 2^(sh + e)
+  __int128 v;
+  if (sh >= 0) {
+    if (sh > 72) return false;
+    v = (__int128)m << sh;
+  } else if (sh > -60) {
+    v = (m + (1LL << (-sh - 1))) >> (-sh);
+  } else {
+    v = 0;
+  }
+  out = ((bits < 0) != neg) ? -v : v;
+  return true;
 }
 
 // round-to-nearest double of (hi 2^24 + lo) 2^e2, hi and lo exact integers
@@ -158,12 +190,13 @@ __device__ __forceinline__ double combine_scaled(long long hi, long long lo, int
 }
 
 
-// exponent e with |x| < 2^e for the largest |x| (0 for an all-zero set)
-__device__ __forceinline__ int exp_above(double mx) {
-  if (!(mx > 0)) return 0;
-  int e;
-  frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): mx < 2^e
-  return e;
+// exponent e with |x| < 2^e from the bit pattern of the largest |x| (0 for an
+// all-zero set; integer operations only):
+// 1.f 2^(E - 1023) < 2^(E - 1022); subnormals < 2^-1022
+__device__ __forceinline__ int exp_above_bits(unsigned long long b) {
+  if (b == 0) return 0;
+  const int E = (int)(b >> 52);
+  return E == 0 ? -1022 : E - 1022;
 }
 
 // Split X (M x K, row-major, ld) row-wise into digit planes in ctx.gx.
@@ -171,11 +204,18 @@ static __device__ void split_rows(Ctx& c, int M, int K, const double* X, int ldx
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int mt = (M + TM - 1) / TM, kc = (K + KC - 1) / KC;
   for (int r = warp; r < mt * TM; r += NT / 32) {
-    double mx = 0;
+    unsigned long long mx = 0;  // largest |x| as bits: integer operations only
     if (r < M)
-      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[(size_t)r * ldx + k]));
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) c.ex[r] = exp_above(mx);
+      for (int k = lane; k < K; k += 32) {
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(X[(size_t)r * ldx + k]) & 0x7FFFFFFFFFFFFFFFULL;
+        mx = b > mx ? b : mx;
+      }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) c.ex[r] = exp_above_bits(mx);
   }
   __syncthreads();
   // work item: one row, 8 consecutive k -> 7 x 16-byte stores
@@ -209,12 +249,16 @@ static __device__ void split_cols(Ctx& c, int K, int N, const double* Y, int ldy
   const int tid = threadIdx.x;
   const int nt = (N + TN - 1) / TN, kc = (K + KC - 1) / KC;
   for (int j = tid; j < nt * TN; j += NT) {
-    double mx = 0;
+    unsigned long long mx = 0;
     if (j < N) {
 #pragma unroll 8
-      for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(Y[(size_t)k * ldy + j]));
+      for (int k = 0; k < K; ++k) {
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(Y[(size_t)k * ldy + j]) & 0x7FFFFFFFFFFFFFFFULL;
+        mx = b > mx ? b : mx;
+      }
     }
-    c.fy[j] = exp_above(mx);
+    c.fy[j] = exp_above_bits(mx);
   }
   __syncthreads();
   const int items = nt * TN * kc * (KC / 8);
