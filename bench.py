@@ -251,7 +251,7 @@ def run_single(args):
                 "unit": "TFLOP/s", "frac": ach / pk[pipe][0], "traffic": None,
                 "note": "all grid-path kernels of one call (products, splits, epilogues, "
                         "elementwise) over the call's event time; flops = the digit products "
-                        "(28 per product flop) or the double products"}
+                        "(pairs kept per product flop) or the double products"}
     diff = None
     fp64_ms = None
     if not args.no_fp64 and args.precision == "mixed":
@@ -467,8 +467,8 @@ def main():
         roofline = {"bound": "tensor", "pipe": "tensor_bf16", "achieved": ach, "peak": pk[0],
                     "peak_source": pk[1], "unit": "TFLOP/s", "frac": ach / pk[0], "traffic": None,
                     "flops_per_step": st["digit_flops"], "products_per_step": st["products"],
-                    "note": "digit-pair flops of every product in the step (28 per product "
-                            "flop) over the step's event time"}
+                    "note": "digit-pair flops of every product in the step (the pairs kept, "
+                            "28 at full accuracy, per product flop) over the step's event time"}
     else:
         roofline = roofline_of(pipe_work(dims, s_host, args.precision), ms, peaks)
         roofline["traffic"] = TRAFFIC.get(args.precision) if BATCH == 4096 and not args.dims else None

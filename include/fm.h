@@ -274,8 +274,9 @@ const char* fm_last_error(void);
 
 /* Work done by the calling thread's last call on the grid path (zeros after a
  * call on the one-CTA path): matrix products, their algorithmic flops (2MNK
- * real, 8MNK complex), the tensor-core flops of their digit products (28
- * digit-pair products per product flop; 0 on the FP64 pipe), and the largest
+ * real, 8MNK complex), the tensor-core flops of their digit products (the
+ * digit pairs kept, 28 at full accuracy, per product flop; 0 on the FP64
+ * pipe), and the largest
  * number of correction steps one shifted system took, and the number of kernel
  * launches of the call.  The library has no
  * counterpart in the paper; it serves measurement. */

@@ -366,7 +366,7 @@ __global__ void b_epilogue(const BMat* mats, const int* mask, const long long* a
 // info -1, done; otherwise correct, and stop after that when em d <= 2^-30.
 static __global__ void b_flags(int batch, const BMat* mats, const unsigned long long* emax, double* prev, int it,
                         int max_iters, int* mask_e, int* mask_u, int* info, int* active,
-                        int* corrections) {
+                        int* corrections, unsigned long long* emax_all) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
   if (!mask_e[b]) {
@@ -385,6 +385,7 @@ static __global__ void b_flags(int batch, const BMat* mats, const unsigned long 
     prev[b] = em;
     mask_u[b] = 1;
     atomicMax(corrections, it + 1);
+    atomicMax(emax_all, emax[b]);
     if (em * mats[b].d <= 9.313225746154785e-10 /* 2^-30 */) mask_e[b] = 0;
   }
   if (mask_e[b]) atomicAdd(active, 1);

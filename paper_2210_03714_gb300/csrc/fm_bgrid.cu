@@ -105,6 +105,8 @@ struct Ctr {
   int err;
   int pad;
   double flops;
+  unsigned long long emax;  // largest residual entry (bits) of the matrices correcting
+  double dflops;
 };
 
 template <class T>
@@ -162,7 +164,8 @@ class BRunner {
   // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
   // row planes of X into px (else reuse those already there)
   void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp,
-            const grid::Epi& e_in, T* out, const int* mask, unsigned long long* emax) {
+            const grid::Epi& e_in, T* out, const int* mask, unsigned long long* emax,
+            int lmax = 8) {
     if (err_ != cudaSuccess) return;
     grid::Epi e = e_in;
     grid::fixed_form(e);
@@ -186,6 +189,7 @@ class BRunner {
       a.sx[1][1] = 1; a.sy[1][1] = 0;
     }
     a.ksplit = 1;
+    a.lmax = lmax;
     a.acc = acc_;
     a.err = &ctr_->err;
     a.items = items_;
@@ -193,6 +197,7 @@ class BRunner {
     a.mask = mask;
     a.store = 1;
     a.flops = &ctr_->flops;
+    a.dflops = &ctr_->dflops;
     grid::oz_tiles<<<(unsigned)g_.items.size(), grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
     check("tensor-core products");
     if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
@@ -313,16 +318,31 @@ int BRunner<T>::run() {
       e1.b2r = -1.0;
       prod(C_, pxC_, exC_, it == 0, Y_, e1, E_, mask_e_, emax_);
       grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, it, j.max_iters, mask_e_,
-                                         mask_u_, j.info_dev, &ctr_->active, &ctr_->corrections);
+                                         mask_u_, j.info_dev, &ctr_->active, &ctr_->corrections,
+                                         &ctr_->emax);
       check("correction flags");
-      // Y = Y E + Y + E
+      const Ctr h = read_ctr();
+      if (err_ != cudaSuccess) break;
+      // Y = Y E + Y + E.  The product Y E needs an absolute accuracy of about
+      // u max|Y| only, and its error is about 2^(14 - 8 Lmax) 8 sqrt(d)
+      // max|Y| max|E|: keep the digit-pair levels that bound requires.
+      double em;
+      memcpy(&em, &h.emax, sizeof em);
+      int lmax = 8;
+      if (em > 0 && em < 1) {
+        const double need = 70.0 + 0.5 * log2((double)dmax) + log2(em);
+        lmax = (int)ceil(need / 8.0);
+        lmax = lmax < 2 ? 2 : (lmax > 8 ? 8 : lmax);
+      }
       grid::Epi e2;
       e2.Z1 = Y_;
       e2.b1r = 1.0;
       e2.Z2 = E_;
       e2.b2r = 1.0;
-      prod(Y_, pxG_, exG_, true, E_, e2, Y_, mask_u_, nullptr);
-      const Ctr h = read_ctr();
+      // first correction: Y = C, whose row planes are already in pxC
+      if (it == 0) prod(Y_, pxC_, exC_, false, E_, e2, Y_, mask_u_, nullptr, lmax);
+      else prod(Y_, pxG_, exG_, true, E_, e2, Y_, mask_u_, nullptr, lmax);
+      api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
       if (h.active == 0) break;
     }
     grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[0][i], cf.b_im[0][i], Y_,
@@ -356,7 +376,7 @@ int BRunner<T>::run() {
     fm_stats* st = (fm_stats*)j.stats;
     st->products = products_;
     st->product_flops = h.flops;
-    st->digit_flops = 28.0 * h.flops;
+    st->digit_flops = h.dflops;
     st->corrections = h.corrections;
     st->launches = launches_;
   }

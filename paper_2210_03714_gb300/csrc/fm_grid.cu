@@ -158,7 +158,7 @@ class Runner {
   // out (M x N, ldo) = epilogue(X (M x K) Y (K x N)); split_x = false reuses
   // the row digit planes of the previous product's X (same matrix, same M, K)
   void prod(int M, int N, int K, const T* X, int ldx, bool split_x, const T* Yp, int ldy,
-            const grid::Epi& e_in, T* out, int ldo) {
+            const grid::Epi& e_in, T* out, int ldo, int lmax = 8) {
     if (err_ != cudaSuccess) return;
     grid::Epi e = e_in;
     grid::fixed_form(e);
@@ -166,7 +166,7 @@ class Runner {
       const double f = (grid::El<T>::parts == 2 ? 8.0 : 2.0) * M * (double)N * K;
       stats_->products += 1;
       stats_->product_flops += f;
-      if (tcp_) stats_->digit_flops += 28.0 * f;
+      if (tcp_) stats_->digit_flops += f * (lmax - 1) * lmax / 2;  // digit pairs kept
     }
     if (!tcp_) {
       const int tiles = ((M + GT - 1) / GT) * ((N + GT - 1) / GT);
@@ -242,6 +242,7 @@ class Runner {
       }
     }
     a.ksplit = ksplit;
+    a.lmax = lmax;
     a.acc = acc_;
     a.err = &misc_->tc_err;
     memset0(acc_, (size_t)parts * Mp * Np * 16, "accumulator reset");
@@ -417,7 +418,14 @@ int Runner<T>::run() {
       }
       prev = em;
       if (stats_ && it + 1 > stats_->corrections) stats_->corrections = it + 1;
-      // Y = Y E + Y + E  (= Y + (I + Y) E)
+      // Y = Y E + Y + E  (= Y + (I + Y) E).  Y E needs an absolute accuracy of
+      // about u max|Y|; its error is about 2^(14 - 8 Lmax) 8 sqrt(d) max|Y| max|E|:
+      // keep the digit-pair levels that bound requires
+      int lmax = 8;
+      if (em < 1) {
+        lmax = (int)ceil((70.0 + 0.5 * log2((double)n) + log2(em)) / 8.0);
+        lmax = lmax < 2 ? 2 : (lmax > 8 ? 8 : lmax);
+      }
       grid::Epi e2;
       e2.Z1 = Y_;
       e2.ld1 = n;
@@ -425,7 +433,7 @@ int Runner<T>::run() {
       e2.Z2 = E_;
       e2.ld2 = n;
       e2.b2r = 1.0;
-      prod(n, n, n, Y_, n, true, E_, n, e2, Y_, n);
+      prod(n, n, n, Y_, n, true, E_, n, e2, Y_, n, lmax);
       if (em <= stop) break;  // the residual after this correction is ~em^2
     }
     for (int f = 0; f < nf; ++f) {

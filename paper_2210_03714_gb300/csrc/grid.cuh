@@ -544,6 +544,10 @@ struct OzTiles {
   int nparts, nseg;
   int sx[2][2], sy[2][2];
   int ksplit;
+  // highest digit-pair level kept, 2..8 (0 means 8): a product whose exact
+  // value only matters to a coarser absolute accuracy drops levels L+1..8,
+  // loads digits 1..L-1 only and issues fewer MMAs
+  int lmax;
   long long* acc;  // [part][mtn*128][ntn*64][2]: hi (2^-40 units), lo (2^-64 units)
   int* err;
   // batch mode (items != nullptr): CTA i computes tile items[i] = (b, part, mt,
@@ -554,6 +558,7 @@ struct OzTiles {
   const int* mask;
   int store;       // 1: plain stores into acc (one CTA per tile), 0: atomic adds
   double* flops;             // batch mode: product flops (2d^3, complex 8d^3) added, nullable
+  double* dflops;            // batch mode: digit-pair flops (pairs kept x product flops), nullable
 };
 
 static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
@@ -571,8 +576,12 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
     const int4 it = a.items[blockIdx.x];
     if (!a.mask[it.x]) return;  // uniform: the whole CTA leaves
     const BMat& M = a.mats[it.x];
-    if (a.flops && threadIdx.x == 0 && it.y == 0 && it.z == 0 && it.w == 0)
-      atomicAdd(a.flops, (a.nparts == 2 ? 8.0 : 2.0) * M.d * (double)M.d * M.d);
+    if (a.flops && threadIdx.x == 0 && it.y == 0 && it.z == 0 && it.w == 0) {
+      const double f = (a.nparts == 2 ? 8.0 : 2.0) * M.d * (double)M.d * M.d;
+      const int L = (a.lmax >= 2 && a.lmax <= 8) ? a.lmax : 8;
+      atomicAdd(a.flops, f);
+      if (a.dflops) atomicAdd(a.dflops, f * (L - 1) * L / 2);
+    }
     part = it.y;
     mt = it.z;
     nt = it.w;
@@ -610,6 +619,8 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
   const int g0 = ks * gpb, g1 = min(groups, g0 + gpb);
   if (g0 >= g1) return;  // the whole CTA leaves before any barrier or allocation
   const int c0 = g0 * GSTEPS, c1 = min(nch, g1 * GSTEPS);
+  const int Lm = (a.lmax >= 2 && a.lmax <= 8) ? a.lmax : 8;  // levels 2..Lm
+  const int nd = Lm - 1;                                    // digits used per operand
 
   if (tid == 0) {
     for (int i = 0; i < GNST; ++i) {
@@ -639,9 +650,9 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
         const unsigned char* xs = px + (size_t)a.sx[part][seg] * pxs + ((size_t)mt * kc + c) * GXST;
         const unsigned char* ys = py + (size_t)a.sy[part][seg] * pys + ((size_t)nt * kc + c) * GYST;
         unsigned char* dst = smem + s * GST;
-        tc::mbar_arrive_expect_tx(&full[s], GST);
-        tc::bulk_g2s(dst, xs, GXST, &full[s]);
-        tc::bulk_g2s(dst + GXST, ys, GYST, &full[s]);
+        tc::mbar_arrive_expect_tx(&full[s], (uint32_t)nd * (GXB + GYB));
+        tc::bulk_g2s(dst, xs, (uint32_t)nd * GXB, &full[s]);
+        tc::bulk_g2s(dst + GXST, ys, (uint32_t)nd * GYB, &full[s]);
       };
       constexpr uint32_t LBO = 128, SBO = (GKC / 8) * 128;
       for (int ch = c0; ch < c1 && !err; ++ch) {
@@ -673,13 +684,16 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
         const uint32_t sy = sx + GXST;
 #pragma unroll
         for (int p = 1; p <= oz::S; ++p) {
+          if (p > nd) break;
           const uint64_t ad = tc::sdesc(sx + (p - 1) * GXB, LBO, SBO);
 #pragma unroll
           for (int q0 = 1; q0 <= 8 - p; q0 += 4) {
-            const int nq = min(4, 8 - p - q0 + 1);
+            if (q0 > Lm - p) break;
+            const int nq = min(4, Lm - p - q0 + 1);
             const uint64_t bd = tc::sdesc(sy + (q0 - 1) * GYB, LBO, SBO);
             const uint32_t id = tc::idesc_bf16(oz::TM, oz::TN * nq);
-            // the first K step of a group starts every accumulator (p = 1 covers all 7)
+            // the first K step of a group starts every accumulator in use
+            // (p = 1 covers levels 2..Lm)
             tc::mma_bf16(tmem + (p + q0 - 2) * oz::TN, ad, bd, id, (first && p == 1) ? 0u : 1u);
           }
         }
@@ -716,6 +730,7 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
       tc::fence_after();
 #pragma unroll
       for (int q = 0; q < GNACC; ++q) {
+        if (q > Lm - 2) break;  // levels above Lm are not accumulated
         // level L = q + 2: value = k 2^-8L exactly with |k| < 2^24; k by the
         // FP32 -> int32 conversion (the 64-bit one runs on the FP64 unit)
         const int L = q + 2;
