@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/fm.h"
@@ -55,6 +56,10 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off) {
       for (int mt = 0; mt < M.mtn; ++mt)
         for (int nt = 0; nt < M.ntn; ++nt) g.items.push_back(make_int4(b, p, mt, nt));
   }
+  // the persistent tile kernel deals items round-robin: longest K first
+  std::stable_sort(g.items.begin(), g.items.end(), [&](const int4& x, const int4& y) {
+    return g.mats[x.x].kc > g.mats[y.x].kc;
+  });
   return g;
 }
 
@@ -136,6 +141,7 @@ class BRunner {
   long long* acc_ = nullptr;
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
   long long products_ = 0;
+  int sms_ = 1;
 
   long long launches_ = 0;
   void check(const char* where) {
@@ -198,7 +204,9 @@ class BRunner {
     a.store = 1;
     a.flops = &ctr_->flops;
     a.dflops = &ctr_->dflops;
-    grid::oz_tiles<<<(unsigned)g_.items.size(), grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
+    a.nitems = (int)g_.items.size();
+    const int ctas = a.nitems < sms_ ? a.nitems : sms_;  // persistent: one CTA per SM
+    grid::oz_tiles<<<ctas, grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
     check("tensor-core products");
     if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
     grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy_, e, out, emax, nullptr);
@@ -213,6 +221,12 @@ int BRunner<T>::run() {
   st_ = j.st;
   const int batch = j.batch;
   g_ = geometry(j.cplx, batch, j.d_host, j.off_host);
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev);
+    if (sms_ < 1) sms_ = 1;
+  }
   L_ = carve(g_, j.cplx, batch);
   if (j.ws_bytes < L_.total) {
     snprintf(msg_, len_, "batched grid path: workspace too small");

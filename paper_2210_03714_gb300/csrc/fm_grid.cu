@@ -246,7 +246,9 @@ class Runner {
     a.acc = acc_;
     a.err = &misc_->tc_err;
     memset0(acc_, (size_t)parts * Mp * Np * 16, "accumulator reset");
-    grid::oz_tiles<<<tiles * ksplit, grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
+    a.nitems = tiles * ksplit;
+    const int ctas = a.nitems < sms_ ? a.nitems : sms_;  // persistent: one CTA per SM
+    grid::oz_tiles<<<ctas, grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
     check("tensor-core product");
     grid::epilogue<T><<<blocks((size_t)M * N), kThreads, 0, st_>>>(
         M, N, acc_, parts, Mp, Np, ex_, fy_, nullptr, 0, e, out, ldo);

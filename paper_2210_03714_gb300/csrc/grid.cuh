@@ -559,8 +559,78 @@ struct OzTiles {
   int store;       // 1: plain stores into acc (one CTA per tile), 0: atomic adds
   double* flops;             // batch mode: product flops (2d^3, complex 8d^3) added, nullable
   double* dflops;            // batch mode: digit-pair flops (pairs kept x product flops), nullable
+  int nitems;                // work items: batch mode, the table's length; else parts x tiles x ksplit
 };
 
+// geometry of work item idx (a tile and K range) of a launch; valid = 0 for a
+// masked matrix or an empty K range
+struct TileGeo {
+  int valid, b, part, mt, nt, kc, mtn, ntn, c0, c1, dm;
+  const unsigned char* px;
+  const unsigned char* py;
+  size_t pxs, pys;
+  long long* acc;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const OzTiles& a, int idx) {
+  TileGeo G;
+  G.valid = 0;
+  int ks, ksplit;
+  if (a.items) {
+    const int4 it = a.items[idx];
+    G.b = it.x;
+    if (!a.mask[it.x]) return G;
+    const BMat& M = a.mats[it.x];
+    G.part = it.y;
+    G.mt = it.z;
+    G.nt = it.w;
+    ks = 0;
+    ksplit = 1;
+    G.mtn = M.mtn;
+    G.ntn = M.ntn;
+    G.kc = M.kc;
+    G.px = a.px + M.px;
+    G.py = a.py + M.py;
+    G.pxs = (size_t)G.mtn * G.kc * GXST;
+    G.pys = (size_t)G.ntn * G.kc * GYST;
+    G.acc = a.acc + M.acc * 2;
+    G.dm = M.d;
+  } else {
+    int item = idx;
+    G.b = 0;
+    ks = item % a.ksplit;
+    item /= a.ksplit;
+    G.nt = item % a.ntn;
+    item /= a.ntn;
+    G.mt = item % a.mtn;
+    G.part = item / a.mtn;
+    ksplit = a.ksplit;
+    G.mtn = a.mtn;
+    G.ntn = a.ntn;
+    G.kc = a.kc;
+    G.px = a.px;
+    G.py = a.py;
+    G.pxs = a.pxs;
+    G.pys = a.pys;
+    G.acc = a.acc;
+    G.dm = 1 << 30;
+  }
+  const int nch = a.nseg * G.kc;
+  const int groups = (nch + GSTEPS - 1) / GSTEPS;
+  const int gpb = (groups + ksplit - 1) / ksplit;
+  const int g0 = ks * gpb, g1 = min(groups, g0 + gpb);
+  if (g0 >= g1) return G;
+  G.c0 = g0 * GSTEPS;
+  G.c1 = min(nch, g1 * GSTEPS);
+  G.valid = 1;
+  return G;
+}
+
+// Persistent: CTA i takes work items i, i + gridDim.x, ... (largest first when
+// the host sorts them).  Warp 8 lane 0 walks the items' K chunks with two
+// cursors, one issuing bulk copies up to GNST chunks ahead (across item
+// boundaries) and one issuing the MMAs; warps 0-7 read the accumulators after
+// every group and write an item's sums after its last group.
 static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
   extern __shared__ unsigned char dsm[];
   __shared__ __align__(8) uint64_t full[GNST], empty[GNST], accf, accr;
@@ -568,57 +638,7 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
   __shared__ int s_err;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned char* smem = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
-  int ks, nt, mt, part, mtn, ntn, kc, ksplit;
-  const unsigned char *px, *py;
-  size_t pxs, pys;
-  long long* acc;
-  if (a.items) {
-    const int4 it = a.items[blockIdx.x];
-    if (!a.mask[it.x]) return;  // uniform: the whole CTA leaves
-    const BMat& M = a.mats[it.x];
-    if (a.flops && threadIdx.x == 0 && it.y == 0 && it.z == 0 && it.w == 0) {
-      const double f = (a.nparts == 2 ? 8.0 : 2.0) * M.d * (double)M.d * M.d;
-      const int L = (a.lmax >= 2 && a.lmax <= 8) ? a.lmax : 8;
-      atomicAdd(a.flops, f);
-      if (a.dflops) atomicAdd(a.dflops, f * (L - 1) * L / 2);
-    }
-    part = it.y;
-    mt = it.z;
-    nt = it.w;
-    ks = 0;
-    ksplit = 1;
-    mtn = M.mtn;
-    ntn = M.ntn;
-    kc = M.kc;
-    px = a.px + M.px;
-    py = a.py + M.py;
-    pxs = (size_t)mtn * kc * GXST;
-    pys = (size_t)ntn * kc * GYST;
-    acc = a.acc + M.acc * 2;
-  } else {
-    int item = blockIdx.x;
-    ks = item % a.ksplit;
-    item /= a.ksplit;
-    nt = item % a.ntn;
-    item /= a.ntn;
-    mt = item % a.mtn;
-    part = item / a.mtn;
-    mtn = a.mtn;
-    ntn = a.ntn;
-    kc = a.kc;
-    ksplit = a.ksplit;
-    px = a.px;
-    py = a.py;
-    pxs = a.pxs;
-    pys = a.pys;
-    acc = a.acc;
-  }
-  const int nch = a.nseg * kc;
-  const int groups = (nch + GSTEPS - 1) / GSTEPS;
-  const int gpb = (groups + ksplit - 1) / ksplit;
-  const int g0 = ks * gpb, g1 = min(groups, g0 + gpb);
-  if (g0 >= g1) return;  // the whole CTA leaves before any barrier or allocation
-  const int c0 = g0 * GSTEPS, c1 = min(nch, g1 * GSTEPS);
+  const int nitems = a.nitems;
   const int Lm = (a.lmax >= 2 && a.lmax <= 8) ? a.lmax : 8;  // levels 2..Lm
   const int nd = Lm - 1;                                    // digits used per operand
 
@@ -642,40 +662,54 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
     // ---- producer and MMA issuer (one thread) ----
     if (lane == 0) {
       int err = 0;
-      int issued = c0;          // next chunk to load
-      int mma_chunks = 0;       // chunks whose MMAs were issued
-      auto load = [&](int ch) {
-        const int s = (ch - c0) % GNST;
-        const int seg = ch / kc, c = ch % kc;
-        const unsigned char* xs = px + (size_t)a.sx[part][seg] * pxs + ((size_t)mt * kc + c) * GXST;
-        const unsigned char* ys = py + (size_t)a.sy[part][seg] * pys + ((size_t)nt * kc + c) * GYST;
-        unsigned char* dst = smem + s * GST;
-        tc::mbar_arrive_expect_tx(&full[s], (uint32_t)nd * (GXB + GYB));
-        tc::bulk_g2s(dst, xs, (uint32_t)nd * GXB, &full[s]);
-        tc::bulk_g2s(dst + GXST, ys, (uint32_t)nd * GYB, &full[s]);
-      };
+      // load cursor (idxL, chL, GL) and MMA cursor (idxM, chM, GM)
+      int idxL = blockIdx.x, idxM = blockIdx.x, chL = 0, chM = 0;
+      TileGeo GL, GM;
+      GL.valid = GM.valid = 0;
+      while (idxL < nitems && !(GL = tile_geo(a, idxL)).valid) idxL += gridDim.x;
+      if (idxL < nitems) chL = GL.c0;
+      idxM = idxL;
+      GM = GL;
+      chM = chL;
+      long long kL = 0, kM = 0;  // chunks loaded / multiplied by this CTA
+      long long gcount = 0;      // groups started
       constexpr uint32_t LBO = 128, SBO = (GKC / 8) * 128;
-      for (int ch = c0; ch < c1 && !err; ++ch) {
+      while (idxM < nitems && !err) {
         // keep up to GNST chunks in flight: a stage is refilled once the MMAs
         // of the chunk that used it (GNST chunks back) have finished
-        while (issued < c1 && issued < ch + GNST) {
-          const int k = issued - c0;
-          if (k >= GNST && !tc::mbar_wait(&empty[k % GNST], ((k / GNST) - 1) & 1, oz::WAIT)) {
+        while (idxL < nitems && kL < kM + GNST) {
+          if (kL >= GNST && !tc::mbar_wait(&empty[kL % GNST], ((kL / GNST) - 1) & 1, oz::WAIT)) {
             err = 1;
             break;
           }
-          load(issued);
-          ++issued;
+          const int s = (int)(kL % GNST);
+          const int seg = chL / GL.kc, c = chL % GL.kc;
+          const unsigned char* xs =
+              GL.px + (size_t)a.sx[GL.part][seg] * GL.pxs + ((size_t)GL.mt * GL.kc + c) * GXST;
+          const unsigned char* ys =
+              GL.py + (size_t)a.sy[GL.part][seg] * GL.pys + ((size_t)GL.nt * GL.kc + c) * GYST;
+          unsigned char* dst = smem + s * GST;
+          tc::mbar_arrive_expect_tx(&full[s], (uint32_t)nd * (GXB + GYB));
+          tc::bulk_g2s(dst, xs, (uint32_t)nd * GXB, &full[s]);
+          tc::bulk_g2s(dst + GXST, ys, (uint32_t)nd * GYB, &full[s]);
+          ++kL;
+          if (++chL == GL.c1) {
+            idxL += gridDim.x;
+            while (idxL < nitems && !(GL = tile_geo(a, idxL)).valid) idxL += gridDim.x;
+            if (idxL < nitems) chL = GL.c0;
+          }
         }
         if (err) break;
-        const int k = ch - c0, s = k % GNST;
-        const int gi = (ch / GSTEPS) - g0;  // group index within this CTA
-        const bool first = (ch % GSTEPS) == 0 || ch == c0;
-        if (first && gi > 0 && !tc::mbar_wait(&accr, (gi - 1) & 1, oz::WAIT)) {
-          err = 1;
-          break;
+        const int s = (int)(kM % GNST);
+        const bool first = (chM % GSTEPS) == 0 || chM == GM.c0;
+        if (first) {
+          if (gcount > 0 && !tc::mbar_wait(&accr, (uint32_t)((gcount - 1) & 1), oz::WAIT)) {
+            err = 1;
+            break;
+          }
+          ++gcount;
         }
-        if (!tc::mbar_wait(&full[s], (k / GNST) & 1, oz::WAIT)) {
+        if (!tc::mbar_wait(&full[s], (uint32_t)((kM / GNST) & 1), oz::WAIT)) {
           err = 1;
           break;
         }
@@ -698,73 +732,86 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
           }
         }
         tc::mma_commit(&empty[s]);
-        ++mma_chunks;
-        const bool last = ((ch + 1) % GSTEPS) == 0 || ch + 1 == c1;
+        ++kM;
+        const bool last = ((chM + 1) % GSTEPS) == 0 || chM + 1 == GM.c1;
         if (last) tc::mma_commit(&accf);
+        if (++chM == GM.c1) {
+          idxM += gridDim.x;
+          while (idxM < nitems && !(GM = tile_geo(a, idxM)).valid) idxM += gridDim.x;
+          if (idxM < nitems) chM = GM.c0;
+        }
       }
       if (err) {
         s_err = 1;
         atomicOr(a.err, 1);
       }
-      // drain before TMEM is freed: the copies still landing, and the last
-      // commit (it covers every MMA issued before it)
-      const int nl = issued - c0, nm = mma_chunks;
-      for (int k = max(0, nl - GNST); k < nl; ++k)
-        tc::mbar_wait(&full[k % GNST], (k / GNST) & 1, oz::WAIT);
-      if (nm > 0) tc::mbar_wait(&empty[(nm - 1) % GNST], ((nm - 1) / GNST) & 1, oz::WAIT);
+      // drain before TMEM is freed: every copy issued, and the last commit
+      // (it covers every MMA issued before it)
+      for (long long k = kM; k < kL; ++k)
+        tc::mbar_wait(&full[k % GNST], (uint32_t)((k / GNST) & 1), oz::WAIT);
+      if (kM > 0) tc::mbar_wait(&empty[(kM - 1) % GNST], (uint32_t)(((kM - 1) / GNST) & 1), oz::WAIT);
     }
   } else {
     // ---- readout warps ----
-    long long ahi[32], alo[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) ahi[j] = alo[j] = 0;
     const int colh = 32 * (warp >> 2);
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     bool ok = true;
-    for (int g = g0; g < g1; ++g) {
-      const int gi = g - g0;
-      if (!tc::mbar_wait(&accf, gi & 1, oz::WAIT)) {
-        ok = false;
-        break;
+    long long g = 0;  // groups read
+    for (int idx = blockIdx.x; idx < nitems && ok; idx += gridDim.x) {
+      const TileGeo G = tile_geo(a, idx);
+      if (!G.valid) continue;
+      if (a.flops && tid == 0 && G.part == 0 && G.mt == 0 && G.nt == 0 && G.c0 == 0) {
+        const double dd = (double)G.dm;
+        const double f = (a.nparts == 2 ? 8.0 : 2.0) * dd * dd * dd;
+        atomicAdd(a.flops, f);
+        if (a.dflops) atomicAdd(a.dflops, f * (Lm - 1) * Lm / 2);
       }
-      tc::fence_after();
+      long long ahi[32], alo[32];
 #pragma unroll
-      for (int q = 0; q < GNACC; ++q) {
-        if (q > Lm - 2) break;  // levels above Lm are not accumulated
-        // level L = q + 2: value = k 2^-8L exactly with |k| < 2^24; k by the
-        // FP32 -> int32 conversion (the 64-bit one runs on the FP64 unit)
-        const int L = q + 2;
-        const float sc = __int_as_float((127 + 8 * L) << 23);  // 2^(8L)
+      for (int j = 0; j < 32; ++j) ahi[j] = alo[j] = 0;
+      const int ng = (G.c1 - G.c0 + GSTEPS - 1) / GSTEPS;
+      for (int gg = 0; gg < ng; ++gg, ++g) {
+        if (!tc::mbar_wait(&accf, (uint32_t)(g & 1), oz::WAIT)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          uint32_t r[16];
-          tc::tmem_ld16(tmem + lane_base + q * oz::TN + colh + 16 * h, r);
-          tc::tmem_ld_wait();
+        for (int q = 0; q < GNACC; ++q) {
+          if (q > Lm - 2) break;  // levels above Lm are not accumulated
+          // level L = q + 2: value = k 2^-8L exactly with |k| < 2^24; k by the
+          // FP32 -> int32 conversion (the 64-bit one runs on the FP64 unit)
+          const int L = q + 2;
+          const float sc = __int_as_float((127 + 8 * L) << 23);  // 2^(8L)
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long k = __float2int_rz(__uint_as_float(r[j]) * sc);
-            if (q < 4) ahi[16 * h + j] += k << (40 - 8 * L);   // 2^-40 units
-            else alo[16 * h + j] += k << (64 - 8 * L);         // 2^-64 units
+          for (int h = 0; h < 2; ++h) {
+            uint32_t r[16];
+            tc::tmem_ld16(tmem + lane_base + q * oz::TN + colh + 16 * h, r);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const long long k = __float2int_rz(__uint_as_float(r[j]) * sc);
+              if (q < 4) ahi[16 * h + j] += k << (40 - 8 * L);   // 2^-40 units
+              else alo[16 * h + j] += k << (64 - 8 * L);         // 2^-64 units
+            }
           }
         }
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&accr);
       }
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&accr);
-    }
-    if (ok && !s_err) {
-      const int Mp = mtn * oz::TM, Np = ntn * oz::TN;
-      const int row = mt * oz::TM + 32 * (warp & 3) + lane;
+      if (!ok || s_err) break;
+      const int Mp = G.mtn * oz::TM, Np = G.ntn * oz::TN;
+      const int row = G.mt * oz::TM + 32 * (warp & 3) + lane;
       unsigned long long* dst =
-          (unsigned long long*)acc + (((size_t)part * Mp + row) * Np + nt * oz::TN + colh) * 2;
+          (unsigned long long*)G.acc + (((size_t)G.part * Mp + row) * Np + G.nt * oz::TN + colh) * 2;
       if (a.store) {
         // only the matrix's own rows and columns: the epilogue reads no others
-        const int dm = a.items ? a.mats[a.items[blockIdx.x].x].d : mtn * oz::TM;
-        const int col0 = nt * oz::TN + colh;
-        if (row < dm) {
+        const int col0 = G.nt * oz::TN + colh;
+        if (row < G.dm) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (col0 + j < dm) *(ulonglong2*)(dst + 2 * j) = make_ulonglong2(ahi[j], alo[j]);
+            if (col0 + j < G.dm) *(ulonglong2*)(dst + 2 * j) = make_ulonglong2(ahi[j], alo[j]);
         }
       } else {
 #pragma unroll
@@ -773,9 +820,8 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
           if (alo[j]) atomicAdd(dst + 2 * j + 1, (unsigned long long)alo[j]);
         }
       }
-    } else if (!ok && lane == 0) {
-      atomicOr(a.err, 1);
     }
+    if (!ok && lane == 0) atomicOr(a.err, 1);
   }
   tc::fence_before();
   __syncthreads();
