@@ -333,6 +333,47 @@ def run_e2e(args, fm, torch, flat, dims, cs, stream, barrier, max_over_ranks, wo
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+# ---- multi-rank host logic: one process per GPU, each running the whole batch
+# (weak scaling, no collective on the data path); the timing is the maximum
+# over ranks and the value counts every rank's matrices.
+def ranks_setup(backend):
+    """(world, rank, local rank) from the torchrun environment; joins the
+    process group when world > 1 (and selects the local GPU for nccl)."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def rank_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def rank_max(x, world, device):
+    """Largest x over the ranks (the step time the job is judged by)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, batch, ms):
+    """Matrices per second of the whole job: every rank's batch over the
+    slowest rank's step time."""
+    return world * batch / (ms / 1000.0)
+
+
 def main():
     global BATCH, DIMS, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -376,24 +417,14 @@ def main():
     import torch.distributed as dist
     import paper_2210_03714_gb300 as fm
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    world, rank, local = ranks_setup("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
 
     def barrier():
-        if world > 1:
-            dist.barrier()
+        rank_barrier(world)
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, world, dev)
 
     fm.lib()
     dims, norms, flat = make_batch()
@@ -431,7 +462,7 @@ def main():
     ms = max_over_ranks(sum(per) / len(per))
     bad = int((info != 0).sum().item())
     s_host = s.cpu().numpy()
-    value = world * BATCH / (ms / 1000.0)
+    value = whole_job_value(world, BATCH, ms)
 
     # the plain double form on the same GPU, same batch
     F64 = torch.empty_like(P.flat)
