@@ -227,6 +227,9 @@ struct Epi {
   // two (sign s*, exponent k*), and each output is summed exactly in 128-bit
   // fixed point and rounded once, without the FP64 unit
   int fx = 0, ka = 0, sa = 0, k1 = 0, s1 = 0, k2 = 0, s2 = 0;
+  // light form (fx = 2): alpha = 1 and b1, b2 = +-1 (or absent); P is rounded
+  // once and Z1, Z2 added with two double operations (m*: 1 add, 2 subtract)
+  int m1 = 0, m2 = 0;
 };
 
 // c = +-2^k
@@ -240,10 +243,17 @@ inline bool epi_pow2(double c, int* neg, int* k) {
   return true;
 }
 
-// select the integer form when every coefficient allows it (host)
+// select the light form, else the integer form, when the coefficients allow (host)
 inline void fixed_form(Epi& e) {
   e.fx = 0;
   if (e.ai != 0 || e.b1i != 0 || e.b2i != 0) return;
+  auto pm1 = [](const void* z, double b) { return !z ? 0 : (b == 1.0 ? 1 : (b == -1.0 ? 2 : -1)); };
+  e.m1 = pm1(e.Z1, e.b1r);
+  e.m2 = pm1(e.Z2, e.b2r);
+  if (e.ar == 1.0 && e.m1 >= 0 && e.m2 >= 0) {
+    e.fx = 2;
+    return;
+  }
   if (!epi_pow2(e.ar, &e.sa, &e.ka) || e.ka < -2) return;
   if (e.Z1 && !epi_pow2(e.b1r, &e.s1, &e.k1)) return;
   if (e.Z2 && !epi_pow2(e.b2r, &e.s2, &e.k2)) return;
@@ -255,7 +265,14 @@ inline void fixed_form(Epi& e) {
 __device__ __forceinline__ double epi_part(const Epi& e, long long hi, long long lo, int e2,
                                            bool h1, double z1, bool h2, double z2, bool diag,
                                            double g) {
-  if (e.fx) {
+  if (e.fx == 2) {
+    double v = oz::combine_scaled(hi, lo, e2);
+    if (e.m1) v = e.m1 == 1 ? __dadd_rn(v, z1) : __dsub_rn(v, z1);
+    if (e.m2) v = e.m2 == 1 ? __dadd_rn(v, z2) : __dsub_rn(v, z2);
+    if (diag && g != 0) v = __dadd_rn(v, g);
+    return v;
+  }
+  if (e.fx == 1) {
     const int u = e2 - 2;  // two fraction bits below the product's unit (alpha >= 1/4)
     __int128 S = (((__int128)hi << 24) + (__int128)lo) << 2;
     S = e.ka >= 0 ? (S << e.ka) : (S >> (-e.ka));

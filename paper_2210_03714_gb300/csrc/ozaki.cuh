@@ -98,14 +98,20 @@ __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out) {
     else if (sh > -63) q = (mant + (1LL << (-sh - 1))) >> (-sh);
   }
   const bool neg = bits < 0;
+  // signed digits from the bytes of q (lowest first): a byte plus the carry
+  // of 128 or more becomes byte - 256 and carries one into the next byte;
+  // 32-bit operations only
+  const unsigned int qlo = (unsigned int)q, qhi = (unsigned int)((unsigned long long)q >> 32);
   int d[S];
+  int carry = 0;
 #pragma unroll
-  for (int p = S - 1; p >= 1; --p) {
-    int v = (int)((q + 128) & 255) - 128;
-    d[p] = v;
-    q = (q - v) >> 8;
+  for (int i = 0; i < S - 1; ++i) {
+    const unsigned int w = i < 4 ? qlo : qhi;
+    const int t = (int)((w >> (8 * (i & 3))) & 255u) + carry;
+    carry = t >= 128;
+    d[S - 1 - i] = t - (carry << 8);
   }
-  d[0] = (int)q;
+  d[0] = (int)(qhi >> 16) + carry;  // q <= 2^56 (rounding may reach 2^56): at most 256
   // d_p 2^(-8p) without conversion instructions: 1.5 2^23 + d_p is exact in
   // FP32 (|d_p| <= 256), one FMA scales it by 2^(-8p) and removes the 1.5 2^23
   // exactly, and the value (at most 8 significant bits) is its own BF16
