@@ -151,6 +151,27 @@ def test_phi1_diffusion_sampled(fm, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_phi1_diffusion_full_batch(fm, prec):
+    """The full diffusion workload: 512 matrices of order 512 in one call;
+    every status 0, three results (first, middle, last) against the oracle
+    (same s, the bar of the sampled test)."""
+    import torch
+    mats, ts, u0, bb = wl.diffusion_batch(batch=512)
+    P = fm.Packed([torch.from_numpy(m) for m in mats], device="cuda")
+    Phi, E, info, s = fm.phi1_batched(P, T(ts), "R8", "R8_phi1", precision=prec)
+    torch.cuda.synchronize()
+    assert int((info != 0).sum().item()) == 0
+    s = s.cpu().numpy()
+    assert 11 <= s.min() and s.max() <= 17  # the doublings this workload needs
+    for b in (0, 255, 511):
+        Phi_ref, E_ref, s_ref, _ = oracle.phi1(mats[b], ts[b], "R8", "R8_phi1")
+        assert s[b] == s_ref
+        tol = max(TOL_FP64, 2.0 ** (int(s_ref) + 3 - 53))
+        assert relerr(P.get(Phi, b).cpu().numpy(), Phi_ref) <= tol
+        assert relerr(P.get(E, b).cpu().numpy(), E_ref) <= tol
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_phi1mv_diffusion_sampled(fm, prec):
     """u(t) = u0 + t phi1(tA)(A u0 + b) for the same workload.  The product
     phi1(tA) w with w = A u0 + b (dominated by the stiff modes that phi1
@@ -249,6 +270,35 @@ def test_adjoint_vs_oracle(fm):
         assert relerr(W[b * 128:(b + 1) * 128], w_fwd[b]) <= TOL_FP64
         assert relerr(Abar[b * 128 * 128:(b + 1) * 128 * 128].reshape(128, 128), Ab_ref) <= 1e-8
         assert relerr(vbar[b * 128:(b + 1) * 128], vb_ref) <= 1e-8
+
+
+def test_adjoint_full_batch(fm):
+    """The full gradient workload: 256 matrices of order 128 (N from each
+    matrix's norm), forward action and adjoint in one call each; three
+    results against the oracle (forward at 1e-12, gradients at 1e-8)."""
+    import torch
+    A, v, y = wl.grad_batch(batch=256)
+    theta = oracle.CS("R8").theta
+    Ns = [oracle.select_nsteps(np.abs(a).sum(0).max(), theta) for a in A]
+    cs = oracle_set("R8")
+    P = fm.Packed([T(a) for a in A])
+    W0, info0, N0 = fm.expmv_batched(P, T(v.ravel()), 1, 1.0, fm.Coeffs(cs), precision="fp64")
+    assert int((info0 != 0).sum().item()) == 0
+    assert [int(x) for x in N0.cpu().numpy()] == Ns
+    W0 = W0.cpu().numpy()
+    wbar = 2 * (W0 - y.ravel())
+    W, Abar, vbar, info = fm.expmv_adjoint_batched(P, T(v.ravel()), T(wbar), Ns, 1.0,
+                                                   fm.Coeffs(cs))
+    torch.cuda.synchronize()
+    assert int((info != 0).sum().item()) == 0
+    W, Abar, vbar = W.cpu().numpy(), Abar.cpu().numpy(), vbar.cpu().numpy()
+    d = 128
+    for b in (0, 128, 255):
+        w_ref, N_ref, _ = oracle.expmv(A[b], v[b], 1.0, cs, nsteps=Ns[b])
+        assert relerr(W[b * d:(b + 1) * d], w_ref) <= TOL_FP64
+        Ab_ref, vb_ref, _ = oracle.expmv_adjoint(A[b], v[b], wbar[b * d:(b + 1) * d], Ns[b], 1.0, cs)
+        assert relerr(Abar[b * d * d:(b + 1) * d * d].reshape(d, d), Ab_ref) <= 1e-8
+        assert relerr(vbar[b * d:(b + 1) * d], vb_ref) <= 1e-8
 
 
 def test_autograd_function_fd(fm):
