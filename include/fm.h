@@ -277,8 +277,9 @@ const char* fm_last_error(void);
  * real, 8MNK complex), the tensor-core flops of their digit products (the
  * digit pairs kept, 28 at full accuracy, per product flop; 0 on the FP64
  * pipe), and the largest
- * number of correction steps one shifted system took, and the number of kernel
- * launches of the call.  The library has no
+ * number of correction steps one shifted system took, the number of kernel
+ * launches of the call, and the summed CUDA-event time of its tensor-core tile
+ * launches (events recorded on the call's stream around each).  The library has no
  * counterpart in the paper; it serves measurement. */
 typedef struct {
   long long products;
@@ -286,6 +287,7 @@ typedef struct {
   double digit_flops;
   int corrections;
   long long launches;  /* kernels the call launched */
+  double tile_ms;      /* CUDA-event time of the tensor-core tile launches */
 } fm_stats;
 void fm_last_stats(fm_stats* out);
 

@@ -39,7 +39,7 @@ class fm_opts(C.Structure):
 class fm_stats(C.Structure):
     _fields_ = [("products", C.c_longlong), ("product_flops", C.c_double),
                 ("digit_flops", C.c_double), ("corrections", C.c_int),
-                ("launches", C.c_longlong)]
+                ("launches", C.c_longlong), ("tile_ms", C.c_double)]
 
 
 def last_stats():

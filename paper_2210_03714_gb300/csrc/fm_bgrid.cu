@@ -13,6 +13,7 @@
 #include "../../include/fm.h"
 #include "bgrid.cuh"
 #include "fm_bgrid.h"
+#include "fm_grid.h"
 
 namespace fmk {
 namespace {
@@ -142,6 +143,7 @@ class BRunner {
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
   long long products_ = 0;
   int sms_ = 1;
+  TileTimer timer_;
 
   long long launches_ = 0;
   void check(const char* where) {
@@ -206,7 +208,9 @@ class BRunner {
     a.dflops = &ctr_->dflops;
     a.nitems = (int)g_.items.size();
     const int ctas = a.nitems < sms_ ? a.nitems : sms_;  // persistent: one CTA per SM
+    timer_.start(st_);
     grid::oz_tiles<<<ctas, grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
+    timer_.stop(st_);
     check("tensor-core products");
     if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
     grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy_, e, out, emax, nullptr);
@@ -393,6 +397,7 @@ int BRunner<T>::run() {
     st->digit_flops = h.dflops;
     st->corrections = h.corrections;
     st->launches = launches_;
+    st->tile_ms = timer_.total_ms();
   }
   return FM_OK;
 }

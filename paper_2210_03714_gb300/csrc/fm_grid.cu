@@ -117,6 +117,7 @@ class Runner {
   long long* acc_ = nullptr;
   cudaError_t err_ = cudaSuccess;
   fm_stats* stats_ = nullptr;
+  TileTimer timer_;
 
   int blocks(size_t count) const {
     size_t b = (count + kThreads - 1) / kThreads;
@@ -248,7 +249,9 @@ class Runner {
     memset0(acc_, (size_t)parts * Mp * Np * 16, "accumulator reset");
     a.nitems = tiles * ksplit;
     const int ctas = a.nitems < sms_ ? a.nitems : sms_;  // persistent: one CTA per SM
+    timer_.start(st_);
     grid::oz_tiles<<<ctas, grid::GTHREADS, grid::GSMEM + 1024, st_>>>(a);
+    timer_.stop(st_);
     check("tensor-core product");
     grid::epilogue<T><<<blocks((size_t)M * N), kThreads, 0, st_>>>(
         M, N, acc_, parts, Mp, Np, ex_, fy_, nullptr, 0, e, out, ldo);
@@ -504,7 +507,10 @@ int Runner<T>::run() {
   Misc hf = read_misc();
   if (err_ != cudaSuccess) return FM_ECUDA;
   if (hf.tc_err) info = -7;
-  if (stats_) stats_->launches = launches_;
+  if (stats_) {
+    stats_->launches = launches_;
+    stats_->tile_ms = timer_.total_ms();
+  }
   return finish(info);
 }
 

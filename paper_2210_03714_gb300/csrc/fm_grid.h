@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "fm_job.h"
 
 namespace fmk {
@@ -37,6 +39,41 @@ struct GridJob {
   int* s_host;
   long* n_host;
   void* stats;  // fm_stats of the calling thread (written during the call)
+};
+
+// CUDA events around each tensor-core tile launch of a call; their times are
+// summed once the call has synchronized its stream
+struct TileTimer {
+  std::vector<cudaEvent_t> ev;  // start, stop pairs
+  bool open = false;
+  void start(cudaStream_t st) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    ev.push_back(a);
+    ev.push_back(b);
+    cudaEventRecord(a, st);
+    open = true;
+  }
+  void stop(cudaStream_t st) {
+    if (!open) return;
+    cudaEventRecord(ev.back(), st);
+    open = false;
+  }
+  double total_ms() const {  // after the stream is synchronized
+    double t = 0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) t += ms;
+    }
+    return t;
+  }
+  ~TileTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 // scratch bytes the grid path needs
