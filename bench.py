@@ -245,13 +245,18 @@ def run_single(args):
         pipe, flops = "tensor_bf16", st["digit_flops"]
     else:
         pipe, flops = "fp64", st["product_flops"]
-    ach = flops / (ms / 1000.0) / 1e12
-    roofline = {"bound": "tensor" if pipe == "tensor_bf16" else "alu", "pipe": pipe,
-                "achieved": ach, "peak": pk[pipe][0], "peak_source": pk[pipe][1],
+    step_ach = flops / (ms / 1000.0) / 1e12
+    kern_s = st["tile_ms"] / 1000.0
+    ach = flops / kern_s / 1e12 if (pipe == "tensor_bf16" and kern_s > 0) else step_ach
+    roofline = {"bound": "tensor" if pipe == "tensor_bf16" else "alu",
+                "kernel": "oz_tiles" if pipe == "tensor_bf16" else "all",
+                "pipe": pipe, "achieved": ach, "peak": pk[pipe][0], "peak_source": pk[pipe][1],
                 "unit": "TFLOP/s", "frac": ach / pk[pipe][0], "traffic": None,
-                "note": "all grid-path kernels of one call (products, splits, epilogues, "
-                        "elementwise) over the call's event time; flops = the digit products "
-                        "(pairs kept per product flop) or the double products"}
+                "kernel_ms": st["tile_ms"], "step_achieved": step_ach,
+                "step_frac": step_ach / pk[pipe][0],
+                "note": "tensor: digit-pair flops (pairs kept per product flop) over the tile "
+                        "launches' CUDA-event time; fp64: product flops over the call; step_* "
+                        "over the whole call"}
     diff = None
     fp64_ms = None
     if not args.no_fp64 and args.precision == "mixed":
