@@ -15,10 +15,6 @@
 namespace fmk {
 namespace grid {
 
-template <class T>
-__device__ __forceinline__ double max_re_im(T v) {
-  return fmax(fabs(El<T>::re(v)), fabs(El<T>::im(v)));
-}
 
 // block-wide maximum with NaN propagation; red: 32 doubles of shared memory
 __device__ __forceinline__ double block_max(double m, double* red) {

@@ -73,10 +73,6 @@ __device__ __forceinline__ unsigned long long abs_bits<zd>(zd v) {
   return a > b ? a : b;
 }
 
-__device__ __forceinline__ void max_bits(unsigned long long* dst, double v) {
-  // non-negative doubles order like their bit patterns
-  atomicMax(dst, (unsigned long long)__double_as_longlong(v));
-}
 
 // ---- a1: finiteness of A, B = t A (one rounding), column sums of |B| -------
 // One thread per column; rows in ascending order (the order of the one-CTA
@@ -521,10 +517,11 @@ __global__ void split_cols(int K, int N, const T* Y, int ldy, const unsigned lon
   }
 }
 
-// One work item per CTA: output tile (mt, nt) of part `part` over a range of
-// exact groups (112 values of the concatenated K).  The part's K runs over
-// nseg segments, segment g pairing X plane set sx[part][g] with Y plane set
-// sy[part][g] (complex: re = Xr Yr + Xi (-Yi), im = Xr Yi + Xi Yr).
+// Work item: output tile (mt, nt) of part `part` over a range of exact
+// groups (112 values of the concatenated K).  The part's K runs over nseg
+// segments, segment g pairing X plane set sx[part][g] with Y plane set
+// sy[part][g] (complex: re = Xr Yr + Xi (-Yi), im = Xr Yi + Xi Yr).  The
+// kernel is persistent: each CTA takes items blockIdx.x, + gridDim.x, ...
 //
 // Accumulator a (TMEM columns 64a .. 64a + 63) holds level L = a + 2 (digit
 // pairs p + q = L).  Bounds at K = 112 in units of the level (|d_1| <= 256,
@@ -567,13 +564,13 @@ struct OzTiles {
   int lmax;
   long long* acc;  // [part][mtn*128][ntn*64][2]: hi (2^-40 units), lo (2^-64 units)
   int* err;
-  // batch mode (items != nullptr): CTA i computes tile items[i] = (b, part, mt,
-  // nt) of matrix b over its whole K (ksplit 1), with the geometry and offsets
-  // of mats[b]; CTAs of matrices with mask[b] == 0 do nothing
+  // batch mode (items != nullptr): item i is tile items[i] = (b, part, mt, nt)
+  // of matrix b over its whole K (ksplit 1), with the geometry and offsets of
+  // mats[b]; items of matrices with mask[b] == 0 are skipped
   const int4* items;
   const BMat* mats;
   const int* mask;
-  int store;       // 1: plain stores into acc (one CTA per tile), 0: atomic adds
+  int store;       // 1: plain stores into acc (one item per tile), 0: atomic adds
   double* flops;             // batch mode: product flops (2d^3, complex 8d^3) added, nullable
   double* dflops;            // batch mode: digit-pair flops (pairs kept x product flops), nullable
   int nitems;                // work items: batch mode, the table's length; else parts x tiles x ksplit
