@@ -114,8 +114,8 @@ enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       
 /* Execution path.  FM_PATH_CTA: one thread block per matrix, every step in it
  * (LU with partial pivoting of each shifted matrix; d <= fm_max_dim()).
  * FM_PATH_GRID: every step is one launch over the whole GPU -- one matrix of
- * any order (single-matrix calls), or a whole batch of exp (batched exp,
- * dmax <= fm_max_dim()); each shifted system (I - c_i B) Y_i = c_i B is solved
+ * any order (single-matrix calls), or a whole batch (batched exp, phi_1 and
+ * phi_1 V, dmax <= fm_max_dim()); each shifted system (I - c_i B) Y_i = c_i B is solved
  * by the residual-correction (Newton-Schulz) iteration
  * Y <- Y + (I + Y)(C - (I - C) Y), C = c_i B, whose only heavy steps are matrix
  * products, until the largest residual entry times d is below 2^-30 (then one
@@ -126,9 +126,9 @@ enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       
  * forms the matrix r(B) once and applies it N times.  Calls on this path
  * synchronize their stream (s or N, the batch orders and the iteration counts
  * are read on the host).
- * FM_PATH_AUTO: single-matrix calls with d > fm_max_dim() and batched exp in
- * FM_FP32_IR with dmax >= 64 take the grid path, everything else the one-CTA
- * kernels. */
+ * FM_PATH_AUTO: single-matrix calls with d > fm_max_dim(), and batched exp,
+ * phi_1 and phi_1 V in FM_FP32_IR with dmax >= 64, take the grid path;
+ * everything else the one-CTA kernels. */
 enum { FM_PATH_AUTO = 0, FM_PATH_CTA = 1, FM_PATH_GRID = 2 };
 
 typedef struct {

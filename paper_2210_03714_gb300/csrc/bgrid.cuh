@@ -387,6 +387,27 @@ static __global__ void b_flags(int batch, const BMat* mats, const unsigned long 
   if (mask_e[b]) atomicAdd(active, 1);
 }
 
+// W_b = V_b + Psi_b V_b (Phi = I + Psi), V_b, W_b d x m at voff: double
+// products on the FP64 pipe (one product per call: O(d^2 m))
+template <class T>
+__global__ void b_apply(const BMat* mats, const int* mask, const T* Psi, const T* V, int m, T* W) {
+  if (!mask[blockIdx.x]) return;
+  const BMat M = mats[blockIdx.x];
+  const int n = M.d;
+  const int r0 = blockIdx.y * RB;
+  if (r0 >= n) return;
+  const int nr = min(RB, n - r0);
+  const T* Pb = Psi + M.off;
+  const T* Vb = V + M.voff;
+  T* Wb = W + M.voff;
+  for (int k = threadIdx.x; k < nr * m; k += blockDim.x) {
+    const int r = r0 + k / m, c = k % m;
+    T acc = Vb[(size_t)r * m + c];
+    for (int q = 0; q < n; ++q) Tr<T>::mac(acc, Pb[(size_t)r * n + q], Vb[(size_t)q * m + c]);
+    Wb[(size_t)r * m + c] = acc;
+  }
+}
+
 // info[b] = code for every live matrix
 static __global__ void b_set_info(int batch, const int* alive, int code, int* info) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;

@@ -275,32 +275,44 @@ fm_status run_grid(const Call& c, const fm_opts& o, cudaStream_t st) {
 
 // a batch of exp over the whole GPU (fm_bgrid.cu)
 fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
-  if (c.kind != JOB_EXPM)
-    return fail(FM_EINVAL, "the grid path takes batches of exp only (other batched jobs: FM_PATH_CTA)");
-  if (!c.A || !c.F || !c.d_dev || !c.off || !c.t_dev || !c.info_dev)
-    return fail(FM_EINVAL, "batched calls need A, F, d_dev, off_dev, t_dev and info_dev");
+  if (c.kind != JOB_EXPM && c.kind != JOB_PHI1 && c.kind != JOB_PHI1MV)
+    return fail(FM_EINVAL, "the grid path takes batches of exp and phi_1 (and phi_1 V) only; "
+                           "other batched jobs: FM_PATH_CTA");
+  const bool act = c.kind == JOB_PHI1MV;
+  if (!c.A || !c.d_dev || !c.off || !c.t_dev || !c.info_dev)
+    return fail(FM_EINVAL, "batched calls need A, d_dev, off_dev, t_dev and info_dev");
+  if (act ? (!c.V || !c.W || !c.voff || c.m < 1) : !c.F)
+    return fail(FM_EINVAL, "output (or V / W / voff_dev / m) missing");
   if (c.dmax < 1 || c.dmax > fm_max_dim()) return fail(FM_ESHAPE, "dmax must be in [1, fm_max_dim()]");
   BGridJob j;
   memset(&j, 0, sizeof j);
   fm_status s = pack(c.ce, c.cp, c.cplx, o.form, j.cf);
   if (s) return s;
   std::vector<int> d(c.batch);
-  std::vector<int64_t> off(c.batch);
+  std::vector<int64_t> off(c.batch), voff(act ? c.batch : 0);
   cudaError_t e = cudaMemcpyAsync(d.data(), c.d_dev, (size_t)c.batch * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(off.data(), c.off, (size_t)c.batch * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && act)
+    e = cudaMemcpyAsync(voff.data(), c.voff, (size_t)c.batch * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "reading the batch orders");
   for (int b = 0; b < c.batch; ++b)
     if (d[b] < 1 || d[b] > c.dmax) return fail(FM_ESHAPE, "a batch order is outside [1, dmax]");
+  j.kind = c.kind;
   j.cplx = c.cplx;
   j.form = o.form;
   j.batch = c.batch;
   j.d_host = d.data();
   j.off_host = off.data();
+  j.voff_host = act ? voff.data() : nullptr;
+  j.m = c.m;
   j.A = c.A;
   j.t_dev = c.t_dev;
   j.F = c.F;
+  j.E = c.E;
+  j.V = c.V;
+  j.W = c.W;
   j.info_dev = c.info_dev;
   j.s_dev = c.s_dev;
   j.anorm = o.anorm;
@@ -308,7 +320,7 @@ fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
   j.max_iters = 40;
   j.st = st;
   j.stats = &g_stats;
-  j.ws_bytes = bgrid_ws_bytes(c.cplx, c.batch, d.data());
+  j.ws_bytes = bgrid_ws_bytes(c.kind, c.cplx, c.batch, d.data());
   s = get_scratch(j.ws_bytes, &o, &j.ws, st);
   if (s) return s;
   return (fm_status)bgrid_run(j, g_err, sizeof g_err);
@@ -325,8 +337,9 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   if (o.path == FM_PATH_GRID && !single) return run_bgrid(c, o, st);
   // batches of exp in mixed precision with matrices of order 64 and up: the
   // grid path (tensor-core products over the whole batch) is the faster one
-  if (o.path == FM_PATH_AUTO && !single && c.kind == JOB_EXPM && o.precision != FM_FP64 &&
-      c.dmax >= 64 && c.dmax <= fm_max_dim())
+  if (o.path == FM_PATH_AUTO && !single &&
+      (c.kind == JOB_EXPM || c.kind == JOB_PHI1 || c.kind == JOB_PHI1MV) &&
+      o.precision != FM_FP64 && c.dmax >= 64 && c.dmax <= fm_max_dim())
     return run_bgrid(c, o, st);
   if (single && c.dmax >= 1 &&
       (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && c.dmax > fm_max_dim())))
@@ -462,12 +475,12 @@ size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_op
   if (batch == 1 && kind != JOB_ADJ &&
       (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && dmax > fm_max_dim())))
     return grid_ws_bytes(kind, cplx, o.precision, dmax, m);
+  const bool bg_kind = kind == JOB_EXPM || kind == JOB_PHI1 || kind == JOB_PHI1MV;
   if (batch > 1 && (o.path == FM_PATH_GRID ||
-                    (o.path == FM_PATH_AUTO && kind == JOB_EXPM && o.precision != FM_FP64 &&
-                     dmax >= 64))) {
-    if (kind != JOB_EXPM || dmax > fm_max_dim()) return 0;
+                    (o.path == FM_PATH_AUTO && bg_kind && o.precision != FM_FP64 && dmax >= 64))) {
+    if (!bg_kind || dmax > fm_max_dim()) return 0;
     std::vector<int> d(batch, dmax);
-    return bgrid_ws_bytes(cplx, batch, d.data());
+    return bgrid_ws_bytes(kind, cplx, batch, d.data());
   }
   if (dmax > fm_max_dim()) return 0;
   return make_plan(kind, cplx, o.precision, batch, dmax, m, k, nmax).total;

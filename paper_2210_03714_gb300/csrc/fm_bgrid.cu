@@ -29,7 +29,7 @@ struct Geo {
   long long rows = 0, cols = 0;
 };
 
-Geo geometry(bool cplx, int batch, const int* d, const int64_t* off) {
+Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64_t* voff) {
   Geo g;
   g.mats.resize(batch);
   const int parts = cplx ? 2 : 1;
@@ -42,6 +42,7 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off) {
     M.kc = (n + grid::GKC - 1) / grid::GKC;
     M.off = g.elems;
     M.uoff = off ? off[b] : 0;
+    M.voff = voff ? voff[b] : 0;
     M.px = g.pxb;
     M.py = g.pyb;
     M.acc = g.accp;
@@ -65,11 +66,11 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off) {
 }
 
 struct Lay {
-  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, C, Y, E, F, pxC, pxG, py,
-      acc, exC, exG, fy, total;
+  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, C, Y, E, F, F1, pxC,
+      pxG, py, acc, exC, exG, fy, total;
 };
 
-Lay carve(const Geo& g, bool cplx, int batch) {
+Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   Lay L;
   const size_t elt = cplx ? 16 : 8;
   size_t o = 0;
@@ -93,6 +94,7 @@ Lay carve(const Geo& g, bool cplx, int batch) {
   L.Y = take((size_t)g.elems * elt);
   L.E = take((size_t)g.elems * elt);
   L.F = take((size_t)g.elems * elt);
+  L.F1 = take(phi ? (size_t)g.elems * elt : 0);
   L.pxC = take((size_t)g.pxb);
   L.pxG = take((size_t)g.pxb);
   L.py = take((size_t)g.pyb);
@@ -137,7 +139,7 @@ class BRunner {
   double* prev_ = nullptr;
   dim3 gE_, gR_, gC_;  // grids: element slices, row slices, column slices
   Ctr* ctr_ = nullptr;
-  T *B_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr;
+  T *B_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr, *F1_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
   long long* acc_ = nullptr;
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
@@ -224,14 +226,15 @@ int BRunner<T>::run() {
   const BGridJob& j = j_;
   st_ = j.st;
   const int batch = j.batch;
-  g_ = geometry(j.cplx, batch, j.d_host, j.off_host);
+  const bool phi = j.kind == JOB_PHI1 || j.kind == JOB_PHI1MV;
+  g_ = geometry(j.cplx, batch, j.d_host, j.off_host, j.voff_host);
   {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev);
     if (sms_ < 1) sms_ = 1;
   }
-  L_ = carve(g_, j.cplx, batch);
+  L_ = carve(g_, j.cplx, batch, phi);
   if (j.ws_bytes < L_.total) {
     snprintf(msg_, len_, "batched grid path: workspace too small");
     return FM_ENOMEM;
@@ -252,6 +255,7 @@ int BRunner<T>::run() {
   Y_ = (T*)(base_ + L_.Y);
   E_ = (T*)(base_ + L_.E);
   F_ = (T*)(base_ + L_.F);
+  F1_ = phi ? (T*)(base_ + L_.F1) : nullptr;
   pxC_ = (unsigned char*)(base_ + L_.pxC);
   pxG_ = (unsigned char*)(base_ + L_.pxG);
   py_ = (unsigned char*)(base_ + L_.py);
@@ -301,22 +305,27 @@ int BRunner<T>::run() {
   int s_max = 0;
   for (int v : s_host) s_max = v > s_max ? v : s_max;
 
-  // a6 (first part): F = base I + d1 B + d2 B^2
-  double base = cf.a0[0];
-  if (j.form == 1)
-    for (int i = 0; i < cf.k; ++i)
-      if (!(cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) base -= cf.b_re[0][i];
-  grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base, F_);
-  check("initial combination");
-  if (cf.d1[0] != 0 || cf.d2[0] != 0) {
-    if (cf.d2[0] != 0) {
-      grid::Epi e;
-      prod(B_, pxG_, exG_, true, B_, e, E_, alive_, nullptr);
-    }
-    grid::b_hybrid<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.d1[0], B_, cf.d2[0],
-                                            cf.d2[0] != 0 ? E_ : nullptr, F_);
-    check("hybrid terms");
+  // a6 (first part): F_f = base_f I + d1 B + d2 B^2 for each function
+  const int nf = phi ? 2 : 1;
+  for (int f = 0; f < nf; ++f) {
+    double base = cf.a0[f];
+    if (j.form == 1)
+      for (int i = 0; i < cf.k; ++i)
+        if (!(cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) base -= cf.b_re[f][i];
+    grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base, f ? F1_ : F_);
+    check("initial combination");
   }
+  const bool need_b2 = cf.d2[0] != 0 || (phi && cf.d2[1] != 0);
+  if (need_b2) {
+    grid::Epi e;
+    prod(B_, pxG_, exG_, true, B_, e, E_, alive_, nullptr);
+  }
+  for (int f = 0; f < nf; ++f)
+    if (cf.d1[f] != 0 || cf.d2[f] != 0) {
+      grid::b_hybrid<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.d1[f], B_, cf.d2[f],
+                                              cf.d2[f] != 0 ? E_ : nullptr, f ? F1_ : F_);
+      check("hybrid terms");
+    }
 
   // a3-a6: the shifted systems, ascending i
   for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
@@ -363,25 +372,56 @@ int BRunner<T>::run() {
       api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
       if (h.active == 0) break;
     }
-    grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[0][i], cf.b_im[0][i], Y_,
-                                                j.form == 1, F_);
-    check("combination");
+    for (int f = 0; f < nf; ++f) {
+      grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[f][i], cf.b_im[f][i], Y_,
+                                                  j.form == 1, f ? F1_ : F_);
+      check("combination");
+    }
   }
   if (err_ != cudaSuccess) return FM_ECUDA;
 
-  // a7: s squarings of F = I + E
+  // a7 in the deviation from the identity: E = F - I (and Psi = F1 - I)
   grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F_, -1.0, E_, 0);
   check("deviation");
+  if (phi) {
+    grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F1_, -1.0, F1_, 0);
+    check("deviation");
+  }
   for (int q = 0; q < s_max; ++q) {
     grid::b_square_mask<<<nb, 256, 0, st_>>>(batch, alive_, s_, q, mask_s_);
     check("squaring mask");
+    if (phi) {
+      // (Phi, E) <- ((E + I) Phi / 2, E^2):  Psi <- Psi + E/2 + E Psi / 2
+      grid::Epi e1;
+      e1.ar = 0.5;
+      e1.Z1 = F1_;
+      e1.b1r = 1.0;
+      e1.Z2 = E_;
+      e1.b2r = 0.5;
+      prod(E_, pxG_, exG_, true, F1_, e1, F1_, mask_s_, nullptr);
+    }
+    // E <- 2E + E E (the row planes of E are already there for phi_1)
     grid::Epi e;
     e.Z1 = E_;
     e.b1r = 2.0;
-    prod(E_, pxG_, exG_, true, E_, e, E_, mask_s_, nullptr);
+    prod(E_, pxG_, exG_, !phi, E_, e, E_, mask_s_, nullptr);
   }
-  grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.F, 1);
-  check("output");
+  if (j.kind == JOB_EXPM) {
+    grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.F, 1);
+    check("output");
+  } else {
+    if (j.kind == JOB_PHI1) {
+      grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F1_, 1.0, (T*)j.F, 1);
+      check("output");
+      if (j.E) {
+        grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.E, 1);
+        check("output");
+      }
+    } else {  // W = Phi V = V + Psi V
+      grid::b_apply<T><<<gR_, NT, 0, st_>>>(mats_, alive_, F1_, (const T*)j.V, j.m, (T*)j.W);
+      check("phi_1 action");
+    }
+  }
   const Ctr h = read_ctr();
   if (err_ != cudaSuccess) return FM_ECUDA;
   if (h.err) {  // a tensor-core wait timed out: every result of the call is invalid
@@ -404,9 +444,9 @@ int BRunner<T>::run() {
 
 }  // namespace
 
-size_t bgrid_ws_bytes(bool cplx, int batch, const int* d_host) {
-  Geo g = geometry(cplx, batch, d_host, nullptr);
-  return carve(g, cplx, batch).total;
+size_t bgrid_ws_bytes(int kind, bool cplx, int batch, const int* d_host) {
+  Geo g = geometry(cplx, batch, d_host, nullptr, nullptr);
+  return carve(g, cplx, batch, kind == JOB_PHI1 || kind == JOB_PHI1MV).total;
 }
 
 int bgrid_run(const BGridJob& j, char* msg, size_t len) {

@@ -10,6 +10,7 @@
 namespace fmk {
 
 struct BGridJob {
+  int kind;                // JOB_EXPM, JOB_PHI1 or JOB_PHI1MV
   bool cplx;
   int form;
   int batch;
@@ -17,7 +18,12 @@ struct BGridJob {
   const int64_t* off_host; // element offsets of the caller's matrices (host copy)
   const void* A;           // packed input (device)
   const double* t_dev;
-  void* F;                 // packed output (device, same offsets)
+  void* F;                 // packed output (device, same offsets): exp or phi_1
+  void* E;                 // phi_1: exp output (nullable), same offsets
+  const void* V;           // phi_1 action: V_b (d_b x m) at voff_host[b]
+  void* W;                 // phi_1 action: W_b = phi_1(t_b A_b) V_b, same offsets
+  const int64_t* voff_host;
+  int m;
   int* info_dev;
   int* s_dev;              // nullable
   double anorm;
@@ -31,10 +37,11 @@ struct BGridJob {
 };
 
 // scratch bytes for a batch of these orders
-size_t bgrid_ws_bytes(bool cplx, int batch, const int* d_host);
+size_t bgrid_ws_bytes(int kind, bool cplx, int batch, const int* d_host);
 
-// runs exp(t_b A_b) for the whole batch; synchronizes the stream (the step
-// counts are read back between launches).  Returns an fm_status value.
+// runs exp(t_b A_b) (or phi_1, or phi_1 times V) for the whole batch;
+// synchronizes the stream (the step counts are read back between launches).
+// Returns an fm_status value.
 int bgrid_run(const BGridJob& j, char* msg, size_t len);
 
 }  // namespace fmk

@@ -548,6 +548,7 @@ struct BMat {
   long long acc;        // offset, in (hi, lo) pairs, of its accumulators
   int eo, fo;           // offsets of its rows (mtn*128) and columns (ntn*64) in the
                         // exponent and maximum arrays
+  long long voff;       // element offset of its block of vectors V / W (d x m), actions
 };
 
 struct OzTiles {

@@ -126,3 +126,32 @@ def test_bgrid_full_size_sampled(fm):
         ref, s_ref, _ = oracle.expm(mats[b], 1.0, "R8")
         assert s[b] == s_ref
         assert relerr(P.get(F, b).cpu().numpy(), ref) <= TOL_FP64, (b, dims[b])
+
+
+def test_bgrid_phi1_and_action(fm):
+    """phi_1 and exp from one set of corrections (two weight vectors), the
+    doublings as paired products, and W = phi_1(tA) V, on a ragged batch."""
+    import torch
+    dims = [3, 40, 100, 130, 200]
+    rng = np.random.default_rng(9)
+    mats = [wl.dense_scaled(d, 3.0, 900 + d) for d in dims]
+    ts = rng.uniform(0.5, 1.0, len(dims))
+    ce, cp = oracle_set("R8"), oracle_set("R8_phi1")
+    P = fm.Packed([T(m) for m in mats])
+    Phi, E, info, s = fm.phi1_batched(P, T(ts), fm.Coeffs(ce), fm.Coeffs(cp), path="grid")
+    Phi, E, info, s = Phi.cpu().numpy(), E.cpu().numpy(), info.cpu().numpy(), s.cpu().numpy()
+    m = 3
+    V = rng.standard_normal(sum(dims) * m)
+    W, info2, s2 = fm.phi1mv_batched(P, T(V), m, T(ts), fm.Coeffs(ce), fm.Coeffs(cp), path="grid")
+    W, info2 = W.cpu().numpy(), info2.cpu().numpy()
+    o = 0
+    for b, (M, t) in enumerate(zip(mats, ts)):
+        Phi_ref, E_ref, s_ref, _ = oracle.phi1(M, t, ce, cp)
+        assert info[b] == 0 and s[b] == s_ref and info2[b] == 0
+        assert relerr(P.get(Phi, b), Phi_ref) <= TOL_FP64
+        assert relerr(P.get(E, b), E_ref) <= TOL_FP64
+        d = dims[b]
+        Vb = V[o:o + d * m].reshape(d, m)
+        W_ref, _, _ = oracle.phi1mv(M, Vb, t, ce, cp)
+        assert relerr(W[o:o + d * m].reshape(d, m), W_ref) <= TOL_FP64
+        o += d * m

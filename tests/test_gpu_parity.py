@@ -127,8 +127,8 @@ def test_phi1_small(fm, prec):
     assert relerr(E.cpu().numpy(), E_ref) <= TOL_FP64
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_phi1_diffusion_sampled(fm, prec):
+@pytest.mark.parametrize("prec,path", PREC_PATH)
+def test_phi1_diffusion_sampled(fm, prec, path):
     """A = -L + 0.1 N (d = 512, stiff; s = 11..17 doublings): phi1(tA) and
     exp(tA) for a batch of 16 of the 512-matrix workload, two results against
     the oracle.  s doublings multiply the relative rounding of r(B) (about u)
@@ -139,7 +139,7 @@ def test_phi1_diffusion_sampled(fm, prec):
     import torch
     mats, ts, u0, bb = wl.diffusion_batch(batch=16)
     P = fm.Packed([torch.from_numpy(m) for m in mats], device="cuda")
-    Phi, E, info, s = fm.phi1_batched(P, T(ts), "R8", "R8_phi1", precision=prec)
+    Phi, E, info, s = fm.phi1_batched(P, T(ts), "R8", "R8_phi1", precision=prec, path=path)
     assert int((info != 0).sum().item()) == 0
     s = s.cpu().numpy()
     for b in (0, 7):
@@ -171,8 +171,8 @@ def test_phi1_diffusion_full_batch(fm, prec):
         assert relerr(P.get(E, b).cpu().numpy(), E_ref) <= tol
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_phi1mv_diffusion_sampled(fm, prec):
+@pytest.mark.parametrize("prec,path", PREC_PATH)
+def test_phi1mv_diffusion_sampled(fm, prec, path):
     """u(t) = u0 + t phi1(tA)(A u0 + b) for the same workload.  The product
     phi1(tA) w with w = A u0 + b (dominated by the stiff modes that phi1
     damps) has condition kappa = ||phi1|| ||w|| / ||phi1 w||; errors are
@@ -182,7 +182,8 @@ def test_phi1mv_diffusion_sampled(fm, prec):
     mats, ts, u0, bb = wl.diffusion_batch(batch=16)
     rhs = np.stack([M @ u + b for M, u, b in zip(mats, u0, bb)])
     P = fm.Packed([torch.from_numpy(m) for m in mats], device="cuda")
-    W, info, s = fm.phi1mv_batched(P, T(rhs.ravel()), 1, T(ts), "R8", "R8_phi1", precision=prec)
+    W, info, s = fm.phi1mv_batched(P, T(rhs.ravel()), 1, T(ts), "R8", "R8_phi1", precision=prec,
+                                   path=path)
     assert int((info != 0).sum().item()) == 0
     W = W.cpu().numpy().reshape(16, 512)
     s = s.cpu().numpy()
