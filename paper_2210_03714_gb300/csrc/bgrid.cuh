@@ -124,6 +124,17 @@ __global__ void b_hybrid(const BMat* mats, const int* mask, double d1, const T* 
   }
 }
 
+// X = alpha B + beta B2: the right-hand side of a fused +-c pair,
+// alpha = (b+ - b-) c, beta = (b+ + b-) c^2 (complex weights)
+template <class T>
+__global__ void b_pair_rhs(const BMat* mats, const int* mask, double ar, double ai, const T* B,
+                           double br, double bi, const T* B2, T* X) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+    X[M.off + e] = Tr<T>::add(cmul<T>(ar, ai, B[M.off + e]), cmul<T>(br, bi, B2[M.off + e]));
+}
+
 // F += b Y (roundoff form) or b (I + Y) (plain form)
 template <class T>
 __global__ void b_accumulate(const BMat* mats, const int* mask, double br, double bi, const T* Y,

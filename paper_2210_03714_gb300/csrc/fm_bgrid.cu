@@ -66,8 +66,8 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 }
 
 struct Lay {
-  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, C, Y, E, F, F1, pxC,
-      pxG, py, acc, exC, exG, fy, total;
+  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, B2, C, Y, E, F, F1,
+      pxC, pxG, py, acc, exC, exG, fy, total;
 };
 
 Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
@@ -90,6 +90,7 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.prev = take((size_t)batch * 8);
   L.ctr = take(64);
   L.B = take((size_t)g.elems * elt);
+  L.B2 = take((size_t)g.elems * elt);
   L.C = take((size_t)g.elems * elt);
   L.Y = take((size_t)g.elems * elt);
   L.E = take((size_t)g.elems * elt);
@@ -139,7 +140,8 @@ class BRunner {
   double* prev_ = nullptr;
   dim3 gE_, gR_, gC_;  // grids: element slices, row slices, column slices
   Ctr* ctr_ = nullptr;
-  T *B_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr, *F1_ = nullptr;
+  T *B_ = nullptr, *B2_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
+    *F1_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
   long long* acc_ = nullptr;
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
@@ -173,6 +175,52 @@ class BRunner {
 
   // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
   // row planes of X into px (else reuse those already there)
+  // Y = (I - C)^-1 C by residual correction from Y = C, for every live matrix:
+  // E = C Y + C - Y, then Y = Y E + Y + E (the product at the digit levels
+  // its accuracy needs), until the largest residual entry times d is below
+  // 2^-30 (then one more correction)
+  void correct(int dmax, int nb) {
+    const int batch = j_.batch;
+    api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
+        "mask copy");
+    for (int it = 0; err_ == cudaSuccess; ++it) {
+      api(cudaMemsetAsync(&ctr_->active, 0, 4, st_), "counter reset");
+      grid::Epi e1;
+      e1.Z1 = C_;
+      e1.b1r = 1.0;
+      e1.Z2 = Y_;
+      e1.b2r = -1.0;
+      prod(C_, pxC_, exC_, it == 0, Y_, e1, E_, mask_e_, emax_);
+      grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, it, j_.max_iters, mask_e_,
+                                         mask_u_, j_.info_dev, &ctr_->active, &ctr_->corrections,
+                                         &ctr_->emax);
+      check("correction flags");
+      const Ctr h = read_ctr();
+      if (err_ != cudaSuccess) break;
+      // Y E needs an absolute accuracy of about u max|Y| only, and its error is
+      // about 2^(14 - 8 Lmax) 8 sqrt(d) max|Y| max|E|: keep the digit-pair
+      // levels that bound requires
+      double em;
+      memcpy(&em, &h.emax, sizeof em);
+      int lmax = 8;
+      if (em > 0 && em < 1) {
+        const double need = 70.0 + 0.5 * log2((double)dmax) + log2(em);
+        lmax = (int)ceil(need / 8.0);
+        lmax = lmax < 2 ? 2 : (lmax > 8 ? 8 : lmax);
+      }
+      grid::Epi e2;
+      e2.Z1 = Y_;
+      e2.b1r = 1.0;
+      e2.Z2 = E_;
+      e2.b2r = 1.0;
+      // first correction: Y = C, whose row planes are already in pxC
+      if (it == 0) prod(Y_, pxC_, exC_, false, E_, e2, Y_, mask_u_, nullptr, lmax);
+      else prod(Y_, pxG_, exG_, true, E_, e2, Y_, mask_u_, nullptr, lmax);
+      api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
+      if (h.active == 0) break;
+    }
+  }
+
   void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp,
             const grid::Epi& e_in, T* out, const int* mask, unsigned long long* emax,
             int lmax = 8) {
@@ -251,6 +299,7 @@ int BRunner<T>::run() {
   prev_ = (double*)(base_ + L_.prev);
   ctr_ = (Ctr*)(base_ + L_.ctr);
   B_ = (T*)(base_ + L_.B);
+  B2_ = (T*)(base_ + L_.B2);
   C_ = (T*)(base_ + L_.C);
   Y_ = (T*)(base_ + L_.Y);
   E_ = (T*)(base_ + L_.E);
@@ -315,67 +364,73 @@ int BRunner<T>::run() {
     grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base, f ? F1_ : F_);
     check("initial combination");
   }
-  const bool need_b2 = cf.d2[0] != 0 || (phi && cf.d2[1] != 0);
+  // pairs (+c, -c) of the roundoff form share one system (Sec. 1: one product
+  // and one inverse per pair): b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
+  //   = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
+  std::vector<int> partner(cf.k, -1);
+  bool any_pair = false;
+  if (j.form == 0)
+    for (int i = 0; i < cf.k; ++i) {
+      if (partner[i] >= 0 || (cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) continue;
+      for (int q = i + 1; q < cf.k; ++q)
+        if (partner[q] < 0 && cf.c_re[q] == -cf.c_re[i] && cf.c_im[q] == -cf.c_im[i]) {
+          partner[i] = q;
+          partner[q] = i;
+          any_pair = true;
+          break;
+        }
+    }
+  const bool need_b2 = cf.d2[0] != 0 || (phi && cf.d2[1] != 0) || any_pair;
   if (need_b2) {
     grid::Epi e;
-    prod(B_, pxG_, exG_, true, B_, e, E_, alive_, nullptr);
+    prod(B_, pxG_, exG_, true, B_, e, B2_, alive_, nullptr);
   }
   for (int f = 0; f < nf; ++f)
     if (cf.d1[f] != 0 || cf.d2[f] != 0) {
       grid::b_hybrid<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.d1[f], B_, cf.d2[f],
-                                              cf.d2[f] != 0 ? E_ : nullptr, f ? F1_ : F_);
+                                              cf.d2[f] != 0 ? B2_ : nullptr, f ? F1_ : F_);
       check("hybrid terms");
     }
 
-  // a3-a6: the shifted systems, ascending i
+  // a3-a6: the shifted systems (and fused pairs), ascending first index
   for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
     const double cr = cf.c_re[i], ci = cf.c_im[i];
     if (cr == 0.0 && ci == 0.0) continue;
-    grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, cr, ci, C_, Y_);
-    check("shift");
-    api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
-        "mask copy");
-    for (int it = 0; err_ == cudaSuccess; ++it) {
-      api(cudaMemsetAsync(&ctr_->active, 0, 4, st_), "counter reset");
-      // E = C Y + C - Y, largest entry per matrix
-      grid::Epi e1;
-      e1.Z1 = C_;
-      e1.b1r = 1.0;
-      e1.Z2 = Y_;
-      e1.b2r = -1.0;
-      prod(C_, pxC_, exC_, it == 0, Y_, e1, E_, mask_e_, emax_);
-      grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, it, j.max_iters, mask_e_,
-                                         mask_u_, j.info_dev, &ctr_->active, &ctr_->corrections,
-                                         &ctr_->emax);
-      check("correction flags");
-      const Ctr h = read_ctr();
-      if (err_ != cudaSuccess) break;
-      // Y = Y E + Y + E.  The product Y E needs an absolute accuracy of about
-      // u max|Y| only, and its error is about 2^(14 - 8 Lmax) 8 sqrt(d)
-      // max|Y| max|E|: keep the digit-pair levels that bound requires.
-      double em;
-      memcpy(&em, &h.emax, sizeof em);
-      int lmax = 8;
-      if (em > 0 && em < 1) {
-        const double need = 70.0 + 0.5 * log2((double)dmax) + log2(em);
-        lmax = (int)ceil(need / 8.0);
-        lmax = lmax < 2 ? 2 : (lmax > 8 ? 8 : lmax);
-      }
-      grid::Epi e2;
-      e2.Z1 = Y_;
-      e2.b1r = 1.0;
-      e2.Z2 = E_;
-      e2.b2r = 1.0;
-      // first correction: Y = C, whose row planes are already in pxC
-      if (it == 0) prod(Y_, pxC_, exC_, false, E_, e2, Y_, mask_u_, nullptr, lmax);
-      else prod(Y_, pxG_, exG_, true, E_, e2, Y_, mask_u_, nullptr, lmax);
-      api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
-      if (h.active == 0) break;
+    if (partner[i] >= 0 && partner[i] < i) continue;  // done with its partner
+    const int q = partner[i];
+    if (q > i) {
+      // C = c^2 B^2
+      grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B2_, cr * cr - ci * ci,
+                                                  2.0 * cr * ci, C_, Y_);
+    } else {
+      grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, cr, ci, C_, Y_);
     }
+    check("shift");
+    correct(dmax, nb);  // Y = (I - C)^-1 C
+    if (err_ != cudaSuccess) break;
     for (int f = 0; f < nf; ++f) {
-      grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[f][i], cf.b_im[f][i], Y_,
-                                                  j.form == 1, f ? F1_ : F_);
-      check("combination");
+      T* Ff = f ? F1_ : F_;
+      if (q > i) {
+        // F += X + Z X with Z = Y = (I - c^2 B^2)^-1 - I and
+        // X = (b+ - b-) c B + (b+ + b-) c^2 B^2 (written over C)
+        const double pr = cf.b_re[f][i], pim = cf.b_im[f][i];
+        const double mr = cf.b_re[f][q], mim = cf.b_im[f][q];
+        const double dr = pr - mr, di = pim - mim, sr = pr + mr, si = pim + mim;
+        const double c2r = cr * cr - ci * ci, c2i = 2.0 * cr * ci;
+        grid::b_pair_rhs<T><<<gE_, NT, 0, st_>>>(mats_, alive_, dr * cr - di * ci, dr * ci + di * cr, B_,
+                                                  sr * c2r - si * c2i, sr * c2i + si * c2r, B2_, C_);
+        check("pair right-hand side");
+        grid::Epi e;
+        e.Z1 = Ff;
+        e.b1r = 1.0;
+        e.Z2 = C_;
+        e.b2r = 1.0;
+        prod(Y_, pxG_, exG_, f == 0, C_, e, Ff, alive_, nullptr);
+      } else {
+        grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[f][i], cf.b_im[f][i], Y_,
+                                                    j.form == 1, Ff);
+        check("combination");
+      }
     }
   }
   if (err_ != cudaSuccess) return FM_ECUDA;
