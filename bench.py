@@ -3,14 +3,15 @@
 
 Workload (one step): 4096 real dense matrices, d drawn uniformly from
 {16, 32, ..., 256}, entries N(0,1)/sqrt(d), each scaled to ||A||_1 ~ U[0.5, 8];
-the R8 set (8 shifted solves, Sec. 4.2) with scaling and squaring.  A step is
-one fm_expm_batched call over the whole batch (norm, s, scaling, 8 factor +
-solve + refinement + combination per matrix, s squarings).
+the R8 set (8 nonzero nodes, Sec. 4.2) with scaling and squaring.  A step is
+one fm_expm_batched call over the whole batch (norm, s, scaling, B^2, the four
++-c node pairs as one system I - c^2 B^2 each, the combination, s squarings).
 
 Printed: one JSON line (rank 0).  value = matrices per second of the mixed
-precision form (single-precision factorizations + refinement to double
-accuracy); the plain double form is timed in the same run (fp64_value) and the
-largest relative difference between the two over the batch is reported.
+precision form (batched grid path: each system solved by residual correction,
+every product a double-accurate BF16 digit product on the tensor cores); the
+double form (one-CTA path, FP64 LU) is timed in the same run (fp64_value) and
+the largest relative difference between the two over the batch is reported.
 Inputs (784 MB) are larger than L2 (129 MB), so no flush is needed between steps.
 
 --impl reference times the CPU oracle (oracle/, plain C, FP64) on a bounded
@@ -30,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "batched f(A)/f(A)V evals/sec at ≤1e-12 rel err, mixed vs FP64 GPU; % roofline"
 WORKLOAD = ("batched expm: 4096 real dense matrices, d uniform in {16,32,...,256}, "
-            "entries N(0,1)/sqrt(d), ||A||_1 ~ U[0.5,8], R8 coefficient set (k=8 shifted solves)")
+            "entries N(0,1)/sqrt(d), ||A||_1 ~ U[0.5,8], R8 coefficient set (8 nodes: 4 +-c pairs)")
 BATCH = 4096
 SEED = 1000
 DIMS = tuple(range(16, 257, 16))
@@ -108,32 +109,36 @@ def make_batch():
 
 
 def method_flops(dims, s):
-    """Algorithmic flops of one evaluation (per matrix) in the paper's count: k = 8
-    shifted LU + d-RHS solves at 8/3 d^3 each (Sec. 1: "8/3 d^3 flops") and s
-    squarings at 2 d^3."""
+    """Algorithmic flops of one evaluation (per matrix): B^2 once (2 d^3), then
+    the R8 nodes +-c as 4 pairs, each one system I - c^2 B^2 factored and solved
+    with d right-hand sides (Sec. 1: 8/3 d^3 per inverse, one inverse per pair),
+    and s squarings at 2 d^3."""
     import numpy as np
     d3 = np.asarray(dims, dtype=np.float64) ** 3
-    return float(np.sum(8 * (8.0 / 3.0) * d3 + 2.0 * np.asarray(s, dtype=np.float64) * d3))
+    return float(np.sum((2.0 + 4 * (8.0 / 3.0)) * d3 + 2.0 * np.asarray(s, dtype=np.float64) * d3))
 
 
-def pipe_work(dims, s, precision, k=8, max_ir=2, digits=7):
+def pipe_work(dims, s, precision, systems=4, max_ir=2, digits=7):
     """Algorithmic work of the persistent kernel per pipe, per launch (flops).
 
-    double path: every factorization, solve and squaring on the FP64 pipe
-      (k (2/3 + 2) d^3 + 2 s d^3).
-    mixed path: FP32 pipe: k factorizations (2/3 d^3) and 1 + max_ir solves with
-      d right-hand sides (2 d^3 each); tensor pipe (BF16 digit products):
-      k max_ir residual products and s squarings, each digits (digits+1)/2 = 28
-      digit-pair products of 2 d^3.
+    R8 in the roundoff form: its 8 nonzero nodes are 4 pairs +-c, each solved as
+    one system I - c^2 B^2 (one factorization, d right-hand sides), after one
+    product B^2.
+    double path: every product, factorization, solve and squaring on the FP64
+      pipe (2 d^3 + systems (2/3 + 2) d^3 + 2 s d^3).
+    mixed path: FP32 pipe: the factorizations (2/3 d^3) and 1 + max_ir solves
+      with d right-hand sides (2 d^3 each); tensor pipe (BF16 digit products):
+      B^2, systems * max_ir residual products and s squarings, each
+      digits (digits+1)/2 = 28 digit-pair products of 2 d^3.
     Elementwise work is O(d^2) and left out."""
     import numpy as np
     d3 = np.asarray(dims, dtype=np.float64) ** 3
     sv = np.asarray(s, dtype=np.float64)
     if precision == "fp64":
-        return {"fp64": float(np.sum(k * (8.0 / 3.0) * d3 + 2.0 * sv * d3))}
+        return {"fp64": float(np.sum((2.0 + systems * (8.0 / 3.0)) * d3 + 2.0 * sv * d3))}
     pairs = digits * (digits + 1) // 2
-    return {"fp32": float(np.sum(k * (2.0 / 3.0 + 2.0 * (1 + max_ir)) * d3)),
-            "tensor_bf16": float(np.sum((k * max_ir + sv) * pairs * 2.0 * d3))}
+    return {"fp32": float(np.sum(systems * (2.0 / 3.0 + 2.0 * (1 + max_ir)) * d3)),
+            "tensor_bf16": float(np.sum((1 + systems * max_ir + sv) * pairs * 2.0 * d3))}
 
 
 def pipe_peaks(peaks):
@@ -540,10 +545,12 @@ def main():
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": (st["launches"] if grid_path else 2) * args.steps,
-            "gpu_launches_note": ("per step: the grid path's launches (splits, tile products, "
-                                  "epilogues, elementwise), as counted by the library"
+            "gpu_launches_note": ("over the timed steps: the grid path's launches per step "
+                                  "(splits, tile products, epilogues, elementwise), as counted "
+                                  "by the library, times the steps"
                                   if grid_path else
-                                  "per step: the batch-ordering kernel and the persistent kernel"),
+                                  "over the timed steps: per step the batch-ordering kernel and "
+                                  "the persistent kernel"),
             "status_nonzero": bad,
             "fp64_value": (world * BATCH / (fp64_ms / 1000.0)) if fp64_ms else None,
             "fp64_ms_per_step": fp64_ms,

@@ -28,7 +28,9 @@
  *    status goes to info (device int per matrix, or the optional info_host of the
  *    single-matrix calls after a synchronize):
  *        0       success
- *        > 0     exactly zero pivot: (term index i) * d + (1-based column)
+ *        > 0     exactly zero pivot: (term index i) * d + (1-based column);
+ *                in the roundoff form a pair of nodes +c, -c is one system
+ *                I - c^2 B^2 and reports the index of its first node
  *        -1      mixed precision: iterative refinement did not reach opts.ir_tol
  *        -2      non-finite entry in A (or V, or t)
  *  - Outputs must not alias inputs.

@@ -32,7 +32,7 @@ size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 int rnd(int x, int q) { return (x + q - 1) / q * q; }
 
 struct Layout {
-  size_t B, C, Y, E, F0, F1, Tm, colsum, misc, rmax, cmax, ex, fy, px, py, acc, total;
+  size_t B, C, Y, E, F0, F1, B2, Tm, colsum, misc, rmax, cmax, ex, fy, px, py, acc, total;
   size_t pxs, pys;
 };
 
@@ -56,6 +56,7 @@ Layout layout(int kind, bool cplx, int precision, int d, int m) {
   L.E = take(nn);
   L.F0 = take(nn);
   L.F1 = take(kind == JOB_PHI1 || kind == JOB_PHI1MV ? nn : 0);
+  L.B2 = take(nn);
   L.Tm = take(precision == 0 ? (size_t)d * w * elt : 0);
   L.colsum = take((size_t)d * 8);
   L.misc = take(256);
@@ -108,7 +109,7 @@ class Runner {
   Layout L_;
   char* base_ = nullptr;
   T *B_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F0_ = nullptr, *F1_ = nullptr,
-    *Tm_ = nullptr;
+    *B2_ = nullptr, *Tm_ = nullptr;
   double* colsum_ = nullptr;
   Misc* misc_ = nullptr;
   unsigned long long *rmax_ = nullptr, *cmax_ = nullptr;
@@ -292,6 +293,7 @@ int Runner<T>::run() {
   E_ = (T*)(base_ + L_.E);
   F0_ = (T*)(base_ + L_.F0);
   F1_ = phi ? (T*)(base_ + L_.F1) : nullptr;
+  B2_ = (T*)(base_ + L_.B2);
   Tm_ = tcp_ ? nullptr : (T*)(base_ + L_.Tm);
   colsum_ = (double*)(base_ + L_.colsum);
   misc_ = (Misc*)(base_ + L_.misc);
@@ -381,23 +383,48 @@ int Runner<T>::run() {
       for (int i = 0; i < cf.k; ++i)
         if (!(cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) base[f] -= cf.b_re[f][i];
   // (plain form: a zero node's term b_i/(1 - 0) = b_i stays in base)
-  bool need_b2 = cf.d2[0] != 0 || (phi && cf.d2[1] != 0);
+  // pairs (+c, -c) of the roundoff form share one system (Sec. 1: one
+  // product and one inverse per pair):
+  //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
+  //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
+  int partner[kMaxTerms];
+  bool any_pair = false;
+  for (int i = 0; i < cf.k; ++i) partner[i] = -1;
+  if (g.form == 0)
+    for (int i = 0; i < cf.k; ++i) {
+      if (partner[i] >= 0 || (cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) continue;
+      for (int q = i + 1; q < cf.k; ++q)
+        if (partner[q] < 0 && cf.c_re[q] == -cf.c_re[i] && cf.c_im[q] == -cf.c_im[i]) {
+          partner[i] = q;
+          partner[q] = i;
+          any_pair = true;
+          break;
+        }
+    }
+  const bool need_b2 = cf.d2[0] != 0 || (phi && cf.d2[1] != 0) || any_pair;
   if (need_b2) {
     grid::Epi e;
-    prod(n, n, n, B_, n, true, B_, n, e, E_, n);
+    prod(n, n, n, B_, n, true, B_, n, e, B2_, n);
   }
   for (int f = 0; f < nf; ++f) {
     grid::init_f<T><<<blocks(nn), kThreads, 0, st_>>>(n, base[f], cf.d1[f], B_, cf.d2[f],
-                                                       need_b2 ? E_ : nullptr, f ? F1_ : F0_);
+                                                       need_b2 ? B2_ : nullptr, f ? F1_ : F0_);
     check("initial combination");
   }
 
-  // a3-a5: every shifted system, ascending i; a6: F_f += b_i Y_i
+  // a3-a5: every shifted system (or fused pair), ascending first index;
+  // a6: F_f += b_i Y_i
   const double stop = ldexp(1.0, -30) / (double)n;
   for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
     const double cr = cf.c_re[i], ci = cf.c_im[i];
     if (cr == 0.0 && ci == 0.0) continue;
-    grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, cr, ci, C_, Y_);
+    const int pq = partner[i];
+    if (pq >= 0 && pq < i) continue;  // done with its partner
+    const double c2r = cr * cr - ci * ci, c2i = 2.0 * cr * ci;
+    if (pq > i)  // C = c^2 B^2
+      grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B2_, c2r, c2i, C_, Y_);
+    else
+      grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, cr, ci, C_, Y_);
     check("shift");
     double prev = INFINITY;
     for (int it = 0;; ++it) {
@@ -441,10 +468,30 @@ int Runner<T>::run() {
       prod(n, n, n, Y_, n, true, E_, n, e2, Y_, n, lmax);
       if (em <= stop) break;  // the residual after this correction is ~em^2
     }
-    for (int f = 0; f < nf; ++f) {
-      grid::accumulate<T><<<blocks(nn), kThreads, 0, st_>>>(n, cf.b_re[f][i], cf.b_im[f][i], Y_,
-                                                           g.form == 1, f ? F1_ : F0_);
-      check("combination");
+    for (int f = 0; f < nf && err_ == cudaSuccess; ++f) {
+      T* Ff = f ? F1_ : F0_;
+      if (pq > i) {
+        // F += X + Y X with Y = (I - c^2 B^2)^-1 - I and
+        // X = (b+ - b-) c B + (b+ + b-) c^2 B^2 (written over C)
+        const double dr = cf.b_re[f][i] - cf.b_re[f][pq], di = cf.b_im[f][i] - cf.b_im[f][pq];
+        const double sr = cf.b_re[f][i] + cf.b_re[f][pq], si = cf.b_im[f][i] + cf.b_im[f][pq];
+        grid::pair_rhs<T><<<blocks(nn), kThreads, 0, st_>>>(
+            nn, dr * cr - di * ci, dr * ci + di * cr, B_, sr * c2r - si * c2i, sr * c2i + si * c2r,
+            B2_, C_);
+        check("pair right-hand side");
+        grid::Epi e;
+        e.Z1 = Ff;
+        e.ld1 = n;
+        e.b1r = 1.0;
+        e.Z2 = C_;
+        e.ld2 = n;
+        e.b2r = 1.0;
+        prod(n, n, n, Y_, n, f == 0, C_, n, e, Ff, n);
+      } else {
+        grid::accumulate<T><<<blocks(nn), kThreads, 0, st_>>>(n, cf.b_re[f][i], cf.b_im[f][i], Y_,
+                                                             g.form == 1, Ff);
+        check("combination");
+      }
     }
   }
   if (err_ != cudaSuccess) return FM_ECUDA;

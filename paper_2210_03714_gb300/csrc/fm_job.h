@@ -66,7 +66,7 @@ FM_HD size_t fm_align(size_t x) { return (x + 255) & ~(size_t)255; }
 // of the factorization type TL.  Offsets are computed identically on the host
 // (to size the buffer) and on the device (to carve it).
 struct WsLayout {
-  size_t B, C, Y, F, Phi, T1, T2, LU, RL, piv, D;   // matrix-function part
+  size_t B, C, Y, F, Phi, T1, T2, B2, LU, RL, piv, D;  // matrix-function part
   size_t Cs, LUs, pivs, Ds, Wc, Wn, U, U2, RHS;    // action part
   size_t Wst, Yst, Lam, Yt;                        // adjoint part
   size_t gx, gy, ex, fy;                           // digit planes (tensor-core products)
@@ -99,6 +99,7 @@ FM_HD WsLayout ws_layout(int kind, int n, int m, int k, size_t elt, size_t lelt,
     L.F = take(nn * elt);
     L.Phi = take(nn * elt);
     L.T2 = take(nn * elt);
+    L.B2 = take(nn * elt);
     L.LU = take(nn * lelt);
     L.piv = take((size_t)n * 4);
   } else {

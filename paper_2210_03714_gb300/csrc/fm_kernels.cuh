@@ -238,15 +238,34 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   }
   __syncthreads();
   const bool hyb = cf.d1[0] != 0 || cf.d2[0] != 0 || (two && (cf.d1[1] != 0 || cf.d2[1] != 0));
-  bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0);
-  if (need_b2) terr |= prod<T>(oc, n, n, n, B, n, B, n, T1, n, smem);
+  // pairs (+c, -c) of the roundoff form share one system (Sec. 1: one
+  // product and one inverse per pair):
+  //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
+  //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
+  signed char partner[kMaxTerms];
+  bool any_pair = false;
+  for (int i = 0; i < cf.k; ++i) partner[i] = -1;
+  if (J.form == 0)
+    for (int i = 0; i < cf.k; ++i) {
+      if (partner[i] >= 0 || (cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) continue;
+      for (int q = i + 1; q < cf.k; ++q)
+        if (partner[q] < 0 && cf.c_re[q] == -cf.c_re[i] && cf.c_im[q] == -cf.c_im[i]) {
+          partner[i] = (signed char)q;
+          partner[q] = (signed char)i;
+          any_pair = true;
+          break;
+        }
+    }
+  T* B2 = (T*)(ws + L.B2);
+  const bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0) || any_pair;
+  if (need_b2) terr |= prod<T>(oc, n, n, n, B, n, B, n, B2, n, smem);
   for (int e = tid; e < n * n; e += NT) {
     int r = e / n, c = e % n;
     for (int f = 0; f < (two ? 2 : 1); ++f) {
       T v = TT::rscale(tdiag<T>(r, c), base[f]);
       if (hyb) {
         if (cf.d1[f] != 0) v = TT::add(v, TT::rscale(B[e], cf.d1[f]));
-        if (cf.d2[f] != 0) v = TT::add(v, TT::rscale(T1[e], cf.d2[f]));
+        if (cf.d2[f] != 0) v = TT::add(v, TT::rscale(B2[e], cf.d2[f]));
       }
       (f == 0 ? F : Ph)[e] = v;
     }
@@ -270,7 +289,33 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
       }
       continue;
     }
+    const int pq = partner[i];
+    if (pq >= 0 && pq < i) continue;  // solved with its partner
     any_shift = true;
+    if (pq > i) {
+      // one system I - C' with C' = c^2 B^2; per function the right-hand
+      // side X = (b+ - b-) c B + (b+ + b-) c^2 B^2, and F += (I - C')^-1 X
+      const double c2r = cre * cre - cim * cim, c2i = 2.0 * cre * cim;
+      build_shift<T, TL>(n, c2r, c2i, B2, C, LU, D, mixed);
+      int fi = cta_getrf<TL, NB>(n, LU, n, piv, (TL*)smem);
+      if (fi) { info = i * n + fi; break; }
+      for (int f = 0; f < (two ? 2 : 1); ++f) {
+        const double dr = cf.b_re[f][i] - cf.b_re[f][pq], di = cf.b_im[f][i] - cf.b_im[f][pq];
+        const double sr = cf.b_re[f][i] + cf.b_re[f][pq], si = cf.b_im[f][i] + cf.b_im[f][pq];
+        const double ar = dr * cre - di * cim, ai = dr * cim + di * cre;
+        const double br = sr * c2r - si * c2i, bi = sr * c2i + si * c2r;
+        for (int e = tid; e < n * n; e += NT)
+          T1[e] = TT::add(wmul<T>(ar, ai, B[e]), wmul<T>(br, bi, B2[e]));
+        __syncthreads();
+        double q = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL,
+                                            smem, oc, &terr);
+        qmax = fmax(qmax, q);
+        T* Fx = f == 0 ? F : Ph;
+        for (int e = tid; e < n * n; e += NT) Fx[e] = TT::add(Fx[e], Y[e]);
+        __syncthreads();
+      }
+      continue;
+    }
     build_shift<T, TL>(n, cre, cim, B, C, LU, D, mixed);
     int fi = cta_getrf<TL, NB>(n, LU, n, piv, (TL*)smem);
     if (fi) { info = i * n + fi; break; }

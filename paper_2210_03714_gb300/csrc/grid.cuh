@@ -148,6 +148,15 @@ __global__ void build_shift(size_t count, const T* B, double cr, double ci, T* C
   }
 }
 
+// X = a B + b B2 (the right-hand side of a fused +-c pair)
+template <class T>
+__global__ void pair_rhs(size_t count, double ar, double ai, const T* B, double br, double bi,
+                         const T* B2, T* X) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+       e += (size_t)gridDim.x * blockDim.x)
+    X[e] = Tr<T>::add(cmul<T>(ar, ai, B[e]), cmul<T>(br, bi, B2[e]));
+}
+
 // F (n x n, ld n) = base I + d1 B + d2 B2   (B2 nullable when d2 == 0)
 template <class T>
 __global__ void init_f(int n, double base, double d1, const T* B, double d2, const T* B2, T* F) {
