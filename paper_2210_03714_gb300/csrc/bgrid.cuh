@@ -124,15 +124,21 @@ __global__ void b_hybrid(const BMat* mats, const int* mask, double d1, const T* 
   }
 }
 
-// X = alpha B + beta B2: the right-hand side of a fused +-c pair,
-// alpha = (b+ - b-) c, beta = (b+ + b-) c^2 (complex weights)
+// a fused +-c pair with Y = (I - c^2 B^2)^-1 - I:
+//   (I + Y)(a B + b' B^2) = a B + a Y B + (b'/c^2) Y,  a = (b+ - b-) c, b'/c^2 = b+ + b-
+// F += (b+ + b-) Y here and G += a Y (G = a Y for the first pair); the terms
+// a B and G B are added once, after the last pair, by one product
 template <class T>
-__global__ void b_pair_rhs(const BMat* mats, const int* mask, double ar, double ai, const T* B,
-                           double br, double bi, const T* B2, T* X) {
+__global__ void b_pair_acc(const BMat* mats, const int* mask, double sr, double si, double ar,
+                           double ai, const T* Y, int first, T* F, T* G) {
   FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
 #pragma unroll 4
-  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-    X[M.off + e] = Tr<T>::add(cmul<T>(ar, ai, B[M.off + e]), cmul<T>(br, bi, B2[M.off + e]));
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const T y = Y[M.off + e];
+    F[M.off + e] = Tr<T>::add(F[M.off + e], cmul<T>(sr, si, y));
+    const T g = cmul<T>(ar, ai, y);
+    G[M.off + e] = first ? g : Tr<T>::add(G[M.off + e], g);
+  }
 }
 
 // F += b Y (roundoff form) or b (I + Y) (plain form)

@@ -67,7 +67,7 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 
 struct Lay {
   size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, B2, C, Y, E, F, F1,
-      pxC, pxG, py, acc, exC, exG, fy, total;
+      G, pxC, pxG, py, acc, exC, exG, fy, total;
 };
 
 Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
@@ -96,6 +96,7 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.E = take((size_t)g.elems * elt);
   L.F = take((size_t)g.elems * elt);
   L.F1 = take(phi ? (size_t)g.elems * elt : 0);
+  L.G = take((size_t)(phi ? 2 : 1) * g.elems * elt);
   L.pxC = take((size_t)g.pxb);
   L.pxG = take((size_t)g.pxb);
   L.py = take((size_t)g.pyb);
@@ -141,7 +142,7 @@ class BRunner {
   dim3 gE_, gR_, gC_;  // grids: element slices, row slices, column slices
   Ctr* ctr_ = nullptr;
   T *B_ = nullptr, *B2_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
-    *F1_ = nullptr;
+    *F1_ = nullptr, *G_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
   long long* acc_ = nullptr;
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
@@ -305,6 +306,7 @@ int BRunner<T>::run() {
   E_ = (T*)(base_ + L_.E);
   F_ = (T*)(base_ + L_.F);
   F1_ = phi ? (T*)(base_ + L_.F1) : nullptr;
+  G_ = (T*)(base_ + L_.G);
   pxC_ = (unsigned char*)(base_ + L_.pxC);
   pxG_ = (unsigned char*)(base_ + L_.pxG);
   py_ = (unsigned char*)(base_ + L_.py);
@@ -364,9 +366,10 @@ int BRunner<T>::run() {
     grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base, f ? F1_ : F_);
     check("initial combination");
   }
-  // pairs (+c, -c) of the roundoff form share one system (Sec. 1: one product
-  // and one inverse per pair): b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
-  //   = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
+  // pairs (+c, -c) of the roundoff form share one system, as Sec. 1 pairs
+  // complex-conjugate roots (one product, x^2, and one inverse per pair):
+  //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
+  //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
   std::vector<int> partner(cf.k, -1);
   bool any_pair = false;
   if (j.form == 0)
@@ -393,6 +396,8 @@ int BRunner<T>::run() {
     }
 
   // a3-a6: the shifted systems (and fused pairs), ascending first index
+  bool pair_seen = false;
+  double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
   for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
     const double cr = cf.c_re[i], ci = cf.c_im[i];
     if (cr == 0.0 && ci == 0.0) continue;
@@ -411,27 +416,36 @@ int BRunner<T>::run() {
     for (int f = 0; f < nf; ++f) {
       T* Ff = f ? F1_ : F_;
       if (q > i) {
-        // F += X + Z X with Z = Y = (I - c^2 B^2)^-1 - I and
-        // X = (b+ - b-) c B + (b+ + b-) c^2 B^2 (written over C)
+        // (I + Y)((b+ - b-) c B + (b+ + b-) c^2 B^2) = a B + a Y B + (b+ + b-) Y
+        // with Y = (I - c^2 B^2)^-1 - I, a = (b+ - b-) c: F += (b+ + b-) Y now,
+        // G += a Y, and a B + G B after the last pair
         const double pr = cf.b_re[f][i], pim = cf.b_im[f][i];
         const double mr = cf.b_re[f][q], mim = cf.b_im[f][q];
-        const double dr = pr - mr, di = pim - mim, sr = pr + mr, si = pim + mim;
-        const double c2r = cr * cr - ci * ci, c2i = 2.0 * cr * ci;
-        grid::b_pair_rhs<T><<<gE_, NT, 0, st_>>>(mats_, alive_, dr * cr - di * ci, dr * ci + di * cr, B_,
-                                                  sr * c2r - si * c2i, sr * c2i + si * c2r, B2_, C_);
-        check("pair right-hand side");
-        grid::Epi e;
-        e.Z1 = Ff;
-        e.b1r = 1.0;
-        e.Z2 = C_;
-        e.b2r = 1.0;
-        prod(Y_, pxG_, exG_, f == 0, C_, e, Ff, alive_, nullptr);
+        const double dr = pr - mr, di = pim - mim;
+        const double ar = dr * cr - di * ci, ai = dr * ci + di * cr;
+        grid::b_pair_acc<T><<<gE_, NT, 0, st_>>>(mats_, alive_, pr + mr, pim + mim, ar, ai, Y_,
+                                                  !pair_seen, Ff, G_ + (size_t)f * g_.elems);
+        check("pair combination");
+        asum_r[f] += ar;
+        asum_i[f] += ai;
       } else {
         grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[f][i], cf.b_im[f][i], Y_,
                                                     j.form == 1, Ff);
         check("combination");
       }
     }
+    if (q > i) pair_seen = true;
+  }
+  // the pairs' a B + G B: one product per function, F = G B + F + (sum a) B
+  for (int f = 0; f < nf && pair_seen && err_ == cudaSuccess; ++f) {
+    T* Ff = f ? F1_ : F_;
+    grid::Epi e;
+    e.Z1 = Ff;
+    e.b1r = 1.0;
+    e.Z2 = B_;
+    e.b2r = asum_r[f];
+    e.b2i = asum_i[f];
+    prod(G_ + (size_t)f * g_.elems, pxG_, exG_, true, B_, e, Ff, alive_, nullptr);
   }
   if (err_ != cudaSuccess) return FM_ECUDA;
 

@@ -32,7 +32,7 @@ size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 int rnd(int x, int q) { return (x + q - 1) / q * q; }
 
 struct Layout {
-  size_t B, C, Y, E, F0, F1, B2, Tm, colsum, misc, rmax, cmax, ex, fy, px, py, acc, total;
+  size_t B, C, Y, E, F0, F1, B2, G, Tm, colsum, misc, rmax, cmax, ex, fy, px, py, acc, total;
   size_t pxs, pys;
 };
 
@@ -57,6 +57,7 @@ Layout layout(int kind, bool cplx, int precision, int d, int m) {
   L.F0 = take(nn);
   L.F1 = take(kind == JOB_PHI1 || kind == JOB_PHI1MV ? nn : 0);
   L.B2 = take(nn);
+  L.G = take((kind == JOB_PHI1 || kind == JOB_PHI1MV ? 2 : 1) * nn);
   L.Tm = take(precision == 0 ? (size_t)d * w * elt : 0);
   L.colsum = take((size_t)d * 8);
   L.misc = take(256);
@@ -109,7 +110,7 @@ class Runner {
   Layout L_;
   char* base_ = nullptr;
   T *B_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F0_ = nullptr, *F1_ = nullptr,
-    *B2_ = nullptr, *Tm_ = nullptr;
+    *B2_ = nullptr, *G_ = nullptr, *Tm_ = nullptr;
   double* colsum_ = nullptr;
   Misc* misc_ = nullptr;
   unsigned long long *rmax_ = nullptr, *cmax_ = nullptr;
@@ -294,6 +295,7 @@ int Runner<T>::run() {
   F0_ = (T*)(base_ + L_.F0);
   F1_ = phi ? (T*)(base_ + L_.F1) : nullptr;
   B2_ = (T*)(base_ + L_.B2);
+  G_ = (T*)(base_ + L_.G);
   Tm_ = tcp_ ? nullptr : (T*)(base_ + L_.Tm);
   colsum_ = (double*)(base_ + L_.colsum);
   misc_ = (Misc*)(base_ + L_.misc);
@@ -383,8 +385,8 @@ int Runner<T>::run() {
       for (int i = 0; i < cf.k; ++i)
         if (!(cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) base[f] -= cf.b_re[f][i];
   // (plain form: a zero node's term b_i/(1 - 0) = b_i stays in base)
-  // pairs (+c, -c) of the roundoff form share one system (Sec. 1: one
-  // product and one inverse per pair):
+  // pairs (+c, -c) of the roundoff form share one system, as Sec. 1 pairs
+  // complex-conjugate roots (one product, x^2, and one inverse per pair):
   //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
   //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
   int partner[kMaxTerms];
@@ -415,6 +417,8 @@ int Runner<T>::run() {
   // a3-a5: every shifted system (or fused pair), ascending first index;
   // a6: F_f += b_i Y_i
   const double stop = ldexp(1.0, -30) / (double)n;
+  bool pair_seen = false;
+  double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
   for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
     const double cr = cf.c_re[i], ci = cf.c_im[i];
     if (cr == 0.0 && ci == 0.0) continue;
@@ -471,28 +475,37 @@ int Runner<T>::run() {
     for (int f = 0; f < nf && err_ == cudaSuccess; ++f) {
       T* Ff = f ? F1_ : F0_;
       if (pq > i) {
-        // F += X + Y X with Y = (I - c^2 B^2)^-1 - I and
-        // X = (b+ - b-) c B + (b+ + b-) c^2 B^2 (written over C)
+        // (I + Y)((b+ - b-) c B + (b+ + b-) c^2 B^2) = a B + a Y B + (b+ + b-) Y
+        // with Y = (I - c^2 B^2)^-1 - I, a = (b+ - b-) c: F += (b+ + b-) Y now,
+        // G += a Y, and a B + G B after the last pair
         const double dr = cf.b_re[f][i] - cf.b_re[f][pq], di = cf.b_im[f][i] - cf.b_im[f][pq];
-        const double sr = cf.b_re[f][i] + cf.b_re[f][pq], si = cf.b_im[f][i] + cf.b_im[f][pq];
-        grid::pair_rhs<T><<<blocks(nn), kThreads, 0, st_>>>(
-            nn, dr * cr - di * ci, dr * ci + di * cr, B_, sr * c2r - si * c2i, sr * c2i + si * c2r,
-            B2_, C_);
-        check("pair right-hand side");
-        grid::Epi e;
-        e.Z1 = Ff;
-        e.ld1 = n;
-        e.b1r = 1.0;
-        e.Z2 = C_;
-        e.ld2 = n;
-        e.b2r = 1.0;
-        prod(n, n, n, Y_, n, f == 0, C_, n, e, Ff, n);
+        const double ar = dr * cr - di * ci, ai = dr * ci + di * cr;
+        grid::pair_acc<T><<<blocks(nn), kThreads, 0, st_>>>(
+            nn, cf.b_re[f][i] + cf.b_re[f][pq], cf.b_im[f][i] + cf.b_im[f][pq], ar, ai, Y_,
+            !pair_seen, Ff, G_ + (size_t)f * nn);
+        check("pair combination");
+        asum_r[f] += ar;
+        asum_i[f] += ai;
       } else {
         grid::accumulate<T><<<blocks(nn), kThreads, 0, st_>>>(n, cf.b_re[f][i], cf.b_im[f][i], Y_,
                                                              g.form == 1, Ff);
         check("combination");
       }
     }
+    if (pq > i) pair_seen = true;
+  }
+  // the pairs' a B + G B: one product per function, F = G B + F + (sum a) B
+  for (int f = 0; f < nf && pair_seen && err_ == cudaSuccess; ++f) {
+    T* Ff = f ? F1_ : F0_;
+    grid::Epi e;
+    e.Z1 = Ff;
+    e.ld1 = n;
+    e.b1r = 1.0;
+    e.Z2 = B_;
+    e.ld2 = n;
+    e.b2r = asum_r[f];
+    e.b2i = asum_i[f];
+    prod(n, n, n, G_ + (size_t)f * nn, n, true, B_, n, e, Ff, n);
   }
   if (err_ != cudaSuccess) return FM_ECUDA;
 

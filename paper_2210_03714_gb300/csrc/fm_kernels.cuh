@@ -238,8 +238,8 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   }
   __syncthreads();
   const bool hyb = cf.d1[0] != 0 || cf.d2[0] != 0 || (two && (cf.d1[1] != 0 || cf.d2[1] != 0));
-  // pairs (+c, -c) of the roundoff form share one system (Sec. 1: one
-  // product and one inverse per pair):
+  // pairs (+c, -c) of the roundoff form share one system, as Sec. 1 pairs
+  // complex-conjugate roots (one product, x^2, and one inverse per pair):
   //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
   //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
   signed char partner[kMaxTerms];

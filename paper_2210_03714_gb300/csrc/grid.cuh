@@ -148,13 +148,18 @@ __global__ void build_shift(size_t count, const T* B, double cr, double ci, T* C
   }
 }
 
-// X = a B + b B2 (the right-hand side of a fused +-c pair)
+// a fused +-c pair with Y = (I - c^2 B^2)^-1 - I: F += s Y and G += a Y
+// (G = a Y for the first pair), s = b+ + b-, a = (b+ - b-) c
 template <class T>
-__global__ void pair_rhs(size_t count, double ar, double ai, const T* B, double br, double bi,
-                         const T* B2, T* X) {
+__global__ void pair_acc(size_t count, double sr, double si, double ar, double ai, const T* Y,
+                         int first, T* F, T* G) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
-       e += (size_t)gridDim.x * blockDim.x)
-    X[e] = Tr<T>::add(cmul<T>(ar, ai, B[e]), cmul<T>(br, bi, B2[e]));
+       e += (size_t)gridDim.x * blockDim.x) {
+    const T y = Y[e];
+    F[e] = Tr<T>::add(F[e], cmul<T>(sr, si, y));
+    const T g = cmul<T>(ar, ai, y);
+    G[e] = first ? g : Tr<T>::add(G[e], g);
+  }
 }
 
 // F (n x n, ld n) = base I + d1 B + d2 B2   (B2 nullable when d2 == 0)
