@@ -308,6 +308,118 @@ def run_single(args):
     return 0
 
 
+def run_trid(args):
+    """The tridiagonal action: 32768 systems of order 1000 (the paper's d for
+    trid{-1,2,-1}, Sec. 5 Fig. 4), R10 in the roundoff form (the paper's R'_10,
+    13d flops per shifted solve and step) or the plain form (R_10, 8d), with
+    ||t A||_1 = 8 (N = 36 steps).  One step is one fm_trid_expmv_batched call."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2210_03714_gb300 as fm
+    from paper_2210_03714_gb300 import workloads as wl
+    rank = int(os.environ.get("RANK", "0"))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fm.lib()
+    batch, d, eta = 32768, 1000, 8.0
+    form = "plain" if args.form == "plain" else "roundoff"
+    dl, dd, du, v, t = wl.trid_batch(batch, d, eta=eta, seed=5000)
+    Dl, Dd, Du, Vd, Td = (torch.tensor(x, dtype=torch.float64, device=dev)
+                          for x in (dl, dd, du, v, t))
+    cs = fm.Coeffs("R10")
+    call = lambda: fm.trid_expmv_batched(Dl, Dd, Du, Vd, Td, cs, form=form)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        W, info, N = call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    bad = int((info != 0).sum().item())
+    Ns = N.cpu().numpy().astype(np.float64)
+    k = sum(1 for c in cs.as_dict()["c_re"] if c != 0)
+    # algorithmic work (the paper's count): per step and system k shifted
+    # solves of 13d flops (roundoff: B v and the Thomas solve) or 8d (plain);
+    # the kernel's traffic per step: per node and element three factors read
+    # and z written and read back, plus v, the diagonals and the output
+    per_solve = 13.0 if form == "roundoff" else 8.0
+    flops = float(Ns.sum()) * k * per_solve * d
+    nbytes = float(Ns.sum()) * d * 8.0 * (5 * k + 6) + batch * d * 8.0 * (3 * k + 4)
+    peaks = load_peaks()
+    pk = pipe_peaks(peaks)
+    sec = ms / 1000.0
+    fp64 = {"achieved": flops / sec / 1e12, "peak": pk["fp64"][0], "peak_source": pk["fp64"][1],
+            "unit": "TFLOP/s"}
+    fp64["frac"] = fp64["achieved"] / fp64["peak"]
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm = {"achieved": nbytes / sec / 1e9, "peak": hbm_peak,
+           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "unit": "GB/s"}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    bound = "hbm" if hbm["frac"] > fp64["frac"] else "alu"
+    b = hbm if bound == "hbm" else fp64
+    roofline = {"bound": bound, "kernel": "trid_steps", "achieved": b["achieved"],
+                "peak": b["peak"], "unit": b["unit"], "frac": b["frac"], "traffic": None,
+                "pipes": {"fp64": fp64, "hbm": hbm},
+                "note": "whole call (the factorization launch included); fp64: the paper's "
+                        "flop count, peak derived from unit counts; hbm: the kernel's design "
+                        "traffic over the measured copy bandwidth"}
+    # one sampled system against the oracle (dense LU of the same matrix)
+    Wh = W[:, 7].cpu().numpy()
+    ref, Nr, _ = oracle.expmv(wl.trid_dense(dl, dd, du, 7), v[:, 7], t[7], "R10",
+                              oracle.PLAIN if form == "plain" else oracle.ROUNDOFF)
+    err = float(np.linalg.norm(Wh - ref) / np.linalg.norm(ref))
+    # end to end with host buffers: inputs in, result and status out, per step
+    pins = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (dl, dd, du, v, t)]
+    W_host = torch.empty((d, batch), dtype=torch.float64).pin_memory()
+    info_host = torch.empty(batch, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    for q in range(e2e_steps + 1):
+        if q == 1:
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+        for dst, src in zip((Dl, Dd, Du, Vd, Td), pins):
+            dst.copy_(src, non_blocking=True)
+        W, info, N = call()
+        W_host.copy_(W, non_blocking=True)
+        info_host.copy_(info, non_blocking=True)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a0.elapsed_time(a1) / e2e_steps
+    e2e = {"value": batch / (e2e_ms / 1000.0), "unit": "systems/s",
+           "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in pins)),
+           "d2h_bytes_per_step": int(W_host.numel() * 8 + info_host.numel() * 4)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        oracle.expmv(wl.trid_dense(dl, dd, du, 8), v[:, 8], t[8], "R10",
+                     oracle.PLAIN if form == "plain" else oracle.ROUNDOFF)
+        cs_ = time.perf_counter() - t0
+        cpu = {"value": 1.0 / cs_, "unit": "systems/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "1 system of the batch (dense LU of the same matrix)"}
+    line = {"metric": "tridiagonal action evals/sec (systems/s) at <=1e-12 rel err",
+            "value": batch / sec, "unit": "systems/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "replicas", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "exp(t A) v: 32768 tridiagonal A of order 1000, "
+                                   "A = -trid{1+e, 2(1+e), 1+e} (e ~ 0.05 N(0,1)), v unit "
+                                   "random, ||t A||_1 = 8, R10 %s form (N = 36)" % form,
+                       "l2": "working set (GBs) larger than L2"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "status_nonzero": bad, "rel_err_vs_oracle_sample": err, "cpu_baseline": cpu,
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -425,16 +537,21 @@ def main():
     ap.add_argument("--dims", default=None,
                     help="comma-separated orders d is drawn from (default 16,32,...,256)")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "hermitian", "dense", "diffusion"],
+                    choices=["batch", "hermitian", "dense", "diffusion", "trid"],
                     help="batch: the 4096-matrix exp batch (default); hermitian: exp(-iH)V, "
                          "d = 4096, V 4096 x 256, N = 206 steps; dense: exp(A), one real "
                          "matrix of order --dim (both on the grid path); diffusion: phi_1 "
-                         "of 512 matrices of order 512 (batched grid path)")
+                         "of 512 matrices of order 512 (batched grid path); trid: exp(tA)v "
+                         "for 32768 tridiagonal A of order 1000 (Thomas solves)")
+    ap.add_argument("--form", default="roundoff", choices=["roundoff", "plain"],
+                    help="form of the rational approximant for --workload trid")
     ap.add_argument("--dim", type=int, default=2048)
     ap.add_argument("--path", default="auto", choices=["auto", "cta", "grid"],
                     help="execution path of the mixed form for the batch (the double form "
                          "always runs one CTA per matrix)")
     args = ap.parse_args()
+    if args.workload == "trid":
+        return run_trid(args)
     if args.workload != "batch":
         return run_single(args)
     if args.batch != BATCH or args.dims:

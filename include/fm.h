@@ -250,6 +250,39 @@ fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, con
                                    double* Abar, double* vbar, int* info_dev,
                                    const fm_opts* opts, void* stream);
 
+/* ---- actions of tridiagonal matrices (Sec. 2.1, Sec. 5) ------------------ */
+/* W_b = r(B_b)^(N_b) V_b ~ exp(t_b A_b) V_b for a batch of tridiagonal A_b of one
+ * order d: the action recurrence of Sec. 1 with B_b = (t_b / N_b) A_b and
+ * N_b = max(1, ceil(||t_b A_b||_1 / theta)) (opts.anorm > 0: anorm |t_b| in place
+ * of the norm; opts.nsteps > 0: N_b = nsteps).  Each shifted matrix I - c_i B_b
+ * is tridiagonal (Sec. 2.1): it is factored once per call by the Thomas
+ * algorithm, without pivoting, and every step solves it in 8d flops (plain
+ * form, Eq. rat1, the paper's R_10) or, with the product B v, 13d (roundoff
+ * form, Eq. ParallRoundOff, the paper's R'_10).  Same N and the same rational
+ * function as fm_expmv on the dense matrix.
+ *
+ * Layout (all DEVICE, double, batch-interleaved): element k of system b is at
+ * k * batch + b in dl (sub-diagonal A[k][k-1], k >= 1; the k = 0 slot is not
+ * read), dd (diagonal A[k][k]), du (super-diagonal A[k][k+1], k <= d - 2; the
+ * k = d - 1 slot is not read), V and W.  t_dev[b]: time of system b.
+ * info_dev[b]: 0; -2 for a non-finite entry of A_b, V_b or t_b (W_b is not
+ * written); or (term index i) * d + (1-based row) for an exactly zero pivot of
+ * the first such I - c_i B_b (W_b is not written).  nsteps_dev[b] (nullable):
+ * N_b.  dl and du may be NULL when d = 1.  Double precision whatever
+ * opts.precision says; the coefficient set must have real nodes, at least one
+ * of them nonzero, and one function (no phi_1 weights).  Scratch:
+ * fm_trid_workspace_size bytes in opts.workspace, or the library's buffer.
+ * Stream-ordered, no host synchronization.  Errors: FM_EINVAL (NULL pointer,
+ * complex or empty node set), FM_ESHAPE (batch or d < 1), FM_ENOMEM, FM_ECUDA. */
+fm_status fm_trid_expmv_batched(const fm_coeffs* cs, int batch, int d, const double* dl,
+                                const double* dd, const double* du, const double* t_dev,
+                                const double* V, double* W, int* info_dev, int* nsteps_dev,
+                                const fm_opts* opts, void* stream);
+
+/* Bytes of device scratch of fm_trid_expmv_batched for batch systems of order
+ * d and a set of k terms (0 for a bad argument). */
+size_t fm_trid_workspace_size(int batch, int d, int k);
+
 /* ---- exp(tA) without any device allocation ------------------------------ */
 /* The paper has no counterpart: this is a deployment variant of fm_expm for
  * callers that cannot allocate device memory (code that runs where cudaMalloc

@@ -95,6 +95,9 @@ _SIGS = {
     "fm_expmv_adjoint_batched": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, C.c_int, _P, _P, _P, _P,
                                            _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(fm_opts),
                                            _P]),
+    "fm_trid_expmv_batched": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, C.c_int, _P, _P, _P, _P,
+                                        _P, _P, _P, _P, C.POINTER(fm_opts), _P]),
+    "fm_trid_workspace_size": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
     "fm_expm_noalloc": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, _P, C.c_int, C.c_double, _P,
                                   C.c_int, C.POINTER(fm_opts), _P, c_ip, c_ip]),
     "fm_last_error": (C.c_char_p, []),

@@ -267,6 +267,28 @@ def phi1mv_batched(P, V, m, t=1.0, ce="R8", cphi="R8_phi1", precision="mixed", *
     return W, info, s
 
 
+def trid_expmv_batched(dl, dd, du, V, t=1.0, coeffs="R10", form="roundoff", **kw):
+    """exp(t_b A_b) v_b for a batch of tridiagonal A_b (fm_trid_expmv_batched).
+
+    dl, dd, du, V: float64 CUDA tensors of shape (d, batch), batch-interleaved:
+    row k holds element k of every system (dl[k] = A[k][k-1], dd[k] = A[k][k],
+    du[k] = A[k][k+1]).  Returns (W (d, batch), info, N)."""
+    for name, x in (("dl", dl), ("dd", dd), ("du", du), ("V", V)):
+        _need(x, torch.float64, name)
+        if x.shape != dd.shape or not x.is_contiguous():
+            raise ValueError("%s must be a contiguous (d, batch) tensor like dd" % name)
+    d, n = dd.shape
+    W = torch.empty_like(V)
+    info = torch.empty(n, dtype=torch.int32, device=V.device)
+    ns = torch.empty(n, dtype=torch.int32, device=V.device)
+    td = _tdev(t, n, V.device)
+    cs = _cs(coeffs)
+    o = _opts("fp64", form=form, **kw)
+    check(lib().fm_trid_expmv_batched(cs.ptr(), n, d, _p(dl), _p(dd), _p(du), _p(td), _p(V),
+                                      _p(W), _p(info), _p(ns), C.byref(o), _stream()))
+    return W, info, ns
+
+
 def expmv_adjoint_batched(P, v, wbar, nsteps, t=1.0, coeffs="R8"):
     """Forward w_N and gradients (Abar flat, vbar flat) of <wbar, w_N> for
     N = nsteps[b] steps (fixed); always double precision."""

@@ -14,6 +14,7 @@
 #include "fm_grid.h"
 #include "fm_job.h"
 #include "fm_launch.h"
+#include "fm_trid.h"
 
 using namespace fmk;
 
@@ -717,6 +718,58 @@ fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, con
   o2.nsteps = 0;
   o2.precision = FM_FP64;
   return run(c, &o2, (cudaStream_t)stream);
+}
+
+fm_status fm_trid_expmv_batched(const fm_coeffs* cs, int batch, int d, const double* dl,
+                                const double* dd, const double* du, const double* t_dev,
+                                const double* V, double* W, int* info_dev, int* nsteps_dev,
+                                const fm_opts* opts, void* stream) {
+  memset(&g_stats, 0, sizeof g_stats);
+  fm_opts o = resolve_opts(opts);
+  fm_status s = check_opts(o);
+  if (s) return s;
+  if (batch < 1 || d < 1) return fail(FM_ESHAPE, "fm_trid_expmv_batched: batch and d must be >= 1");
+  if (!dd || !t_dev || !V || !W || !info_dev || (d > 1 && (!dl || !du)))
+    return fail(FM_EINVAL, "fm_trid_expmv_batched: NULL pointer");
+  FmCoef cf;
+  s = pack(cs, nullptr, false, o.form, cf);
+  if (s) return s;
+  int nonzero = 0;
+  for (int i = 0; i < cf.k; ++i) nonzero += cf.c_re[i] != 0.0;
+  if (!nonzero) return fail(FM_EINVAL, "fm_trid_expmv_batched: the set needs a nonzero node");
+  const size_t need = trid_ws_bytes(batch, d, cf.k);
+  void* ws = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  s = get_scratch(need, &o, &ws, st);
+  if (s) return s;
+  TridJob j;
+  j.batch = batch;
+  j.d = d;
+  j.form = o.form;
+  j.dl = dl;
+  j.dd = dd;
+  j.du = du;
+  j.t = t_dev;
+  j.V = V;
+  j.W = W;
+  j.info = info_dev;
+  j.nsteps = nsteps_dev;
+  j.anorm = o.anorm;
+  j.nsteps_fixed = o.nsteps;
+  j.cf = cf;
+  j.ws = ws;
+  j.ws_bytes = o.workspace ? o.workspace_bytes : need;
+  j.st = st;
+  char msg[256];
+  const int r = trid_run(j, msg, sizeof msg);
+  if (r) return fail((fm_status)r, msg);
+  g_stats.launches = 2;
+  return FM_OK;
+}
+
+size_t fm_trid_workspace_size(int batch, int d, int k) {
+  if (k < 1 || k > FM_MAX_TERMS) return 0;
+  return trid_ws_bytes(batch, d, k);
 }
 
 const char* fm_last_error(void) { return g_err; }

@@ -97,3 +97,37 @@ def toeplitz_paper(d=100):
     """Eq. (Ex2b): A_ij = 1/(1 + (i - j)^2)."""
     i = np.arange(d)
     return 1.0 / (1.0 + (i[:, None] - i[None, :]) ** 2)
+
+
+def trid_batch(batch, d, eta=8.0, seed=5000, spread=0.1):
+    """A batch of tridiagonal systems shaped like the paper's trid{-1,2,-1}
+    example (Sec. 5, Fig. 4, d = 1000), negated so that exp(tA) decays as in a
+    diffusion step: A_b = -trid{1 + e', 2 (1 + e), 1 + e''} with e, e', e''
+    ~ spread N(0,1) / 2 per entry; v_b = w / ||w||_2, w ~ N(0,1) (the paper's
+    unit random vector); t_b = eta / ||A_b||_1, so ||t_b A_b||_1 = eta up to
+    rounding.  Returned batch-interleaved, shape (d, batch): row k holds entry
+    k of every system (dl[0] and du[d-1] are zero and not part of A)."""
+    g = _rng(seed)
+    h = spread / 2
+    dd = -2.0 * (1.0 + h * g.standard_normal((d, batch)))
+    dl = 1.0 + h * g.standard_normal((d, batch))
+    du = 1.0 + h * g.standard_normal((d, batch))
+    dl[0] = 0.0
+    du[d - 1] = 0.0
+    w = g.standard_normal((d, batch))
+    v = w / np.linalg.norm(w, axis=0)
+    # ||A_b||_1: column k holds du[k-1], dd[k], dl[k+1]
+    col = np.abs(dd).copy()
+    col[1:] += np.abs(du[:-1])
+    col[:-1] += np.abs(dl[1:])
+    t = eta / col.max(axis=0)
+    return dl, dd, du, v, t
+
+
+def trid_dense(dl, dd, du, b):
+    """System b of a batch-interleaved tridiagonal batch as a dense matrix."""
+    d = dd.shape[0]
+    A = np.diag(dd[:, b])
+    if d > 1:
+        A += np.diag(dl[1:, b], -1) + np.diag(du[:-1, b], 1)
+    return A

@@ -82,3 +82,28 @@ def test_workspace_size_monotone():
     b = L.fm_workspace_size(0, 16, 256, 0, 9, None)
     assert 0 < a < b
     assert L.fm_workspace_size(0, 16, 100000, 0, 9, None) == 0
+
+
+def test_trid_host_validation():
+    """fm_trid_expmv_batched rejects bad shapes, NULL pointers and complex
+    node sets before any device work; its scratch size grows with the batch
+    and the order and is 0 for bad arguments."""
+    import ctypes as C
+    import paper_2210_03714_gb300 as fm
+    from paper_2210_03714_gb300 import _ffi
+    L = fm.lib()
+    cs = _ffi.fm_coeffs()
+    assert L.fm_coeffs_builtin(_ffi.BUILTIN["R10"], C.byref(cs)) == 0
+    args = [None] * 8
+    assert L.fm_trid_expmv_batched(C.byref(cs), 0, 10, *args, None, None) == _ffi.FM_ESHAPE
+    assert L.fm_trid_expmv_batched(C.byref(cs), 4, 10, *args, None, None) == _ffi.FM_EINVAL
+    assert b"NULL" in L.fm_last_error()
+    fake = [C.c_void_p(256)] * 7 + [None]   # never dereferenced: rejected first
+    cp = _ffi.fm_coeffs()
+    assert L.fm_coeffs_builtin(_ffi.BUILTIN["pade22"], C.byref(cp)) == 0
+    assert L.fm_trid_expmv_batched(C.byref(cp), 4, 10, *fake, None, None) == _ffi.FM_EINVAL
+    a = L.fm_trid_workspace_size(10, 100, 10)
+    assert 0 < a < L.fm_trid_workspace_size(20, 100, 10)
+    assert a < L.fm_trid_workspace_size(10, 200, 10)
+    assert L.fm_trid_workspace_size(0, 100, 10) == 0
+    assert L.fm_trid_workspace_size(10, 100, 17) == 0
