@@ -321,7 +321,7 @@ def run_trid(args):
     rank = int(os.environ.get("RANK", "0"))
     dev = torch.device("cuda", torch.cuda.current_device())
     fm.lib()
-    batch, d, eta = 32768, 1000, 8.0
+    batch, d, eta = args.trid_batch, 1000, 8.0
     form = "plain" if args.form == "plain" else "roundoff"
     dl, dd, du, v, t = wl.trid_batch(batch, d, eta=eta, seed=5000)
     Dl, Dd, Du, Vd, Td = (torch.tensor(x, dtype=torch.float64, device=dev)
@@ -408,9 +408,9 @@ def run_trid(args):
             "value": batch / sec, "unit": "systems/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "replicas", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "exp(t A) v: 32768 tridiagonal A of order 1000, "
+            "config": {"workload": "exp(t A) v: %d tridiagonal A of order 1000, "
                                    "A = -trid{1+e, 2(1+e), 1+e} (e ~ 0.05 N(0,1)), v unit "
-                                   "random, ||t A||_1 = 8, R10 %s form (N = 36)" % form,
+                                   "random, ||t A||_1 = 8, R10 %s form (N = 36)" % (batch, form),
                        "l2": "working set (GBs) larger than L2"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "status_nonzero": bad, "rel_err_vs_oracle_sample": err, "cpu_baseline": cpu,
@@ -543,6 +543,8 @@ def main():
                          "matrix of order --dim (both on the grid path); diffusion: phi_1 "
                          "of 512 matrices of order 512 (batched grid path); trid: exp(tA)v "
                          "for 32768 tridiagonal A of order 1000 (Thomas solves)")
+    ap.add_argument("--trid-batch", type=int, default=32768,
+                    help="systems of order 1000 for --workload trid")
     ap.add_argument("--form", default="roundoff", choices=["roundoff", "plain"],
                     help="form of the rational approximant for --workload trid")
     ap.add_argument("--dim", type=int, default=2048)

@@ -14,7 +14,8 @@
 //               N steps.  With m, l, u the diagonal, sub- and super-diagonal
 //               of I - c_i B:  beta_0 = m_0, lam_k = l_k / beta_{k-1},
 //               beta_k = m_k - lam_k u_{k-1}; stored: lam_k, 1/beta_k and
-//               g_k = u_k / beta_k.  No pivoting: |c_i| ||B||_1 is far below
+//               g_k = u_k / beta_k (one division per node and row: the
+//               quotients are products with 1/beta).  No pivoting: |c_i| ||B||_1 is far below
 //               1/2 for the sets here at ||B||_1 <= theta, so I - c_i B is
 //               diagonally dominant.  An exactly zero pivot stops the system
 //               with info = i d + (1-based row), i the first such term.
@@ -38,6 +39,9 @@ namespace fmk {
 namespace {
 
 constexpr int kThreads = 128;
+// one warp per block for the steps: the FP64 pipe of each SM is their limit,
+// and single-warp blocks spread the systems evenly over the SMs
+constexpr int kStepThreads = 32;
 
 size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -109,7 +113,7 @@ __global__ void trid_prep(TArgs a) {
     N = q < 1.0 ? 1 : (q > 2147483647.0 ? 2147483647LL : (long long)q);
   }
   const double h = t / (double)N;
-  // factors, k outer so the diagonals are read once; beta and u of the
+  // factors, k outer so the diagonals are read once; 1/beta and u of the
   // previous row per node (local arrays: this runs once per call)
   double beta[kMaxTerms], uprev[kMaxTerms];
   int zrow[kMaxTerms];
@@ -125,15 +129,16 @@ __global__ void trid_prep(TArgs a) {
       double bet = m;
       if (k > 0) {
         const double l = -__dmul_rn(c, hdl);
-        const double lam = l / beta[j];
+        const double lam = __dmul_rn(l, beta[j]);  // beta[j] holds 1 / beta_{k-1}
         bet = __dsub_rn(m, __dmul_rn(lam, uprev[j]));
         a.lam[at] = lam;
       }
       if (bet == 0.0 && zrow[j] == 0) zrow[j] = k + 1;
       const double u = k + 1 < n ? -__dmul_rn(c, hdu) : 0.0;
-      a.ib[at] = 1.0 / bet;
-      a.g[at] = u / bet;
-      beta[j] = bet;
+      const double r = 1.0 / bet;  // the one division per node and row
+      a.ib[at] = r;
+      a.g[at] = __dmul_rn(u, r);
+      beta[j] = r;
       uprev[j] = u;
     }
   }
@@ -150,7 +155,7 @@ __global__ void trid_prep(TArgs a) {
 // of the next k are issued before the current k is computed (read-only path,
 // no aliasing), so each thread keeps two iterations of loads in flight.
 template <int KN>
-__global__ void __launch_bounds__(kThreads) trid_steps(TArgs a) {
+__global__ void __launch_bounds__(kStepThreads) trid_steps(TArgs a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.batch) return;
   const int N = a.ns[b];
@@ -273,8 +278,8 @@ __global__ void __launch_bounds__(kThreads) trid_steps(TArgs a) {
 
 template <int KN>
 cudaError_t launch_steps(const TArgs& a, cudaStream_t st) {
-  const int blocks = (a.batch + kThreads - 1) / kThreads;
-  trid_steps<KN><<<blocks, kThreads, 0, st>>>(a);
+  const int blocks = (a.batch + kStepThreads - 1) / kStepThreads;
+  trid_steps<KN><<<blocks, kStepThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
