@@ -420,6 +420,99 @@ def run_trid(args):
     return 0
 
 
+def run_small(args):
+    """The two latency-bound configurations on the one-CTA kernels: exp of one
+    real d = 64 matrix (N(0,1) scaled to ||A||_1 = 2, R4, s = 10), and the
+    gradient batch (256 matrices of order 128, N(0,1)/sqrt(d), R8 action with
+    N from each matrix's norm, forward and adjoint in one call)."""
+    import numpy as np
+    import torch
+    import paper_2210_03714_gb300 as fm
+    from paper_2210_03714_gb300 import workloads as wl
+    rank = int(os.environ.get("RANK", "0"))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fm.lib()
+    peaks = load_peaks()
+    fp64_peak = pipe_peaks(peaks)["fp64"][0]
+    if args.workload == "single":
+        A, _ = wl.single_d64()
+        Ad = torch.tensor(A, dtype=torch.float64, device=dev)
+        cs = fm.Coeffs("R4")
+        call = lambda prec: fm.expm(Ad, 1.0, cs, precision=prec, status=False)
+        units, d = 1, 64
+        metric = "exp of one d=64 matrix, evals/sec at <=1e-12 rel err (one CTA)"
+        workload = "exp(A): one real d=64 matrix, N(0,1) scaled to ||A||_1 = 2, R4 (s = 10)"
+    else:
+        A, v, y = wl.grad_batch(batch=256)
+        d = A.shape[1]
+        P = fm.Packed([torch.from_numpy(a) for a in A], device=dev)
+        vd = torch.tensor(v.ravel(), dtype=torch.float64, device=dev)
+        cs = fm.Coeffs("R8")
+        W0, info0, N0 = fm.expmv_batched(P, vd, 1, 1.0, cs, precision="fp64")
+        Ns = [int(x) for x in N0.cpu().numpy()]
+        wbar = 2 * (W0 - torch.tensor(y.ravel(), dtype=torch.float64, device=dev))
+        call = lambda prec: fm.expmv_adjoint_batched(P, vd, wbar, Ns, 1.0, cs)
+        units = len(A)
+        metric = "gradient of an R8 action, items/sec (forward + adjoint, one CTA per item)"
+        workload = ("d/dA, d/dv of <wbar, r(B)^N v>: 256 matrices of order 128, N(0,1)/sqrt(d), "
+                    "R8, N = ceil(||A||_1/theta) per matrix (mean %.0f)" % np.mean(Ns))
+    stream = torch.cuda.current_stream()
+    prec = args.precision if args.workload == "single" else "fp64"
+    for _ in range(args.warmup):
+        out = call(prec)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out = call(prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    extra = {}
+    if args.workload == "single":
+        _, _, s = fm.expm(Ad, 1.0, cs, precision=prec)
+        # B^2, the two +-c pairs of R4 (one LU and a d-column solve each), s squarings
+        flops = (2.0 + 2 * 8.0 / 3.0) * d ** 3 + 2.0 * s * d ** 3
+        sm_peak = fp64_peak / 152
+        ach = flops / (ms / 1000.0) / 1e12
+        roofline = {"bound": "latency", "pipe": "fp64", "achieved": ach, "peak": sm_peak,
+                    "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": None,
+                    "note": "one CTA on one SM: the paper's flop count over one SM's derived "
+                            "FP64 rate (1/152 of the GPU's)"}
+        if prec == "mixed":
+            ref = fm.expm(Ad, 1.0, cs, precision="fp64")[0]
+            extra["rel_diff_vs_fp64"] = float(((out - ref).norm() / ref.norm()).item())
+        extra["s"] = s
+    else:
+        Nv = np.array(Ns, dtype=np.float64)
+        k = 8
+        # forward: k LUs and N steps of k solves and one product; reverse: N
+        # steps of k transposed solves, k rank-one updates and two products
+        flops = float(np.sum(k * (2.0 / 3.0) * d ** 3 + Nv * (k * 2 * d * d + 2 * d * d)
+                             + Nv * (k * 2 * d * d + k * 2 * d * d + 4 * d * d)))
+        ach = flops / (ms / 1000.0) / 1e12
+        roofline = {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                    "note": "model flop count of the forward map and its adjoint over the "
+                            "derived FP64 peak; the factors are reused N times from the "
+                            "CTA's scratch, so the path is latency-bound"}
+        extra["status_nonzero"] = int((out[3] != 0).sum().item())
+    line = {"metric": metric, "value": units * 1000.0 / ms, "unit": "evals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "replicas", "vs_baseline": None,
+            "dtype": ("f32+f64" if prec == "mixed" else "f64"), "data": "synthetic",
+            "config": {"workload": workload, "precision": prec, "path": "one-CTA",
+                       "l2": "working set within L2 (latency-bound)"},
+            "roofline": roofline, "clocks": clk}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -537,12 +630,14 @@ def main():
     ap.add_argument("--dims", default=None,
                     help="comma-separated orders d is drawn from (default 16,32,...,256)")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "hermitian", "dense", "diffusion", "trid"],
+                    choices=["batch", "hermitian", "dense", "diffusion", "trid", "single",
+                             "adjoint"],
                     help="batch: the 4096-matrix exp batch (default); hermitian: exp(-iH)V, "
                          "d = 4096, V 4096 x 256, N = 206 steps; dense: exp(A), one real "
                          "matrix of order --dim (both on the grid path); diffusion: phi_1 "
                          "of 512 matrices of order 512 (batched grid path); trid: exp(tA)v "
-                         "for 32768 tridiagonal A of order 1000 (Thomas solves)")
+                         "for 32768 tridiagonal A of order 1000 (Thomas solves); single: exp "
+                         "of one d = 64 matrix; adjoint: the gradient batch (256 x 128^2)")
     ap.add_argument("--trid-batch", type=int, default=32768,
                     help="systems of order 1000 for --workload trid")
     ap.add_argument("--form", default="roundoff", choices=["roundoff", "plain"],
@@ -554,6 +649,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "trid":
         return run_trid(args)
+    if args.workload in ("single", "adjoint"):
+        return run_small(args)
     if args.workload != "batch":
         return run_single(args)
     if args.batch != BATCH or args.dims:
