@@ -596,7 +596,7 @@ def rank_barrier(world):
 
 
 def rank_max(x, world, device):
-    """Largest x over the ranks (the step time the job is judged by)."""
+    """Largest x over the ranks (the whole job's step time)."""
     if world == 1:
         return x
     import torch
