@@ -541,8 +541,38 @@ __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b,
   __syncthreads();
 }
 
+// y = s M x, M n x n row-major (one warp per row); y must not alias x
+__device__ __forceinline__ void cta_gemv(int n, const double* M, const double* x, double s,
+                                         double* y) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int r = w; r < n; r += NT / 32) {
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) acc = fma(M[(size_t)r * n + c], x[c], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[r] = s * acc;
+  }
+  __syncthreads();
+}
+
+// y = s M^T x (+ y when accumulate), one thread per column; y must not alias x
+__device__ __forceinline__ void cta_gemv_t(int n, const double* M, const double* x, double s,
+                                           double* y, bool accumulate) {
+  for (int c = threadIdx.x; c < n; c += NT) {
+    double acc = 0.0;
+    for (int r = 0; r < n; ++r) acc = fma(M[(size_t)r * n + c], x[r], acc);
+    y[c] = accumulate ? fma(s, acc, y[c]) : s * acc;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // adjoint of the action (real, double, one vector): JOB_ADJ
+//
+// The factors of every I - c_i B serve 2N solves with one right-hand side
+// each, so each processor forms its inverse once (Sec. 1: each processor
+// computes an inverse; d column solves of its LU factors), and every step's
+// solve is a CTA-wide matrix-vector product: Y_i = c_i M_i^-1 u forward,
+// lambda_i = b_i M_i^-T wbar in reverse.
 // ---------------------------------------------------------------------------
 template <int NB>
 __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem) {
@@ -585,6 +615,15 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
     int fi = cta_getrf<T, NB>(n, LUi, n, pivi, (T*)smem);
     if (fi) info = i * n + fi;
   }
+  // M_i^-1 in place of C_i (not used past the factorization)
+  for (int i = 0; i < k && info == 0; ++i) {
+    if (cf.c_re[i] == 0.0) continue;
+    T* Inv = (T*)(ws + L.Cs) + (size_t)i * n * n;
+    for (int e = tid; e < n * n; e += NT) Inv[e] = (e / n == e % n) ? 1.0 : 0.0;
+    __syncthreads();
+    cta_getrs<T, NB>(n, (T*)(ws + L.LUs) + (size_t)i * n * n, n, (int*)(ws + L.pivs) + (size_t)i * n,
+                     n, Inv, n, (T*)smem);
+  }
   if (info == 0) {
     // forward sweep, storing w_q and Y_iq
     for (int r = tid; r < n; r += NT) Wst[r] = ((const T*)J.V)[vo + r];
@@ -592,7 +631,7 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
     for (long long q = 1; q <= N; ++q) {
       const T* wp = Wst + (size_t)(q - 1) * n;
       T* wq = Wst + (size_t)q * n;
-      cta_gemm<T>(n, 1, n, 1.0, B, n, wp, 1, 0.0, u, 1, (T*)(smem + 256));
+      cta_gemv(n, B, wp, 1.0, u);
       for (int r = tid; r < n; r += NT) wq[r] = TT::rscale(wp[r], cf.a0[0]);
       __syncthreads();
       for (int i = 0; i < k; ++i) {
@@ -602,10 +641,7 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
           __syncthreads();
           continue;
         }
-        for (int r = tid; r < n; r += NT) yi[r] = TT::rscale(u[r], cf.c_re[i]);
-        __syncthreads();
-        solve_lu<T, NB>(J, n, (T*)(ws + L.LUs) + (size_t)i * n * n,
-                        (int*)(ws + L.pivs) + (size_t)i * n, 1, yi, smem);
+        cta_gemv(n, (const T*)(ws + L.Cs) + (size_t)i * n * n, u, cf.c_re[i], yi);
         for (int r = tid; r < n; r += NT) wq[r] = TT::add(wq[r], TT::rscale(yi[r], cf.b_re[0][i]));
         __syncthreads();
       }
@@ -628,10 +664,7 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
         const double c = cf.c_re[i];
         if (c == 0.0) continue;
         const T* yi = Yst + ((size_t)(q - 1) * k + i) * n;
-        for (int r = tid; r < n; r += NT) y[r] = TT::rscale(wb[r], cf.b_re[0][i]);
-        __syncthreads();
-        cta_getrs_t<T>(n, (T*)(ws + L.LUs) + (size_t)i * n * n, n,
-                       (int*)(ws + L.pivs) + (size_t)i * n, y);
+        cta_gemv_t(n, (const T*)(ws + L.Cs) + (size_t)i * n * n, wb, cf.b_re[0][i], y, false);
         for (int r = tid; r < n; r += NT) {
           ub[r] = TT::add(ub[r], TT::rscale(y[r], c));
           Lam[(size_t)r * (k + 1) + kk] = TT::rscale(y[r], c);
@@ -647,8 +680,8 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
       __syncthreads();
       // Bbar += [c_i lambda_i, ubar] [Y_i^T; w^T]
       cta_gemm<T>(n, n, kk + 1, 1.0, Lam, k + 1, Yt, n, 1.0, Cb, n, (T*)(smem + 256));
-      // wbar_{q-1} += B^T ubar  (as the row vector ubar^T B)
-      cta_gemm<T>(1, n, n, 1.0, ub, n, B, n, 1.0, wbp, n, (T*)(smem + 256));
+      // wbar_{q-1} += B^T ubar
+      cta_gemv_t(n, B, ub, 1.0, wbp, true);
       for (int r = tid; r < n; r += NT) wb[r] = wbp[r];
       __syncthreads();
     }
