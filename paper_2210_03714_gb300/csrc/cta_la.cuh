@@ -687,33 +687,4 @@ __host__ __device__ inline int getrs_width(int n, int m, size_t budget_elems) {
   return (int)w;
 }
 
-// ---------------------------------------------------------------------------
-// Solve (P^T L U)^T x = x for one vector x (length n, global), real types.
-// U^T z = x (forward), L^T w = z (backward), then the exchanges in reverse.
-// Column-oriented: after x_i is final, every later entry is updated.
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ __noinline__ void cta_getrs_t(int n, const T* LU, int lda, const int* piv, T* x) {
-  using TT = Tr<T>;
-  const int tid = threadIdx.x;
-  for (int i = 0; i < n; ++i) {
-    if (tid == 0) x[i] = TT::div(x[i], LU[(size_t)i * lda + i]);
-    __syncthreads();
-    T xi = x[i];
-    for (int l = i + 1 + tid; l < n; l += NT) x[l] = TT::sub(x[l], TT::mul(LU[(size_t)i * lda + l], xi));
-    __syncthreads();
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    T xi = x[i];
-    for (int l = tid; l < i; l += NT) x[l] = TT::sub(x[l], TT::mul(LU[(size_t)i * lda + l], xi));
-    __syncthreads();
-  }
-  if (tid == 0)
-    for (int k = n - 1; k >= 0; --k) {
-      int p = piv[k];
-      if (p != k) { T t = x[k]; x[k] = x[p]; x[p] = t; }
-    }
-  __syncthreads();
-}
-
 }  // namespace fmk
