@@ -349,6 +349,35 @@ def test_expmv_diagonal_closed_form():
     assert np.abs(W - ref).max() < 1e-13
 
 
+@pytest.mark.parametrize("name", ["R10", "R5"])
+def test_expmv_trid_sine_closed_form(name):
+    """The matrix of Sec. 5 (Fig. 4), A = trid{-1,2,-1}: its eigenvectors are the
+    sine vectors q_j(k) = sqrt(2/(d+1)) sin(j k pi/(d+1)) with eigenvalues
+    2 - 2 cos(j pi/(d+1)), so N steps of the action are Q diag(r(h l_j)^N) Q^T v
+    with r in 50-digit arithmetic.  This pins the reference of the tridiagonal
+    path's parity tests on the paper's own example."""
+    d, t = 40, 0.6
+    A = 2 * np.eye(d) - np.eye(d, k=1) - np.eye(d, k=-1)
+    j = np.arange(1, d + 1)
+    Q = np.sqrt(2.0 / (d + 1)) * np.sin(np.outer(j, j) * np.pi / (d + 1))
+    lam = 2 - 2 * np.cos(j * np.pi / (d + 1))
+    v = rng(31).standard_normal(d)
+    v /= np.linalg.norm(v)
+    W, N, info = oracle.expmv(A, v, t, name)
+    theta = oracle.CS(name).theta
+    assert info == 0 and N == oracle.select_nsteps(4 * t, theta)
+    cs = oc.SETS[name]
+    h = mp.mpf(t) / N
+    g = np.array([float(r_scalar(cs, h * mp.mpf(float(l))) ** N) for l in lam])
+    ref = Q @ (g * (Q.T @ v))
+    # N steps of the roundoff form each round at u (sum_i |b_i c_i| theta + 1)
+    # (Sec. 4.3): 5e-12 for R10's large weights, 2e-13 for R5
+    bc = sum(abs(float(b) * float(c)) for b, c in zip(cs.b, cs.c))
+    tol = max(5e-13, 2 * N * 2.0 ** -53 * (bc * theta + 1))
+    assert relerr(W, ref) < tol
+    assert relerr(W, Q @ (np.exp(t * lam) * (Q.T @ v))) < tol + 1e-13
+
+
 def test_phi1mv():
     A = rng(15).standard_normal((20, 20)) * 0.2
     V = rng(16).standard_normal((20, 2))
