@@ -549,17 +549,33 @@ int orc_expmv_adjoint(int n, const double* A, double t, const orc_coeffs* cs, lo
 /* complex matrices (z-variants): the same steps with complex c_i, b_i        */
 /* ------------------------------------------------------------------------ */
 
-/* r(B) R with complex B, c, b; R = NULL means I.  Returns info. */
-static int zapply(int n, const double complex* B, const orc_coeffs* cs, int form, int m,
-                  const double complex* R, double complex* out) {
-  size_t nm = (size_t)n * m, nn = (size_t)n * n;
+/* Factorizations of M_i = I - c_i B for complex B, c_i (c_i != 0), as
+ * factor_real does for real sets.  lu: k blocks of n*n, piv: k blocks of n.
+ * Returns info (0 or shift*n+col). */
+static int zfactor(int n, const double complex* B, const orc_coeffs* cs, double complex* lu,
+                   int* piv) {
+  for (int i = 0; i < cs->k; ++i) {
+    double complex c = cs->c_re[i] + I * cs->c_im[i];
+    if (c == 0.0) continue;
+    double complex* M = lu + (size_t)i * n * n;
+    for (int r = 0; r < n; ++r)
+      for (int q = 0; q < n; ++q)
+        M[(size_t)r * n + q] = (r == q ? 1.0 : 0.0) - c * B[(size_t)r * n + q];
+    int f = orc_zgepp(n, M, piv + (size_t)i * n);
+    if (f) return i * n + f;
+  }
+  return 0;
+}
+
+/* r(B) R with complex B, c, b and the factors from zfactor; R = NULL means I. */
+static void zapply_lu(int n, const double complex* B, const orc_coeffs* cs, int form, int m,
+                      const double complex* R, const double complex* lu, const int* piv,
+                      double complex* out) {
+  size_t nm = (size_t)n * m;
   double complex* Rm = malloc(nm * sizeof(double complex));
   double complex* U = malloc(nm * sizeof(double complex));
   double complex* U2 = malloc(nm * sizeof(double complex));
-  double complex* M = malloc(nn * sizeof(double complex));
   double complex* Y = malloc(nm * sizeof(double complex));
-  int* piv = malloc((size_t)n * sizeof(int));
-  int info = 0;
   if (R) memcpy(Rm, R, nm * sizeof(double complex));
   else for (int r = 0; r < n; ++r) for (int q = 0; q < n; ++q) Rm[(size_t)r * n + q] = (r == q);
   if (R) zmatmul(n, n, m, B, Rm, U); else memcpy(U, B, nm * sizeof(double complex));
@@ -576,16 +592,21 @@ static int zapply(int n, const double complex* B, const orc_coeffs* cs, int form
       if (form == ORC_PLAIN) for (size_t e = 0; e < nm; ++e) out[e] += b * Rm[e];
       continue;
     }
-    for (int r = 0; r < n; ++r)
-      for (int q = 0; q < n; ++q)
-        M[(size_t)r * n + q] = (r == q ? 1.0 : 0.0) - c * B[(size_t)r * n + q];
-    int f = orc_zgepp(n, M, piv);
-    if (f) { info = i * n + f; break; }
     for (size_t e = 0; e < nm; ++e) Y[e] = (form == ORC_ROUNDOFF) ? c * U[e] : Rm[e];
-    orc_zgetrs(n, M, piv, m, Y);
+    orc_zgetrs(n, lu + (size_t)i * n * n, piv + (size_t)i * n, m, Y);
     for (size_t e = 0; e < nm; ++e) out[e] += b * Y[e];
   }
-  free(Rm); free(U); free(U2); free(M); free(Y); free(piv);
+  free(Rm); free(U); free(U2); free(Y);
+}
+
+/* r(B) R with complex B, c, b; R = NULL means I.  Returns info. */
+static int zapply(int n, const double complex* B, const orc_coeffs* cs, int form, int m,
+                  const double complex* R, double complex* out) {
+  double complex* lu = malloc((size_t)cs->k * n * n * sizeof(double complex));
+  int* piv = malloc((size_t)cs->k * n * sizeof(int));
+  int info = zfactor(n, B, cs, lu, piv);
+  if (!info) zapply_lu(n, B, cs, form, m, R, lu, piv, out);
+  free(lu); free(piv);
   return info;
 }
 
@@ -624,15 +645,17 @@ int orc_zexpmv(int n, const double complex* A, double t, const orc_coeffs* cs, i
   double h = t / (double)N;
   for (size_t e = 0; e < nn; ++e) B[e] = h * A[e];
   memcpy(W, V, nm * sizeof(double complex));
-  int info = 0;
-  /* the factorizations are redone per step here only to keep one code path;
-   * the result is identical to reusing them */
+  /* every M_i is factored once and its factors serve all N steps (Sec. 5.1
+   * remarks: the LU decomposition is done only once) */
+  double complex* lu = malloc((size_t)cs->k * nn * sizeof(double complex));
+  int* piv = malloc((size_t)cs->k * n * sizeof(int));
+  int info = zfactor(n, B, cs, lu, piv);
   for (long q = 0; q < N && !info; ++q) {
-    info = zapply(n, B, cs, form, m, W, Wn);
+    zapply_lu(n, B, cs, form, m, W, lu, piv, Wn);
     memcpy(W, Wn, nm * sizeof(double complex));
   }
   if (n_out) *n_out = N;
-  free(B); free(Wn);
+  free(B); free(Wn); free(lu); free(piv);
   return info;
 }
 
