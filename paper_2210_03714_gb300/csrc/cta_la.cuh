@@ -576,6 +576,9 @@ __device__ __noinline__ void cta_getrs_ll(int n, const T* LU, int lda, const int
   const int G = m >= NT ? 1 : min(BK, NT / m);  // groups sharing the k loop
   const int cpp = NT / G;                       // columns per pass
   const int g = tid / cpp, cl = tid % cpp;
+  // when G does not divide NT, the last NT - G cpp threads have no group: they
+  // only take part in the barriers
+  const bool busy = g < G;
   // row exchanges, in order (thread owns columns); none when piv is the identity
   int moved = 0;
   for (int k = tid; k < n; k += NT) moved |= (piv[k] != k);
@@ -613,7 +616,7 @@ __device__ __noinline__ void cta_getrs_ll(int n, const T* LU, int lda, const int
         T acc[BK];
 #pragma unroll
         for (int r = 0; r < BK; ++r) acc[r] = TT::zero();
-        if (c < m) {
+        if (busy && c < m) {
           const int kn = k1 - k0;
           const int kb = (kn * g) / G, ke = (kn * (g + 1)) / G;
           // eight loads in flight per thread before their FMAs
@@ -637,8 +640,9 @@ __device__ __noinline__ void cta_getrs_ll(int n, const T* LU, int lda, const int
           }
         }
         if (G > 1) {
+          if (busy)
 #pragma unroll
-          for (int r = 0; r < BK; ++r) part[((size_t)g * BK + r) * cpp + cl] = acc[r];
+            for (int r = 0; r < BK; ++r) part[((size_t)g * BK + r) * cpp + cl] = acc[r];
           __syncthreads();
           if (g == 0)
             for (int h = 1; h < G; ++h)
