@@ -73,6 +73,9 @@ def lib():
         L.orc_expm.argtypes = [C.c_int, dp, C.c_double, cp, C.c_int, C.c_double, C.c_int, dp, ip]
         L.orc_phi1.argtypes = [C.c_int, dp, C.c_double, cp, cp, C.c_int, C.c_double, C.c_int,
                                dp, dp, ip]
+        L.orc_trig.argtypes = [C.c_int, dp, C.c_double, cp, cp, C.c_int, C.c_double, C.c_int,
+                               dp, dp, ip]
+        L.orc_rfun.argtypes = [C.c_int, dp, C.c_double, cp, C.c_int, dp]
         L.orc_expmv.argtypes = [C.c_int, dp, C.c_double, cp, C.c_int, C.c_double, C.c_long,
                                 C.c_int, dp, dp, lp]
         L.orc_phi1mv.argtypes = [C.c_int, dp, C.c_double, cp, cp, C.c_int, C.c_double, C.c_int,
@@ -195,6 +198,29 @@ def phi1(A, t=1.0, ce="R8", cp="R8_phi1", form=ROUNDOFF, anorm=0.0, s=None):
     info = lib().orc_phi1(n, _dp(A), float(t), ce.ptr(), cp.ptr(), form, float(anorm),
                           -1 if s is None else int(s), _dp(Phi), _dp(E), C.byref(so))
     return Phi, E, so.value, info
+
+
+def trig(A, t=1.0, cc="R8_cos", cs="R8_sin", form=ROUNDOFF, anorm=0.0, s=None):
+    """(cos(tA), sin(tA), s, info) by the double-angle recurrence."""
+    A = _f64(A)
+    n = A.shape[0]
+    cc, cs = _cs(cc), _cs(cs)
+    Cm = np.zeros((n, n))
+    Sm = np.zeros((n, n))
+    so = C.c_int(0)
+    info = lib().orc_trig(n, _dp(A), float(t), cc.ptr(), cs.ptr(), form, float(anorm),
+                          -1 if s is None else int(s), _dp(Cm), _dp(Sm), C.byref(so))
+    return Cm, Sm, so.value, info
+
+
+def rfun(A, t=1.0, cs="frac4_log1m", form=ROUNDOFF):
+    """(r(tA), info) with no range reduction."""
+    A = _f64(A)
+    n = A.shape[0]
+    cs = _cs(cs)
+    F = np.zeros((n, n))
+    info = lib().orc_rfun(n, _dp(A), float(t), cs.ptr(), form, _dp(F))
+    return F, info
 
 
 def expmv(A, V, t=1.0, cs="R8", form=ROUNDOFF, anorm=0.0, nsteps=0):

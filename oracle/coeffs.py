@@ -44,7 +44,23 @@ def taylor_log1m(k):
     return Fr(0) if k == 0 else Fr(-1, k)
 
 
-TAYLOR = {"exp": taylor_exp, "phi1": taylor_phi1, "log1m": taylor_log1m}
+def taylor_phi2(k):
+    """a_k for phi_2(x) = (e^x - 1 - x)/x^2: 1/(k+2)! (Sec. 1, the phi-functions)."""
+    return Fr(1, factorial(k + 2))
+
+
+def taylor_cos(k):
+    """a_k for cos(x): (-1)^(k/2)/k! for even k, 0 for odd k."""
+    return Fr(0) if k % 2 else Fr((-1) ** (k // 2), factorial(k))
+
+
+def taylor_sin(k):
+    """a_k for sin(x): (-1)^((k-1)/2)/k! for odd k, 0 for even k."""
+    return Fr((-1) ** ((k - 1) // 2), factorial(k)) if k % 2 else Fr(0)
+
+
+TAYLOR = {"exp": taylor_exp, "phi1": taylor_phi1, "phi2": taylor_phi2, "log1m": taylor_log1m,
+          "cos": taylor_cos, "sin": taylor_sin}
 
 
 # ---------------------------------------------------------------------------
@@ -191,6 +207,11 @@ def build_sets():
     c = _alpha_c(5, [1, Fr(2, 3), Fr(1, 2), Fr(2, 5)])
     S["R8"] = CoeffSet("R8", c, solve_b_plain(c, "exp"), "exp", 8)
     S["R8_phi1"] = CoeffSet("R8_phi1", c, solve_b_plain(c, "phi1"), "phi1", 8)
+    # Sec. 1: cos and sin (double-angle formulae) and phi_2 from the same R8
+    # resolvents, their weights from Eq. (LinearEqsbi) with their Taylor a_k
+    S["R8_cos"] = CoeffSet("R8_cos", c, solve_b_plain(c, "cos"), "cos", 8)
+    S["R8_sin"] = CoeffSet("R8_sin", c, solve_b_plain(c, "sin"), "sin", 8)
+    S["R8_phi2"] = CoeffSet("R8_phi2", c, solve_b_plain(c, "phi2"), "phi2", 8)
     # Sec. 4.4, Eq. (Frac5bi0): R5, c1 = 0, c_i = 1/(i+1), i = 2..6
     c = [Fr(0)] + [Fr(1, i + 1) for i in range(2, 7)]
     S["R5"] = CoeffSet("R5", c, solve_b_plain(c, "exp"), "exp", 5)

@@ -418,6 +418,55 @@ int orc_phi1(int n, const double* A, double t, const orc_coeffs* ce, const orc_c
   return info;
 }
 
+/* cos(tA) and sin(tA) from one set of resolvents: the two sets share the c_i
+ * (Sec. 2: another function from the same F_i only needs new b_i), scaling
+ * B = tA/2^s, then s steps of the double-angle formulae of Sec. 1,
+ * cos(2X) = 2 cos(X)^2 - I and sin(2X) = 2 sin(X) cos(X).
+ * theta = min of the two sets. */
+int orc_trig(int n, const double* A, double t, const orc_coeffs* cc, const orc_coeffs* cs,
+             int form, double anorm, int s_fixed, double* C, double* S, int* s_out) {
+  size_t nn = (size_t)n * n;
+  if (!all_finite(nn, A) || !isfinite(t)) return -2;
+  double* B = malloc(nn * sizeof(double));
+  double* T = malloc(nn * sizeof(double));
+  double* T2 = malloc(nn * sizeof(double));
+  for (size_t e = 0; e < nn; ++e) B[e] = t * A[e];
+  double eta = anorm > 0.0 ? anorm * fabs(t) : orc_norm1(n, B);
+  double th = cc->theta < cs->theta ? cc->theta : cs->theta;
+  int s = s_fixed >= 0 ? s_fixed : orc_select_s(eta, th);
+  for (size_t e = 0; e < nn; ++e) B[e] = ldexp(B[e], -s);
+  const orc_coeffs* sets[2] = {cc, cs};
+  double* outs[2] = {C, S};
+  int info = orc_rational_apply(n, B, 2, sets, form, n, NULL, outs);
+  for (int q = 0; q < s && !info; ++q) {
+    matmul(n, n, n, S, C, T);   /* sin(X) cos(X) */
+    matmul(n, n, n, C, C, T2);  /* cos(X)^2 */
+    for (size_t e = 0; e < nn; ++e) {
+      S[e] = 2.0 * T[e];
+      C[e] = 2.0 * T2[e];
+    }
+    for (int r = 0; r < n; ++r) C[(size_t)r * n + r] -= 1.0;
+  }
+  if (s_out) *s_out = s;
+  free(B); free(T); free(T2);
+  return info;
+}
+
+/* r(tA) for one set, with no range reduction: B = tA and r(B) as Sec. 2
+ * defines it (f(B) ~ r(B) for sufficiently small ||B||; e.g. the weights for
+ * log(1 - x) printed after Eq. Frac4bi0, for which the paper gives no scaling). */
+int orc_rfun(int n, const double* A, double t, const orc_coeffs* cs, int form, double* F) {
+  size_t nn = (size_t)n * n;
+  if (!all_finite(nn, A) || !isfinite(t)) return -2;
+  double* B = malloc(nn * sizeof(double));
+  for (size_t e = 0; e < nn; ++e) B[e] = t * A[e];
+  const orc_coeffs* sets[1] = {cs};
+  double* outs[1] = {F};
+  int info = orc_rational_apply(n, B, 1, sets, form, n, NULL, outs);
+  free(B);
+  return info;
+}
+
 /* ------------------------------------------------------------------------ */
 /* action: exp(tA) V by N steps of r(tA/N) with the LU reused (Sec. 1, 2, 5) */
 /* ------------------------------------------------------------------------ */

@@ -15,6 +15,12 @@ Parity status per oracle function:
   orc_phi1mv ... phi1(A) V product of a pinned matrix                  pinned
   orc_expmv_adjoint ... central finite differences, full FD at d = 4   pinned
   orc_zexpm / zexpmv ... Hermitian closed form, unitarity              pinned
+  orc_trig (cos, sin; double angle) ... nilpotent Taylor sums, 50-digit
+               scalar recurrence on eigenvalues, Re/Im of the complex
+               exponential, cos^2 + sin^2 = I (tests/test_oracle_functions.py) pinned
+  orc_rfun (r(tA), no range reduction; log(1 - x), phi_2) ... nilpotent
+               Taylor sums, 50-digit scalars, the forward bound of Sec. 3
+               against log(1 - x) (tests/test_oracle_functions.py)   pinned
 """
 from fractions import Fraction as Fr
 
@@ -121,7 +127,8 @@ def _exact_poly(cs, Bq, n, form):
     return np.array([[float(v) for v in row] for row in out])
 
 
-@pytest.mark.parametrize("name", ["R4", "R8", "R8_phi1", "R10", "frac4_log1m"])
+@pytest.mark.parametrize("name", ["R4", "R8", "R8_phi1", "R10", "frac4_log1m", "R8_cos", "R8_sin",
+                                  "R8_phi2"])
 @pytest.mark.parametrize("form", [oracle.ROUNDOFF, oracle.PLAIN])
 def test_nilpotent_exact(name, form):
     """B strictly upper triangular (B^n = 0): r(B) = sum_{k<n} alpha_k B^k exactly
