@@ -48,7 +48,7 @@ def load_peaks():
 # DRAM bytes (read + write) per launch of the persistent kernel on the full
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
 # None until captured for the current kernel.
-TRAFFIC = {"mixed": None, "fp64": None}
+TRAFFIC = {"mixed": None, "fp64": None, "grid": None}
 
 
 class Clocks:
@@ -141,15 +141,66 @@ def pipe_work(dims, s, precision, systems=4, max_ir=2, digits=7):
             "tensor_bf16": float(np.sum((1 + systems * max_ir + sv) * pairs * 2.0 * d3))}
 
 
+MEASURED = {}  # peaks measured in this run (measure_peaks)
+
+
+def measure_peaks(dev):
+    """FP64 and FP32 dense peaks of this GPU, measured at the start of the run:
+    the best of several torch.matmul calls (cuBLAS DGEMM 4096^3, SGEMM 8192^3
+    with TF32 off), each timed with CUDA events on the current stream."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n, reps in (("fp64", torch.float64, 4096, 3), ("fp32", torch.float32, 8192, 5)):
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            c = a @ b
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                torch.matmul(a, b, out=c)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = (2.0 * n ** 3 / (best / 1000.0) / 1e12,
+                         "measured: torch.matmul %s %d^3 (cuBLAS), best of %d, CUDA events"
+                         % (str(dt).replace("torch.", ""), n, reps))
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    torch.cuda.empty_cache()
+    MEASURED.update(out)
+    return out
+
+
 def pipe_peaks(peaks):
-    """TFLOP/s per pipe.  BF16 tensor: the measured burst figure; FP32 and FP64
-    are derived from unit counts and the maximum SM clock (152 SMs; 128 FP32
-    lanes and, on GB300, about 2 FP64 FMA per SM per clock)."""
+    """TFLOP/s per pipe.  BF16 tensor: the driver's measured burst figure; FP64
+    and FP32: measured in this run by measure_peaks (cuBLAS through torch), else
+    derived from unit counts and the maximum SM clock (152 SMs; 128 FP32 lanes
+    and, on GB300, about 2 FP64 FMA per SM per clock)."""
     mhz = peaks.get("sm_max_mhz", 2070.0)
-    return {"fp32": (152 * 128 * 2 * mhz * 1e6 / 1e12, "derived: 152 SMs x 128 lanes x 2 x max clock"),
-            "fp64": (152 * 2 * 2 * mhz * 1e6 / 1e12, "derived: 152 SMs x 2 DFMA x 2 x max clock"),
+    fp32 = MEASURED.get("fp32", (152 * 128 * 2 * mhz * 1e6 / 1e12,
+                                 "derived: 152 SMs x 128 lanes x 2 x max clock"))
+    fp64 = MEASURED.get("fp64", (152 * 2 * 2 * mhz * 1e6 / 1e12,
+                                 "derived: 152 SMs x 2 DFMA x 2 x max clock"))
+    return {"fp32": fp32, "fp64": fp64,
             "tensor_bf16": ((peaks["bf16_tflops"], "measured burst") if "bf16_tflops" in peaks
                             else (1900.0, "fallback"))}
+
+
+def survey_flops(dims, s, k=8):
+    """The algorithmic count of the method per matrix, as the scope table states
+    it: k shifted systems (the R8 nodes), each an inverse of 8/3 d^3 flops (Sec. 1:
+    LU and d triangular solves), and s squarings of 2 d^3: (8/3 k + 2 s) d^3,
+    summed over the batch.  (The fused +-c pairs do less work than this count.)"""
+    import numpy as np
+    d3 = np.asarray(dims, dtype=np.float64) ** 3
+    return float(np.sum((8.0 / 3.0 * k + 2.0 * np.asarray(s, dtype=np.float64)) * d3))
 
 
 def roofline_of(work, ms, peaks):
@@ -195,7 +246,7 @@ def cpu_baseline(dims, norms, sample, gpu_F=None, P=None):
                 seconds=dt), errs
 
 
-def run_single(args):
+def run_single(args, emit=True):
     """One large matrix on the grid path: the Hermitian action (A = -iH, d = 4096,
     V complex 4096 x 256, spectral radius 20, R8, N = 206) or exp of one real
     dense matrix of order --dim (entries N(0,1)/sqrt(d), ||A||_1 = 4, R8); or
@@ -228,7 +279,11 @@ def run_single(args):
                   "doublings (batched grid path)")
         ref = lambda: fm.phi1_batched(Pd, td, cs, cp, precision="fp64")[0]
     elif args.workload == "hermitian":
-        A, V, rho = wl.hermitian_action(d=4096, m=256, rho=20.0, seed=2000)
+        # the scale to spectral radius 20 stored with the oracle's result, so the
+        # comparison below sees the same A bit for bit
+        gpath = os.path.join(ROOT, "tests", "golden", "hermitian_d4096.npz")
+        scale = float(np.load(gpath)["scale"]) if os.path.exists(gpath) else None
+        A, V, rho = wl.hermitian_action(d=4096, m=256, rho=20.0, seed=2000, scale=scale)
         Ad = torch.tensor(A, dtype=torch.complex128, device=dev)
         Vd = torch.tensor(V, dtype=torch.complex128, device=dev)
         call = lambda prec: fm.expmv(Ad, Vd, 1.0, cs, precision=prec, anorm=rho)[0]
@@ -263,22 +318,54 @@ def run_single(args):
     ms = sum(per) / len(per)
     peaks = load_peaks()
     pk = pipe_peaks(peaks)
-    if args.precision == "mixed":
-        pipe, flops = "tensor_bf16", st["digit_flops"]
+    # the method's algorithmic flops per call (the scope table's count; complex
+    # arithmetic as 4 real flops per multiply-add)
+    if args.workload == "diffusion":
+        _, _, _, s_d = fm.phi1_batched(Pd, td, cs, cp, precision=args.precision)
+        sv = s_d.cpu().numpy().astype(float)
+        alg = float(np.sum((8.0 / 3.0 * 8 + 4.0 * sv) * 512.0 ** 3))
+    elif args.workload == "hermitian":
+        dd, mm, NN = 4096.0, 256.0, 206.0
+        alg = 8 * (8.0 / 3.0) * 4 * dd ** 3 + NN * (1 + 8) * 8 * dd * dd * mm
     else:
-        pipe, flops = "fp64", st["product_flops"]
-    step_ach = flops / (ms / 1000.0) / 1e12
+        _, _, s_d = fm.expm(Ad, 1.0, cs, precision=args.precision)
+        alg = (8.0 / 3.0 * 8 + 2.0 * s_d) * float(args.dim) ** 3
+    if args.precision == "mixed":
+        pipe, work = "tensor_bf16", st["digit_flops"]
+    else:
+        pipe, work = "fp64", st["product_flops"]
+    step_ach = alg / (ms / 1000.0) / 1e12
     kern_s = st["tile_ms"] / 1000.0
-    ach = flops / kern_s / 1e12 if (pipe == "tensor_bf16" and kern_s > 0) else step_ach
+    ach = alg / kern_s / 1e12 if (pipe == "tensor_bf16" and kern_s > 0) else step_ach
     roofline = {"bound": "tensor" if pipe == "tensor_bf16" else "alu",
                 "kernel": "oz_tiles" if pipe == "tensor_bf16" else "all",
                 "pipe": pipe, "achieved": ach, "peak": pk[pipe][0], "peak_source": pk[pipe][1],
                 "unit": "TFLOP/s", "frac": ach / pk[pipe][0], "traffic": None,
-                "kernel_ms": st["tile_ms"], "step_achieved": step_ach,
+                "flops_per_call": alg, "kernel_ms": st["tile_ms"], "step_achieved": step_ach,
                 "step_frac": step_ach / pk[pipe][0],
-                "note": "tensor: digit-pair flops (pairs kept per product flop) over the tile "
-                        "launches' CUDA-event time; fp64: product flops over the call; step_* "
-                        "over the whole call"}
+                "vs_fp64_peak": ach / pk["fp64"][0],
+                "note": "the method's algorithmic flops per call over the tile launches' "
+                        "CUDA-event time (tensor) or the whole call (fp64); step_* over the "
+                        "whole call"}
+    if pipe == "tensor_bf16" and kern_s > 0:
+        roofline["tensor_busy"] = {"achieved": work / kern_s / 1e12,
+                                   "frac": work / kern_s / 1e12 / pk[pipe][0],
+                                   "note": "digit-pair products issued over the tile time"}
+    # against the oracle: the stored full-size result (three columns) for the
+    # Hermitian action, one matrix for the diffusion batch, one for dense exp
+    err_oracle = None
+    if not args.no_cpu_baseline:
+        import oracle
+        if args.workload == "hermitian":
+            gpath = os.path.join(ROOT, "tests", "golden", "hermitian_d4096.npz")
+            if os.path.exists(gpath):
+                g = np.load(gpath)
+                Wc = out.cpu().numpy()[:, g["cols"]]
+                err_oracle = float(np.linalg.norm(Wc - g["W_full"]) / np.linalg.norm(g["W_full"]))
+        elif args.workload == "diffusion":
+            Pref, _, _, _ = oracle.phi1(mats[0], ts[0], "R8", "R8_phi1")
+            got = Pd.get(out, 0).cpu().numpy()
+            err_oracle = float(np.linalg.norm(got - Pref) / np.linalg.norm(Pref))
     diff = None
     fp64_ms = None
     if not args.no_fp64 and args.precision == "mixed":
@@ -302,13 +389,14 @@ def run_single(args):
                                              "l2": "working set > L2"},
             "roofline": roofline, "products": st["products"],
             "corrections": st["corrections"], "fp64_ms": fp64_ms,
+            "rel_err_vs_oracle": err_oracle,
             "rel_diff_vs_fp64": diff, "clocks": clk}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
-def run_trid(args):
+def run_trid(args, emit=True):
     """The tridiagonal action: 32768 systems of order 1000 (the paper's d for
     trid{-1,2,-1}, Sec. 5 Fig. 4), R10 in the roundoff form (the paper's R'_10,
     13d flops per shifted solve and step) or the plain form (R_10, 8d), with
@@ -415,12 +503,12 @@ def run_trid(args):
             "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "status_nonzero": bad, "rel_err_vs_oracle_sample": err, "cpu_baseline": cpu,
             "clocks": clk}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
-def run_small(args):
+def run_small(args, emit=True):
     """The two latency-bound configurations on the one-CTA kernels: exp of one
     real d = 64 matrix (N(0,1) scaled to ||A||_1 = 2, R4, s = 10), and the
     gradient batch (256 matrices of order 128, N(0,1)/sqrt(d), R8 action with
@@ -508,9 +596,9 @@ def run_small(args):
                        "l2": "working set within L2 (latency-bound)"},
             "roofline": roofline, "clocks": clk}
     line.update(extra)
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_reference(args):
@@ -612,6 +700,37 @@ def whole_job_value(world, batch, ms):
     return world * batch / (ms / 1000.0)
 
 
+def other_configs(args):
+    """Short runs of the other configurations in the default run (a few steps
+    each, mixed form; the value, the roofline fraction and the error against
+    the oracle).  Each entry is the line the --workload run prints, reduced."""
+    import copy
+    import torch
+    out = {}
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config",
+            "roofline", "rel_err_vs_oracle", "rel_diff_vs_fp64", "rel_err_vs_oracle_sample",
+            "e2e", "cpu_baseline", "clocks", "s", "status_nonzero")
+    plan = (("single_d64_R4", "single", run_small, dict(steps=10, warmup=3)),
+            ("gradient_256x128", "adjoint", run_small, dict(steps=3, warmup=1)),
+            ("hermitian_action_d4096", "hermitian", run_single, dict(steps=2, warmup=1)),
+            ("diffusion_phi1_512x512", "diffusion", run_single, dict(steps=2, warmup=1)),
+            ("trid_action_32768x1000", "trid", run_trid, dict(steps=3, warmup=1)))
+    for name, wl_name, fn, kw in plan:
+        a = copy.copy(args)
+        a.workload = wl_name
+        a.no_fp64 = True
+        for k, v in kw.items():
+            setattr(a, k, v)
+        try:
+            r = fn(a, emit=False)
+            out[name] = {k: r[k] for k in keep if k in r}
+        except Exception as e:  # report, do not lose the main line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     global BATCH, DIMS, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -646,13 +765,22 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "cta", "grid"],
                     help="execution path of the mixed form for the batch (the double form "
                          "always runs one CTA per matrix)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the short runs of the other configurations in the default run")
     args = ap.parse_args()
+    if args.workload != "batch" and args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the "
+                          "oracle on the default batch workload only"}), flush=True)
+        return 0
     if args.workload == "trid":
-        return run_trid(args)
+        run_trid(args)
+        return 0
     if args.workload in ("single", "adjoint"):
-        return run_small(args)
+        run_small(args)
+        return 0
     if args.workload != "batch":
-        return run_single(args)
+        run_single(args)
+        return 0
     if args.batch != BATCH or args.dims:
         BATCH = args.batch
         if args.dims:
@@ -678,6 +806,7 @@ def main():
         return rank_max(x, world, dev)
 
     fm.lib()
+    measure_peaks(dev)
     dims, norms, flat = make_batch()
     P = fm.Packed(dims=[int(d) for d in dims], flat=torch.from_numpy(flat).to(dev))
     F = torch.empty_like(P.flat)
@@ -749,17 +878,29 @@ def main():
         # last timed call)
         pk = pipe_peaks(peaks)["tensor_bf16"]
         tile_s = st["tile_ms"] / 1000.0
-        ach = st["digit_flops"] / tile_s / 1e12 if tile_s > 0 else 0.0
-        step_ach = st["digit_flops"] / (ms / 1000.0) / 1e12
+        alg = survey_flops(dims, s_host)
+        ach = alg / tile_s / 1e12 if tile_s > 0 else 0.0
+        busy = st["digit_flops"] / tile_s / 1e12 if tile_s > 0 else 0.0
+        step_ach = alg / (ms / 1000.0) / 1e12
+        fp64_pk = pipe_peaks(peaks)["fp64"]
         roofline = {"bound": "tensor", "kernel": "oz_tiles", "pipe": "tensor_bf16",
                     "achieved": ach, "peak": pk[0], "peak_source": pk[1], "unit": "TFLOP/s",
-                    "frac": ach / pk[0], "traffic": None,
-                    "flops_per_step": st["digit_flops"], "products_per_step": st["products"],
+                    "frac": ach / pk[0], "traffic": TRAFFIC.get("grid") if BATCH == 4096 and not args.dims else None,
+                    "flops_per_step": alg, "flops_count": "(8/3 k + 2 s) d^3 per matrix, k = 8",
                     "kernel_ms_per_step": st["tile_ms"], "step_achieved": step_ach,
                     "step_frac": step_ach / pk[0],
-                    "note": "digit-pair flops of the step's products (the pairs kept, 28 at "
-                            "full accuracy, per product flop) over the tile launches' "
-                            "CUDA-event time; step_* over the whole step"}
+                    "vs_fp64_peak": ach / fp64_pk[0], "fp64_peak": fp64_pk[0],
+                    "fp64_peak_source": fp64_pk[1],
+                    "tensor_busy": {"achieved": busy, "frac": busy / pk[0],
+                                    "digit_flops_per_step": st["digit_flops"],
+                                    "products_per_step": st["products"],
+                                    "note": "digit-pair products the tile kernel issues (28 "
+                                            "pairs per product flop at full accuracy, fewer on "
+                                            "level-capped corrections) over its event time"},
+                    "note": "achieved = the method's algorithmic flops per step over the tile "
+                            "launches' CUDA-event time (each product is emulated by BF16 digit "
+                            "products, so the tensor pipe does ~28x this work: tensor_busy); "
+                            "step_* over the whole step"}
     else:
         roofline = roofline_of(pipe_work(dims, s_host, args.precision), ms, peaks)
         roofline["traffic"] = TRAFFIC.get(args.precision) if BATCH == 4096 and not args.dims else None
@@ -802,11 +943,16 @@ def main():
             "path": "grid" if grid_path else "cta",
             "mixed_cta_path_value": cta_value,
             "clocks": clk}
+    line["peaks_measured"] = {k: {"tflops": v[0], "source": v[1]} for k, v in MEASURED.items()}
     if rank == 0 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(dims, norms, args.cpu_sample, F, P)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         if errs:
             line["max_rel_err_vs_oracle_sample"] = max(errs)
+    if world == 1 and not args.no_configs:
+        del F64, P, F
+        torch.cuda.empty_cache()
+        line["configs"] = other_configs(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -29,14 +29,32 @@
  *    single-matrix calls after a synchronize):
  *        0       success
  *        > 0     exactly zero pivot: (term index i) * d + (1-based column);
- *                in the roundoff form a pair of nodes +c, -c is one system
- *                I - c^2 B^2 and reports the index of its first node
- *        -1      mixed precision: iterative refinement did not reach opts.ir_tol
+ *                a system that serves two terms (a pair of nodes +c, -c
+ *                of the roundoff form, I - c^2 B^2, or a conjugate pair)
+ *                reports the index of its first term
+ *        -1      FM_FP32_IR: iterative refinement did not reach opts.ir_tol;
+ *                FM_BF16_IR: the correction iteration did not converge
  *        -2      non-finite entry in A (or V, or t)
+ *        -3      adjoint: nsteps_dev[b] < 1 or > opts.nsteps (not computed)
+ *        -4      batched calls: d_dev[b] outside [1, dmax] (matrix b is left
+ *                out; its outputs are not written)
+ *        -5      fm_rfun: ||tA||_1 > theta, outside the accuracy range of the
+ *                set (the result is still computed)
+ *        -7      a bounded wait inside a tensor-core kernel ran out (the
+ *                kernel stopped early; the results of the call are invalid)
  *  - Outputs must not alias inputs.
  *  - Scratch: opts.workspace (device, opts.workspace_bytes >= fm_workspace_size)
- *    or, when NULL, a buffer the library allocates once per device and reuses
- *    (grown when a larger problem arrives; released at process exit).
+ *    or, when NULL, a buffer the library keeps per (device, stream): calls on
+ *    one stream share it in stream order, calls on different streams use
+ *    different buffers and may overlap.  A buffer is taken with
+ *    cudaMallocAsync on the call's stream the first time a problem does not
+ *    fit it (the smaller one is released with cudaFreeAsync on that stream,
+ *    after the work queued before it), so make the first call of each size
+ *    before capturing the stream into a graph.  Host threads that share a
+ *    stream take turns (a lock per buffer, held until the call has queued
+ *    its work).  Buffers are released at process exit; streams are told apart
+ *    by handle (cudaStreamPerThread by calling thread).  A caller-provided
+ *    opts.workspace must not be used by two calls that overlap on the GPU.
  *  - Errors: FM_EINVAL (bad pointer, value or coefficient set), FM_ESHAPE (bad
  *    dimension or leading dimension, or d beyond what the kernels support),
  *    FM_ENOMEM, FM_ECUDA (launch or runtime failure).  fm_last_error() returns
@@ -65,8 +83,14 @@ typedef enum {
 
 /* A coefficient set (Sec. 2 and 4).  k terms with nodes c_i and weights b_i
  * (c_i = 0 terms allowed: they cost no solve).  conj_pair = 1 means each term
- * stands for 2 Re(b_i / (1 - c_i x)) with complex c_i, b_i (Eq. Pade4, Pade4phi1;
- * real matrices only).  a0 = r(0); d1, d2 = hybrid polynomial part (Eq. Frac10).
+ * stands for 2 Re(b_i / (1 - c_i x)) with complex c_i, b_i (Eq. Pade4, Pade4phi1):
+ * on real matrices every such term is one real system
+ * I - 2 Re(c_i) B + |c_i|^2 B^2 after one product B^2 (Sec. 1: one product x^2
+ * and one inverse per pair of complex-conjugate roots); on complex matrices
+ * (z functions) the term means its analytic form
+ * b_i / (1 - c_i x) + conj(b_i) / (1 - conj(c_i) x), two complex systems.
+ * The tridiagonal action and the adjoint take sets with conj_pair = 0 only.
+ * a0 = r(0); d1, d2 = hybrid polynomial part (Eq. Frac10).
  * order = s of Eq. (approx1); theta = ||B|| threshold for the target tolerance
  * (Sec. 3).  Arrays are host memory of length k; c_im / b_im may be NULL for
  * real sets.  k <= FM_MAX_TERMS. */
@@ -84,8 +108,9 @@ typedef struct {
 } fm_coeffs;
 
 /* Built-in sets.  The b_i are those printed in the paper, or (FM_R8_PHI1,
- * FM_R4_PHI1_A5) the solution of Eq. (LinearEqsbi) with the printed c_i and
- * a_k = 1/(k+1)!.  theta is computed for the double-precision unit roundoff
+ * FM_R4_PHI1_A5, FM_R8_COS, FM_R8_SIN, FM_R8_PHI2) the exact solution of
+ * Eq. (LinearEqsbi) with the printed c_i and the Taylor coefficients a_k of
+ * the function.  theta is computed for the double-precision unit roundoff
  * 2^-53 from the forward bound of Sec. 3. */
 enum {
   FM_R4 = 0,         /* Eq. Frac4ci/Frac4bi, alpha = 5, exp, 4 solves          */
@@ -97,21 +122,47 @@ enum {
   FM_R10 = 6,        /* Eq. Frac10ci/Frac10bi, hybrid, 10 solves + B^2          */
   FM_R10_STAR = 7,   /* Eq. Frac10ciNO/Frac10biNO, hybrid, 10 solves + B^2      */
   FM_PADE22 = 8,     /* Eq. Pade4, one conjugate pair                           */
-  FM_PADE22_PHI1 = 9 /* Eq. Pade4phi1, one conjugate pair                       */
+  FM_PADE22_PHI1 = 9,/* Eq. Pade4phi1, one conjugate pair                       */
+  FM_R8_COS = 10,    /* R8 nodes, cos weights (Sec. 1, with fm_cossin)          */
+  FM_R8_SIN = 11,    /* R8 nodes, sin weights (shares R8_COS's solves)          */
+  FM_R8_PHI2 = 12,   /* R8 nodes, phi_2 weights (Sec. 1, the phi-functions)     */
+  FM_FRAC4_EXP = 13, /* c_i = 1/(i+1), i = 1..5, Eq. Frac4bi0 (exp)             */
+  FM_FRAC4_PHI1 = 14,/* same nodes, the printed phi_1 weights                   */
+  FM_FRAC4_LOG1M = 15/* same nodes, the printed log(1 - x) weights (fm_rfun)    */
 };
-#define FM_NUM_BUILTIN 10
+#define FM_NUM_BUILTIN 16
+
+/* Target functions of a set (its Taylor coefficients a_k, Eq. fB). */
+enum { FM_FUNC_EXP = 0, FM_FUNC_PHI1 = 1, FM_FUNC_PHI2 = 2, FM_FUNC_COS = 3, FM_FUNC_SIN = 4,
+       FM_FUNC_LOG1M = 5 };
 
 /* Fill *out with built-in set id.  The arrays point to static storage that
  * stays valid for the life of the process.  Returns FM_EINVAL for a bad id. */
 fm_status fm_coeffs_builtin(int id, fm_coeffs* out);
 
 /* Forward bound eps(x) = sum_{k>order} |a_k - alpha_k| x^k (Sec. 3) of a set
- * against target function func (0 = exp, 1 = phi_1), and the x at which it
- * reaches tol.  Host computation in extended precision.  Returns FM_EINVAL on
- * bad arguments. */
+ * against target function func (FM_FUNC_*), and the x at which it reaches
+ * tol.  Host computation in extended precision.  Returns FM_EINVAL on bad
+ * arguments. */
 fm_status fm_theta(const fm_coeffs* cs, int func, double tol, double* theta_out);
 
-enum { FM_FP64 = 0, FM_FP32_IR = 1 };   /* precision of the shifted solves      */
+/* Arithmetic of a call (opts.precision).  Every value is accurate to double.
+ *  FM_FP64     every step in double on the FP64 pipe (any path).
+ *  FM_FP32_IR  one-CTA kernels only: each shifted matrix factored and solved
+ *              in single precision, then opts.max_ir_iters steps of iterative
+ *              refinement whose residuals are accurate to double (real
+ *              matrices: products as exact BF16 digit products on the tensor
+ *              cores; complex: double products); info = -1 when the last
+ *              correction exceeds opts.ir_tol.
+ *  FM_BF16_IR  grid paths only: every matrix product is a BF16 digit product
+ *              on the tensor cores with exact accumulation (accurate to
+ *              double), and each shifted system is solved by the correction
+ *              iteration of FM_PATH_GRID, run to its own stop rule (at most 40
+ *              steps; info = -1 if it does not converge); opts.max_ir_iters
+ *              and opts.ir_tol are not used.
+ *  FM_MIXED    FM_FP32_IR on the one-CTA kernels, FM_BF16_IR on the grid
+ *              paths (the default). */
+enum { FM_FP64 = 0, FM_FP32_IR = 1, FM_BF16_IR = 2, FM_MIXED = 3 };
 enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       */
 /* Execution path.  FM_PATH_CTA: one thread block per matrix, every step in it
  * (LU with partial pivoting of each shifted matrix; d <= fm_max_dim()).
@@ -124,38 +175,40 @@ enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       
  * more correction); it needs the spectral radius of c_i B well below 1, as
  * every set here gives with ||B||_1 <= theta (||c_i B||_1 <= 0.05).  Products
  * run on the FP64 pipe (FM_FP64) or as BF16 digit products on the tensor cores
- * with exact accumulation (FM_FP32_IR), both accurate to double.  The action
- * forms the matrix r(B) once and applies it N times.  Calls on this path
- * synchronize their stream (s or N, the batch orders and the iteration counts
- * are read on the host).
- * FM_PATH_AUTO: single-matrix calls with d > fm_max_dim(), and batched exp,
- * phi_1 and phi_1 V in FM_FP32_IR with dmax >= 64, take the grid path;
- * everything else the one-CTA kernels. */
+ * with exact accumulation (FM_BF16_IR, FM_MIXED), both accurate to double.
+ * The action forms the matrix r(B) once and applies it N times.  Calls on
+ * this path synchronize their stream (s or N, the batch orders and the
+ * iteration counts are read on the host).
+ * FM_PATH_AUTO: FM_BF16_IR calls, single-matrix calls with d > fm_max_dim(),
+ * and batched exp, phi_1 and phi_1 V in FM_MIXED with dmax >= 64 take the grid
+ * path; everything else the one-CTA kernels.  A precision value and a path
+ * that do not go together (FM_FP32_IR with FM_PATH_GRID, FM_BF16_IR with
+ * FM_PATH_CTA, a batched action on the grid path) give FM_EINVAL. */
 enum { FM_PATH_AUTO = 0, FM_PATH_CTA = 1, FM_PATH_GRID = 2 };
 
 typedef struct {
-  int precision;      /* FM_FP64: every step in double.  FM_FP32_IR: factor and
-                         solve in single, then max_ir_iters steps of iterative
-                         refinement with double-accurate residuals.            */
+  int precision;      /* FM_FP64, FM_FP32_IR, FM_BF16_IR or FM_MIXED (above)    */
   int form;           /* FM_ROUNDOFF (default) or FM_PLAIN                      */
   int max_ir_iters;   /* refinement steps for FM_FP32_IR (default 2)            */
   double ir_tol;      /* info = -1 when the last correction exceeds ir_tol times
                          the solution (max norms); 0 disables (default 1e-8)    */
   double anorm;       /* > 0: use anorm*|t| in place of ||tA||_1 to pick s / N  */
-  int s_fixed;        /* >= 0: force s for matrix functions (default -1)        */
+  int s_fixed;        /* >= 0: force s for matrix functions (default -1); -2:
+                         s = 0 and info -5 when ||tA||_1 > theta (fm_rfun)     */
   long nsteps;        /* > 0: force N for actions (default 0)                   */
   void* workspace;    /* device scratch or NULL                                 */
   size_t workspace_bytes;
   int path;           /* FM_PATH_AUTO (default), FM_PATH_CTA or FM_PATH_GRID     */
 } fm_opts;
 
-/* Defaults: FM_FP32_IR, FM_ROUNDOFF, 2 refinement steps, ir_tol 1e-8, automatic
- * s and N, library-managed workspace. */
+/* Defaults: FM_MIXED, FM_ROUNDOFF, 2 refinement steps, ir_tol 1e-8, automatic
+ * s and N, library-managed workspace, FM_PATH_AUTO. */
 void fm_opts_default(fm_opts* o);
 
 /* Job kinds for fm_workspace_size. */
 enum { FM_JOB_EXPM = 0, FM_JOB_PHI1 = 1, FM_JOB_EXPMV = 2, FM_JOB_PHI1MV = 3,
-       FM_JOB_ZEXPM = 4, FM_JOB_ZEXPMV = 5, FM_JOB_EXPMV_ADJ = 6 };
+       FM_JOB_ZEXPM = 4, FM_JOB_ZEXPMV = 5, FM_JOB_EXPMV_ADJ = 6, FM_JOB_COSSIN = 7,
+       FM_JOB_RFUN = 8 };
 
 /* Bytes of device scratch a call of that job needs for matrices up to dmax, m
  * vectors, k terms, on the current device. */
@@ -235,6 +288,34 @@ fm_status fm_zexpmv_batched(const fm_coeffs* cs, int batch, int dmax, const int*
                             const int64_t* voff_dev, const double* V, double* W, int* info_dev,
                             int* s_dev, const fm_opts* opts, void* stream);
 
+/* ---- other functions from the same resolvents (Sec. 1, Sec. 2) ---------- */
+/* C = cos(tA) and (if S != NULL) S = sin(tA), real A: both from one set of
+ * shifted solves with two weight vectors cc and cs over the same nodes
+ * (Sec. 2; FM_R8_COS and FM_R8_SIN), B = tA/2^s with theta the smaller of the
+ * two sets', then s steps of the double-angle formulae of Sec. 1,
+ * (C, S) <- (2 C^2 - I, 2 S C).  Each step can multiply the rounding by about
+ * 4 ||C||: the results are accurate to about 4^s u.  Layout, paths and status
+ * as fm_phi1 (C takes the place of Phi, S of E). */
+fm_status fm_cossin(const fm_coeffs* cc, const fm_coeffs* cs, int d, const double* A, int lda,
+                    double t, double* C, int ldc, double* S, int lds, const fm_opts* opts,
+                    void* stream, int* info_host, int* s_host);
+fm_status fm_cossin_batched(const fm_coeffs* cc, const fm_coeffs* cs, int batch, int dmax,
+                            const int* d_dev, const int64_t* off_dev, const double* A,
+                            const double* t_dev, double* C, double* S, int* info_dev, int* s_dev,
+                            const fm_opts* opts, void* stream);
+
+/* F = r(tA) for any set, with no range reduction: B = tA, F = r(B) (Sec. 2:
+ * f(B) ~ r(B) for sufficiently small ||B||).  For functions the paper gives no
+ * scaling for, such as log(1 - x) with the weights printed after Eq.
+ * Frac4bi0 (FM_FRAC4_LOG1M), or phi_2 (FM_R8_PHI2).  info = -5 when
+ * ||tA||_1 > theta (the result is still written).  Paths, layout and the other
+ * status values as fm_expm; opts.s_fixed is ignored. */
+fm_status fm_rfun(const fm_coeffs* cs, int d, const double* A, int lda, double t, double* F,
+                  int ldf, const fm_opts* opts, void* stream, int* info_host);
+fm_status fm_rfun_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                          const int64_t* off_dev, const double* A, const double* t_dev, double* F,
+                          int* info_dev, const fm_opts* opts, void* stream);
+
 /* ---- adjoint of the action (real, roundoff form, one vector) ----------- */
 /* For each matrix of the batch: the forward map w_0 = v, w_q = r(B) w_{q-1}
  * (q = 1..N, B = tA/N with N = nsteps_dev[b] fixed, as fm_expmv computes it),
@@ -249,6 +330,28 @@ fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, con
                                    const double* v, const double* wbar, double* W,
                                    double* Abar, double* vbar, int* info_dev,
                                    const fm_opts* opts, void* stream);
+
+/* ---- step a1 alone: the scaling each call would choose ------------------ */
+/* For each matrix of a batch (layout of the batched calls: order d_dev[b] <=
+ * dmax, dense at A + off_dev[b], time t_dev[b]): eta = ||t_b A_b||_1, the
+ * largest column sum of |t_b a_ij| (or opts.anorm |t_b|), and then what the
+ * call of that job chooses from it (Sec. 1: N such that ||A/N|| < theta, N = 2^s
+ * for scaling and squaring; theta from the forward bound of Sec. 3):
+ *   job FM_JOB_EXPM, FM_JOB_PHI1, FM_JOB_PHI1MV, FM_JOB_ZEXPM:
+ *       out_dev[b] = s, the smallest s >= 0 with eta / 2^s <= theta
+ *       (opts.s_fixed >= 0: s_fixed);
+ *   job FM_JOB_EXPMV, FM_JOB_ZEXPMV, FM_JOB_EXPMV_ADJ:
+ *       out_dev[b] = N = max(1, ceil(eta / theta)) (opts.nsteps > 0: nsteps),
+ *       the step count that fm_expmv_adjoint_batched takes as nsteps_dev.
+ * theta is that of cs (phi_1 jobs: the smaller of cs and cphi).  FM_JOB_Z*
+ * read A as complex.  out_dev (device, 64-bit long per matrix), info_dev
+ * (device): 0, -2 (non-finite entry of A_b or t_b) or -4 (d_dev[b] outside
+ * [1, dmax]; out_dev[b] = 0).  One launch, no synchronization.  Errors:
+ * FM_EINVAL (NULL pointer, bad job or set), FM_ESHAPE, FM_ECUDA. */
+fm_status fm_select_batched(const fm_coeffs* cs, const fm_coeffs* cphi, int job, int batch,
+                            int dmax, const int* d_dev, const int64_t* off_dev, const double* A,
+                            const double* t_dev, long* out_dev, int* info_dev, const fm_opts* opts,
+                            void* stream);
 
 /* ---- actions of tridiagonal matrices (Sec. 2.1, Sec. 5) ------------------ */
 /* W_b = r(B_b)^(N_b) V_b ~ exp(t_b A_b) V_b for a batch of tridiagonal A_b of one

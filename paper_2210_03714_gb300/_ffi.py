@@ -15,11 +15,15 @@ c_lp = C.POINTER(C.c_long)
 c_i64p = C.POINTER(C.c_int64)
 
 FM_OK, FM_EINVAL, FM_ESHAPE, FM_ENOMEM, FM_ECUDA, FM_ESINGULAR, FM_ENOCONV, FM_ETIMEOUT = range(8)
-FM_FP64, FM_FP32_IR = 0, 1
+FM_FP64, FM_FP32_IR, FM_BF16_IR, FM_MIXED = 0, 1, 2, 3
+PRECISION = {"fp64": FM_FP64, "fp32_ir": FM_FP32_IR, "bf16_ir": FM_BF16_IR, "mixed": FM_MIXED}
 FM_ROUNDOFF, FM_PLAIN = 0, 1
 BUILTIN = {"R4": 0, "R4_phi1": 1, "R4_phi1_a5": 2, "R8": 3, "R8_phi1": 4, "R5": 5, "R10": 6,
-           "R10star": 7, "pade22": 8, "pade22_phi1": 9}
-JOB = {"expm": 0, "phi1": 1, "expmv": 2, "phi1mv": 3, "zexpm": 4, "zexpmv": 5, "expmv_adj": 6}
+           "R10star": 7, "pade22": 8, "pade22_phi1": 9, "R8_cos": 10, "R8_sin": 11,
+           "R8_phi2": 12, "frac4_exp": 13, "frac4_phi1": 14, "frac4_log1m": 15}
+JOB = {"expm": 0, "phi1": 1, "expmv": 2, "phi1mv": 3, "zexpm": 4, "zexpmv": 5, "expmv_adj": 6,
+       "cossin": 7, "rfun": 8}
+FUNC = {"exp": 0, "phi1": 1, "phi2": 2, "cos": 3, "sin": 4, "log1m": 5}
 MAX_TERMS = 16
 
 
@@ -98,6 +102,17 @@ _SIGS = {
     "fm_trid_expmv_batched": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, C.c_int, _P, _P, _P, _P,
                                         _P, _P, _P, _P, C.POINTER(fm_opts), _P]),
     "fm_trid_workspace_size": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "fm_cossin": (C.c_int, [C.POINTER(fm_coeffs), C.POINTER(fm_coeffs), C.c_int, _P, C.c_int,
+                            C.c_double, _P, C.c_int, _P, C.c_int, C.POINTER(fm_opts), _P, c_ip,
+                            c_ip]),
+    "fm_cossin_batched": (C.c_int, [C.POINTER(fm_coeffs), C.POINTER(fm_coeffs), C.c_int, C.c_int,
+                                    _P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(fm_opts), _P]),
+    "fm_rfun": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, _P, C.c_int, C.c_double, _P, C.c_int,
+                          C.POINTER(fm_opts), _P, c_ip]),
+    "fm_rfun_batched": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, C.c_int, _P, _P, _P, _P, _P, _P,
+                                  C.POINTER(fm_opts), _P]),
+    "fm_select_batched": (C.c_int, [C.POINTER(fm_coeffs), C.POINTER(fm_coeffs), C.c_int, C.c_int,
+                                    C.c_int, _P, _P, _P, _P, _P, _P, C.POINTER(fm_opts), _P]),
     "fm_expm_noalloc": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, _P, C.c_int, C.c_double, _P,
                                   C.c_int, C.POINTER(fm_opts), _P, c_ip, c_ip]),
     "fm_last_error": (C.c_char_p, []),
@@ -140,7 +155,7 @@ def default_opts(**kw):
     lib().fm_opts_default(C.byref(o))
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
-            v = {"fp64": FM_FP64, "mixed": FM_FP32_IR, "fp32_ir": FM_FP32_IR}[v]
+            v = PRECISION[v]
         if k == "form" and isinstance(v, str):
             v = {"roundoff": FM_ROUNDOFF, "plain": FM_PLAIN}[v]
         if k == "path" and isinstance(v, str):

@@ -158,6 +158,36 @@ def phi1mv(A, V, t=1.0, ce="R8", cphi="R8_phi1", precision="mixed", **kw):
     return (W.reshape(-1) if vec else W), info.value, s.value
 
 
+def cossin(A, t=1.0, cc="R8_cos", cs="R8_sin", precision="mixed", want_sin=True, **kw):
+    """(cos(tA), sin(tA) or None, info, s) from one set of shifted solves and the
+    double-angle recurrence (fm_cossin)."""
+    _need(A, torch.float64, "A")
+    d = A.shape[0]
+    Cm = torch.empty_like(A)
+    Sm = torch.empty_like(A) if want_sin else None
+    cc, cs = _cs(cc), _cs(cs)
+    o = _opts(precision, **kw)
+    info, s = C.c_int(0), C.c_int(0)
+    check(lib().fm_cossin(cc.ptr(), cs.ptr(), d, _p(A), _ld(A), float(t), _p(Cm), _ld(Cm), _p(Sm),
+                          _ld(Sm) if Sm is not None else d, C.byref(o), _stream(), C.byref(info),
+                          C.byref(s)))
+    return Cm, Sm, info.value, s.value
+
+
+def rfun(A, t=1.0, coeffs="frac4_log1m", precision="mixed", **kw):
+    """(r(tA), info) with no range reduction (fm_rfun); info -5 when
+    ||tA||_1 > theta."""
+    _need(A, torch.float64, "A")
+    d = A.shape[0]
+    F = torch.empty_like(A)
+    cs = _cs(coeffs)
+    o = _opts(precision, **kw)
+    info = C.c_int(0)
+    check(lib().fm_rfun(cs.ptr(), d, _p(A), _ld(A), float(t), _p(F), _ld(F), C.byref(o), _stream(),
+                        C.byref(info)))
+    return F, info.value
+
+
 # ---------------------------------------------------------------------------
 # batches
 # ---------------------------------------------------------------------------
@@ -227,6 +257,35 @@ def phi1_batched(P, t=1.0, ce="R8", cphi="R8_phi1", precision="mixed", want_exp=
                                 _p(P.flat), _p(td), _p(Phi), _p(E), _p(info), _p(s), C.byref(o),
                                 _stream()))
     return Phi, E, info, s
+
+
+def cossin_batched(P, t=1.0, cc="R8_cos", cs="R8_sin", precision="mixed", want_sin=True, **kw):
+    """(cos flat, sin flat or None, info, s) for a Packed batch (fm_cossin_batched)."""
+    n = len(P)
+    Cm = P.empty_like()
+    Sm = P.empty_like() if want_sin else None
+    info = torch.empty(n, dtype=torch.int32, device=P.flat.device)
+    s = torch.empty(n, dtype=torch.int32, device=P.flat.device)
+    td = _tdev(t, n, P.flat.device)
+    cc, cs = _cs(cc), _cs(cs)
+    o = _opts(precision, **kw)
+    check(lib().fm_cossin_batched(cc.ptr(), cs.ptr(), n, P.dmax, _p(P.d_dev), _p(P.off_dev),
+                                  _p(P.flat), _p(td), _p(Cm), _p(Sm), _p(info), _p(s), C.byref(o),
+                                  _stream()))
+    return Cm, Sm, info, s
+
+
+def rfun_batched(P, t=1.0, coeffs="frac4_log1m", precision="mixed", **kw):
+    """(r(t_b A_b) flat, info) for a Packed batch, no range reduction."""
+    n = len(P)
+    F = P.empty_like()
+    info = torch.empty(n, dtype=torch.int32, device=P.flat.device)
+    td = _tdev(t, n, P.flat.device)
+    cs = _cs(coeffs)
+    o = _opts(precision, **kw)
+    check(lib().fm_rfun_batched(cs.ptr(), n, P.dmax, _p(P.d_dev), _p(P.off_dev), _p(P.flat),
+                                _p(td), _p(F), _p(info), C.byref(o), _stream()))
+    return F, info
 
 
 def _voff(P, m):
@@ -311,26 +370,48 @@ def expmv_adjoint_batched(P, v, wbar, nsteps, t=1.0, coeffs="R8"):
     return W, Abar, vbar, info
 
 
-def nsteps_for(A, t=1.0, coeffs="R8"):
-    """N = max(1, ceil(||tA||_1 / theta)) as the action chooses it (host helper)."""
-    import math
+def select_batched(P, t=1.0, coeffs="R8", job="expmv", cphi=None, **kw):
+    """Step a1 alone (fm_select_batched): s or N per matrix of a Packed batch,
+    as the call of that job would choose it; returns (out int64, info)."""
+    n = len(P)
+    dev = P.flat.device
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    info = torch.empty(n, dtype=torch.int32, device=dev)
+    td = _tdev(t, n, dev)
     cs = _cs(coeffs)
-    eta = float(torch.linalg.matrix_norm(t * A, ord=1).item())
-    return max(1, math.ceil(eta / cs.theta))
+    cp = _cs(cphi) if cphi is not None else None
+    o = _opts("fp64", **kw)
+    check(lib().fm_select_batched(cs.ptr(), cp.ptr() if cp is not None else None, _ffi.JOB[job], n,
+                                  P.dmax, _p(P.d_dev), _p(P.off_dev), _p(P.flat), _p(td), _p(out),
+                                  _p(info), C.byref(o), _stream()))
+    return out, info
+
+
+def _raise_info(info, what):
+    bad = torch.nonzero(info != 0)
+    if bad.numel():
+        b = int(bad[0, 0])
+        raise _ffi.FmError(_ffi.FM_EINVAL, "%s: matrix %d has info %d" % (what, b, int(info[b])))
 
 
 class ExpmvFn(torch.autograd.Function):
     """w = exp(tA) v for a batch of equal-order real matrices, with the
     hand-written adjoint kernel as backward.  A: (batch, d, d) float64 CUDA,
-    v: (batch, d); nsteps: step counts, fixed (not differentiated)."""
+    v: (batch, d); nsteps: step counts, fixed (not differentiated); None
+    takes N = max(1, ceil(||tA||_1 / theta)) per matrix from the library.  A
+    nonzero status of any matrix raises FmError."""
 
     @staticmethod
-    def forward(ctx, A, v, nsteps, t=1.0, coeffs="R8"):
+    def forward(ctx, A, v, nsteps=None, t=1.0, coeffs="R8"):
         b, d, _ = A.shape
         P = Packed(dims=[d] * b, flat=A.reshape(-1).contiguous())
+        if nsteps is None:  # N as the action chooses it, computed on the device
+            nsteps, info = select_batched(P, t, coeffs, "expmv_adj")
+            _raise_info(info, "ExpmvFn step count")
         vf = v.reshape(-1).contiguous()
         zero = torch.zeros_like(vf)
-        W, _, _, _ = expmv_adjoint_batched(P, vf, zero, nsteps, t, coeffs)
+        W, _, _, info = expmv_adjoint_batched(P, vf, zero, nsteps, t, coeffs)
+        _raise_info(info, "ExpmvFn forward")
         ctx.save_for_backward(A, v)
         ctx.nsteps, ctx.t, ctx.coeffs = nsteps, t, coeffs
         return W.view(b, d)
@@ -340,7 +421,8 @@ class ExpmvFn(torch.autograd.Function):
         A, v = ctx.saved_tensors
         b, d, _ = A.shape
         P = Packed(dims=[d] * b, flat=A.reshape(-1).contiguous())
-        _, Abar, vbar, _ = expmv_adjoint_batched(P, v.reshape(-1).contiguous(),
-                                                 gw.reshape(-1).contiguous(), ctx.nsteps, ctx.t,
-                                                 ctx.coeffs)
+        _, Abar, vbar, info = expmv_adjoint_batched(P, v.reshape(-1).contiguous(),
+                                                    gw.reshape(-1).contiguous(), ctx.nsteps, ctx.t,
+                                                    ctx.coeffs)
+        _raise_info(info, "ExpmvFn backward")
         return Abar.view(b, d, d), vbar.view(b, d), None, None, None

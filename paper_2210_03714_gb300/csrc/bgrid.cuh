@@ -10,6 +10,7 @@
 // correction), F = a0 I + sum_i b_i Y_i (Eq. ParallRoundOff), and s
 // squarings of F = I + E as E <- 2E + E E.
 #pragma once
+#include "fm_job.h"
 #include "grid.cuh"
 
 namespace fmk {
@@ -39,6 +40,14 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
   __shared__ double red[32];
   const BMat M = mats[blockIdx.x];
   const int n = M.d, tid = threadIdx.x;
+  if (n == 0) {  // order outside [1, dmax]: left out of the call
+    if (tid == 0) {
+      if (s_out) s_out[blockIdx.x] = 0;
+      info[blockIdx.x] = -4;
+      alive[blockIdx.x] = 0;
+    }
+    return;
+  }
   const T* Ab = A + M.uoff;
   T* Bb = B + M.off;
   const double tb = t[blockIdx.x];
@@ -58,7 +67,9 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
   cmax = block_max(cmax, red);
   const double eta = anorm > 0 ? anorm * fabs(tb) : cmax;
   int s = s_fixed;
-  if (s < 0) {
+  if (s == kSRfun) {
+    s = 0;  // r(tA) as it is: no range reduction
+  } else if (s < 0) {
     s = 0;
     while (eta > ldexp(theta, s) && s < 1023) ++s;
   }
@@ -68,7 +79,7 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
   }
   if (tid == 0) {
     if (s_out) s_out[blockIdx.x] = s;
-    info[blockIdx.x] = bad ? -2 : 0;
+    info[blockIdx.x] = bad ? -2 : ((s_fixed == kSRfun && !(eta <= theta)) ? -5 : 0);
     alive[blockIdx.x] = !bad;
   }
 }
@@ -95,6 +106,21 @@ __global__ void b_build_shift(const BMat* mats, const int* mask, const T* B, dou
 #pragma unroll 4
   for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const T v = cmul<T>(cr, ci, B[M.off + e]);
+    C[M.off + e] = v;
+    Y[M.off + e] = v;
+  }
+}
+
+// C = u1 B + u2 B2 (each product rounded once; C = u2 B2 when u1 = 0); Y = C
+template <class T>
+__global__ void b_build_shift2(const BMat* mats, const int* mask, const T* B, double u1r,
+                               double u1i, const T* B2, double u2r, double u2i, T* C, T* Y) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+  const bool one = u1r == 0.0 && u1i == 0.0;
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    T v = cmul<T>(u2r, u2i, B2[M.off + e]);
+    if (!one) v = Tr<T>::add(cmul<T>(u1r, u1i, B[M.off + e]), v);
     C[M.off + e] = v;
     Y[M.off + e] = v;
   }

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -33,15 +35,24 @@ fm_status cuda_fail(cudaError_t e, const char* where) {
   return FM_ECUDA;
 }
 
-// ---- library-managed scratch (one buffer per device, grown on demand) -----
-struct DevBuf {
+// ---- library-managed scratch: one buffer per (device, stream) ---------------
+// Calls on one stream run in stream order, so they can share its buffer;
+// calls on different streams get different buffers and may overlap.  A buffer
+// grows stream-ordered: the old one is released with cudaFreeAsync on its
+// stream (after the work already queued there) and the new one taken with
+// cudaMallocAsync.  Each buffer has a lock that a call holds from the lookup
+// until it has queued its last launch, so host threads sharing a stream take
+// turns and never see a buffer freed under them.
+struct Scratch {
+  std::mutex mu;
   void* p = nullptr;
   size_t bytes = 0;
 };
 std::mutex g_mu;
-std::vector<DevBuf> g_bufs;
+std::map<std::pair<int, uintptr_t>, std::unique_ptr<Scratch>> g_bufs;
 
-fm_status get_scratch(size_t need, const fm_opts* o, void** out, cudaStream_t st) {
+fm_status get_scratch(size_t need, const fm_opts* o, void** out, cudaStream_t st,
+                      std::unique_lock<std::mutex>* hold) {
   if (o && o->workspace) {
     if (o->workspace_bytes < need) return fail(FM_ENOMEM, "opts.workspace is smaller than fm_workspace_size()");
     *out = o->workspace;
@@ -50,27 +61,34 @@ fm_status get_scratch(size_t need, const fm_opts* o, void** out, cudaStream_t st
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if ((int)g_bufs.size() <= dev) g_bufs.resize(dev + 1);
-  DevBuf& b = g_bufs[dev];
-  if (b.bytes < need) {
-    if (b.p) {
-      // the previous buffer may still be in use by earlier work on any stream
-      cudaDeviceSynchronize();
-      cudaFree(b.p);
-      b.p = nullptr;
-      b.bytes = 0;
+  // cudaStreamPerThread names a different stream in every host thread
+  static thread_local char per_thread_key;
+  const uintptr_t key = st == cudaStreamPerThread ? (uintptr_t)&per_thread_key : (uintptr_t)st;
+  Scratch* b;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    std::unique_ptr<Scratch>& slot = g_bufs[std::make_pair(dev, key)];
+    if (!slot) slot.reset(new Scratch);
+    b = slot.get();
+  }
+  *hold = std::unique_lock<std::mutex>(b->mu);
+  if (b->bytes < need) {
+    if (b->p) {
+      e = cudaFreeAsync(b->p, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync of the library scratch");
+      b->p = nullptr;
+      b->bytes = 0;
     }
-    size_t sz = need + need / 4;
-    e = cudaMalloc(&b.p, sz);
+    const size_t sz = need + need / 4;
+    e = cudaMallocAsync(&b->p, sz, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(FM_ENOMEM, "cudaMalloc of the library scratch failed");
+      b->p = nullptr;
+      return fail(FM_ENOMEM, "cudaMallocAsync of the library scratch failed");
     }
-    b.bytes = sz;
+    b->bytes = sz;
   }
-  (void)st;
-  *out = b.p;
+  *out = b->p;
   return FM_OK;
 }
 
@@ -92,12 +110,15 @@ fm_status pack_one(const fm_coeffs* cs, int f, bool complex_ok, FmCoef& cf) {
   if (!cs) return fail(FM_EINVAL, "coefficient set is NULL");
   if (cs->k < 1 || cs->k > FM_MAX_TERMS) return fail(FM_EINVAL, "coefficient set: k must be in [1, 16]");
   if (!cs->c_re || !cs->b_re) return fail(FM_EINVAL, "coefficient set: c_re and b_re are required");
-  if (cs->conj_pair) return fail(FM_EINVAL, "conjugate-pair sets are not supported by the CUDA kernels");
+  if (cs->conj_pair != 0 && cs->conj_pair != 1) return fail(FM_EINVAL, "coefficient set: conj_pair must be 0 or 1");
+  if (f == 1 && cs->conj_pair != cf.conj_pair)
+    return fail(FM_EINVAL, "the two coefficient sets must both be conjugate-pair sets or neither");
+  if (f == 0) cf.conj_pair = cs->conj_pair;
   for (int i = 0; i < cs->k; ++i) {
     double ci = cs->c_im ? cs->c_im[i] : 0.0, bi = cs->b_im ? cs->b_im[i] : 0.0;
     if (!isfinite(cs->c_re[i]) || !isfinite(ci) || !isfinite(cs->b_re[i]) || !isfinite(bi))
       return fail(FM_EINVAL, "coefficient set: non-finite value");
-    if (!complex_ok && (ci != 0.0 || bi != 0.0))
+    if (!complex_ok && !cs->conj_pair && (ci != 0.0 || bi != 0.0))
       return fail(FM_EINVAL, "complex c_i or b_i need the complex (z) entry points");
     if (f == 0) {
       cf.c_re[i] = cs->c_re[i];
@@ -124,6 +145,38 @@ fm_status pack_one(const fm_coeffs* cs, int f, bool complex_ok, FmCoef& cf) {
   return FM_OK;
 }
 
+// A conjugate-pair set on complex matrices: each term b_i c_i x / (1 - c_i x)
+// + conj(b_i) conj(c_i) x / (1 - conj(c_i) x) (the analytic form of 2 Re(...)),
+// written out as two terms (one for a real node, with weight 2 Re(b_i)).
+fm_status expand_conj(FmCoef& cf) {
+  FmCoef o = cf;
+  int k = 0;
+  for (int i = 0; i < cf.k; ++i) {
+    const bool real_node = cf.c_im[i] == 0.0;
+    if (k + (real_node ? 1 : 2) > kMaxTerms)
+      return fail(FM_EINVAL, "conjugate-pair set: more than 16 terms once written out for complex matrices");
+    o.c_re[k] = cf.c_re[i];
+    o.c_im[k] = cf.c_im[i];
+    for (int f = 0; f < 2; ++f) {
+      o.b_re[f][k] = real_node ? 2.0 * cf.b_re[f][i] : cf.b_re[f][i];
+      o.b_im[f][k] = real_node ? 0.0 : cf.b_im[f][i];
+    }
+    ++k;
+    if (real_node) continue;
+    o.c_re[k] = cf.c_re[i];
+    o.c_im[k] = -cf.c_im[i];
+    for (int f = 0; f < 2; ++f) {
+      o.b_re[f][k] = cf.b_re[f][i];
+      o.b_im[f][k] = -cf.b_im[f][i];
+    }
+    ++k;
+  }
+  o.k = k;
+  o.conj_pair = 0;
+  cf = o;
+  return FM_OK;
+}
+
 fm_status pack(const fm_coeffs* ce, const fm_coeffs* cp, bool complex_ok, int form, FmCoef& cf) {
   memset(&cf, 0, sizeof cf);
   fm_status s = pack_one(ce, 0, complex_ok, cf);
@@ -134,7 +187,11 @@ fm_status pack(const fm_coeffs* ce, const fm_coeffs* cp, bool complex_ok, int fo
     if (s) return s;
     cf.nfun = 2;
   }
-  if (form == FM_PLAIN)
+  if (cf.conj_pair && complex_ok) {
+    s = expand_conj(cf);
+    if (s) return s;
+  }
+  if (form == FM_PLAIN && !cf.conj_pair)
     for (int f = 0; f < cf.nfun; ++f)
       for (int i = 0; i < cf.k; ++i)
         if (cf.b_im[f][i] != 0.0) return fail(FM_EINVAL, "the plain form needs real weights b_i");
@@ -149,11 +206,11 @@ fm_opts resolve_opts(const fm_opts* o) {
 }
 
 fm_status check_opts(const fm_opts& o) {
-  if (o.precision != FM_FP64 && o.precision != FM_FP32_IR) return fail(FM_EINVAL, "opts.precision");
+  if (o.precision < FM_FP64 || o.precision > FM_MIXED) return fail(FM_EINVAL, "opts.precision");
   if (o.form != FM_ROUNDOFF && o.form != FM_PLAIN) return fail(FM_EINVAL, "opts.form");
   if (o.max_ir_iters < 0 || o.max_ir_iters > 20) return fail(FM_EINVAL, "opts.max_ir_iters must be in [0, 20]");
   if (!(o.ir_tol >= 0) || !isfinite(o.anorm) || o.anorm < 0) return fail(FM_EINVAL, "opts.ir_tol / opts.anorm");
-  if (o.s_fixed > 1000) return fail(FM_EINVAL, "opts.s_fixed");
+  if (o.s_fixed > 1000 || o.s_fixed < kSRfun) return fail(FM_EINVAL, "opts.s_fixed");
   if (o.nsteps < 0) return fail(FM_EINVAL, "opts.nsteps");
   if (o.path < FM_PATH_AUTO || o.path > FM_PATH_GRID) return fail(FM_EINVAL, "opts.path");
   return FM_OK;
@@ -184,7 +241,7 @@ Plan make_plan(int kind, bool cplx, int precision, int batch, int dmax, int m, i
   p.smem = smem_for(cplx, p.nb, dmax, precision);
   size_t elt, lelt;
   type_sizes(cplx, precision, elt, lelt);
-  int lk = kind == JOB_PHI1MV ? JOB_PHI1 : kind;
+  int lk = layout_kind(kind);
   p.per_cta =
       fm_align(ws_layout(lk, dmax, m, k, elt, lelt, nmax, uses_tc(cplx, precision)).total);
   int occ = launch_occupancy(cplx, precision, p.nb, p.smem);
@@ -196,6 +253,51 @@ Plan make_plan(int kind, bool cplx, int precision, int batch, int dmax, int m, i
   p.header = 256 + fm_align((size_t)batch * 4);
   p.total = p.header + (size_t)p.grid * p.per_cta;
   return p;
+}
+
+// Which kernels run a call.  FM_FP64 runs anywhere; FM_FP32_IR (single
+// factors + refinement) only on the one-CTA kernels; FM_BF16_IR (tensor-core
+// digit products in the correction iteration) only on the grid paths;
+// FM_MIXED picks by path.  The batched grid path takes exp, phi_1 and phi_1 V.
+enum Route { R_CTA = 0, R_GRID = 1, R_BGRID = 2, R_BAD = -1 };
+
+Route route(int kind, bool single, int dmax, int precision, int path, const char** why) {
+  const bool bg_kind = kind == JOB_EXPM || kind == JOB_PHI1 || kind == JOB_PHI1MV || kind == JOB_TRIG;
+  *why = "";
+  if (kind == JOB_ADJ) return R_CTA;
+  if (precision == FM_FP32_IR && path == FM_PATH_GRID) {
+    *why = "FM_FP32_IR runs on the one-CTA kernels; the grid paths take FM_FP64, FM_BF16_IR or FM_MIXED";
+    return R_BAD;
+  }
+  if (precision == FM_BF16_IR && path == FM_PATH_CTA) {
+    *why = "FM_BF16_IR runs on the grid paths; the one-CTA kernels take FM_FP64, FM_FP32_IR or FM_MIXED";
+    return R_BAD;
+  }
+  const bool want_grid = path == FM_PATH_GRID || precision == FM_BF16_IR;
+  if (single) {
+    if (want_grid) return R_GRID;
+    if (path == FM_PATH_AUTO && dmax > fm_max_dim()) {
+      if (precision == FM_FP32_IR) {
+        *why = "FM_FP32_IR runs on the one-CTA kernels (d <= fm_max_dim())";
+        return R_BAD;
+      }
+      return R_GRID;
+    }
+    return R_CTA;
+  }
+  if (want_grid) {
+    if (!bg_kind) {
+      *why = "the grid path takes batches of exp, phi_1 (and phi_1 V) and cos/sin only; other batched "
+             "jobs run on the one-CTA kernels (FM_PATH_CTA with FM_FP64, FM_FP32_IR or FM_MIXED)";
+      return R_BAD;
+    }
+    return R_BGRID;
+  }
+  // batches of exp and phi_1 in FM_MIXED with matrices of order 64 and up: the
+  // grid path (tensor-core products over the whole batch) is the faster one
+  if (path == FM_PATH_AUTO && bg_kind && precision == FM_MIXED && dmax >= 64 && dmax <= fm_max_dim())
+    return R_BGRID;
+  return R_CTA;
 }
 
 struct Call {
@@ -269,16 +371,17 @@ fm_status run_grid(const Call& c, const fm_opts& o, cudaStream_t st) {
   g.n_host = c.n_host;
   g.stats = &g_stats;
   g.ws_bytes = grid_ws_bytes(c.kind, c.cplx, o.precision, n, c.m);
-  s = get_scratch(g.ws_bytes, &o, &g.ws, st);
+  std::unique_lock<std::mutex> hold;  // the scratch stays ours until the work is queued
+  s = get_scratch(g.ws_bytes, &o, &g.ws, st, &hold);
   if (s) return s;
   return (fm_status)grid_run(g, g_err, sizeof g_err);
 }
 
 // a batch of exp over the whole GPU (fm_bgrid.cu)
 fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
-  if (c.kind != JOB_EXPM && c.kind != JOB_PHI1 && c.kind != JOB_PHI1MV)
-    return fail(FM_EINVAL, "the grid path takes batches of exp and phi_1 (and phi_1 V) only; "
-                           "other batched jobs: FM_PATH_CTA");
+  if (c.kind != JOB_EXPM && c.kind != JOB_PHI1 && c.kind != JOB_PHI1MV && c.kind != JOB_TRIG)
+    return fail(FM_EINVAL, "the grid path takes batches of exp, phi_1 (and phi_1 V) and cos/sin "
+                           "only; other batched jobs: FM_PATH_CTA");
   const bool act = c.kind == JOB_PHI1MV;
   if (!c.A || !c.d_dev || !c.off || !c.t_dev || !c.info_dev)
     return fail(FM_EINVAL, "batched calls need A, d_dev, off_dev, t_dev and info_dev");
@@ -298,8 +401,10 @@ fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
     e = cudaMemcpyAsync(voff.data(), c.voff, (size_t)c.batch * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "reading the batch orders");
+  // a matrix whose order is outside [1, dmax] is left out (order 0 in the
+  // tables: no tiles, no elements) and gets info = -4, as on the one-CTA path
   for (int b = 0; b < c.batch; ++b)
-    if (d[b] < 1 || d[b] > c.dmax) return fail(FM_ESHAPE, "a batch order is outside [1, dmax]");
+    if (d[b] < 1 || d[b] > c.dmax) d[b] = 0;
   j.kind = c.kind;
   j.cplx = c.cplx;
   j.form = o.form;
@@ -322,7 +427,8 @@ fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
   j.st = st;
   j.stats = &g_stats;
   j.ws_bytes = bgrid_ws_bytes(c.kind, c.cplx, c.batch, d.data());
-  s = get_scratch(j.ws_bytes, &o, &j.ws, st);
+  std::unique_lock<std::mutex> hold;  // the scratch stays ours until the work is queued
+  s = get_scratch(j.ws_bytes, &o, &j.ws, st, &hold);
   if (s) return s;
   return (fm_status)bgrid_run(j, g_err, sizeof g_err);
 }
@@ -335,20 +441,18 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   if (c.kind == JOB_ADJ) o.precision = FM_FP64;
   if (c.batch < 1) return fail(FM_ESHAPE, "batch must be >= 1");
   const bool single = c.d_dev == nullptr && c.kind != JOB_ADJ;
-  if (o.path == FM_PATH_GRID && !single) return run_bgrid(c, o, st);
-  // batches of exp in mixed precision with matrices of order 64 and up: the
-  // grid path (tensor-core products over the whole batch) is the faster one
-  if (o.path == FM_PATH_AUTO && !single &&
-      (c.kind == JOB_EXPM || c.kind == JOB_PHI1 || c.kind == JOB_PHI1MV) &&
-      o.precision != FM_FP64 && c.dmax >= 64 && c.dmax <= fm_max_dim())
-    return run_bgrid(c, o, st);
-  if (single && c.dmax >= 1 &&
-      (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && c.dmax > fm_max_dim())))
-    return run_grid(c, o, st);
+  const char* why = "";
+  const Route r = route(c.kind, single, c.dmax, o.precision, o.path, &why);
+  if (r == R_BAD) return fail(FM_EINVAL, why);
+  // the kernels see 0 (double) or 1 (single factors / tensor-core products)
+  o.precision = o.precision == FM_FP64 ? 0 : 1;
+  if (r == R_BGRID) return run_bgrid(c, o, st);
+  if (r == R_GRID && c.dmax >= 1) return run_grid(c, o, st);
   if (c.dmax < 1 || c.dmax > fm_max_dim()) return fail(FM_ESHAPE, "d (or dmax) must be in [1, fm_max_dim()]");
   if ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV) && c.m < 1) return fail(FM_ESHAPE, "m must be >= 1");
   if (!c.A) return fail(FM_EINVAL, "A is NULL");
-  if ((c.kind == JOB_EXPM || c.kind == JOB_PHI1) && !c.F) return fail(FM_EINVAL, "output is NULL");
+  if ((c.kind == JOB_EXPM || c.kind == JOB_PHI1 || c.kind == JOB_TRIG) && !c.F)
+    return fail(FM_EINVAL, "output is NULL");
   if ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV || c.kind == JOB_ADJ) && (!c.V || !c.W))
     return fail(FM_EINVAL, "V / W is NULL");
   if (c.d_dev) {
@@ -357,7 +461,7 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
       return fail(FM_EINVAL, "batched actions need voff_dev");
   } else {
     const int n = c.d1;
-    if (c.lda < n || ((c.kind == JOB_EXPM || c.kind == JOB_PHI1) && c.ldf < n) ||
+    if (c.lda < n || ((c.kind == JOB_EXPM || c.kind == JOB_PHI1 || c.kind == JOB_TRIG) && c.ldf < n) ||
         (c.E && c.lde < n) ||
         ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV) && (c.ldv < c.m || c.ldw < c.m)))
       return fail(FM_ESHAPE, "leading dimension smaller than the row length");
@@ -371,7 +475,8 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
 
   Plan p = make_plan(c.kind, c.cplx, o.precision, c.batch, c.dmax, c.m, cf.k, c.nsteps_max);
   void* ws = nullptr;
-  s = get_scratch(p.total, &o, &ws, st);
+  std::unique_lock<std::mutex> hold;  // the scratch stays ours until the work is queued
+  s = get_scratch(p.total, &o, &ws, st, &hold);
   if (s) return s;
 
   FmJob J;
@@ -447,7 +552,7 @@ extern "C" {
 void fm_opts_default(fm_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof *o);
-  o->precision = FM_FP32_IR;
+  o->precision = FM_MIXED;
   o->form = FM_ROUNDOFF;
   o->max_ir_iters = 2;
   o->ir_tol = 1e-8;
@@ -470,21 +575,25 @@ size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_op
     case FM_JOB_EXPMV: case FM_JOB_ZEXPMV: kind = JOB_EXPMV; break;
     case FM_JOB_PHI1MV: kind = JOB_PHI1MV; break;
     case FM_JOB_EXPMV_ADJ: kind = JOB_ADJ; nmax = o.nsteps > 0 ? o.nsteps : 1; o.precision = FM_FP64; break;
+    case FM_JOB_COSSIN: kind = JOB_TRIG; break;
+    case FM_JOB_RFUN: kind = JOB_EXPM; break;
     default: return 0;
   }
   if (batch < 1 || dmax < 1 || k < 1 || k > FM_MAX_TERMS) return 0;
-  if (batch == 1 && kind != JOB_ADJ &&
-      (o.path == FM_PATH_GRID || (o.path == FM_PATH_AUTO && dmax > fm_max_dim())))
-    return grid_ws_bytes(kind, cplx, o.precision, dmax, m);
-  const bool bg_kind = kind == JOB_EXPM || kind == JOB_PHI1 || kind == JOB_PHI1MV;
-  if (batch > 1 && (o.path == FM_PATH_GRID ||
-                    (o.path == FM_PATH_AUTO && bg_kind && o.precision != FM_FP64 && dmax >= 64))) {
-    if (!bg_kind || dmax > fm_max_dim()) return 0;
+  if (o.precision < FM_FP64 || o.precision > FM_MIXED) return 0;
+  // batch == 1 sizes the single-matrix calls; batch > 1 the batched ones
+  const char* why = "";
+  const Route r = route(kind, batch == 1 && kind != JOB_ADJ, dmax, o.precision, o.path, &why);
+  const int prec = o.precision == FM_FP64 ? 0 : 1;
+  if (r == R_BAD) return 0;
+  if (r == R_GRID) return grid_ws_bytes(kind, cplx, prec, dmax, m);
+  if (r == R_BGRID) {
+    if (dmax > fm_max_dim()) return 0;
     std::vector<int> d(batch, dmax);
     return bgrid_ws_bytes(kind, cplx, batch, d.data());
   }
   if (dmax > fm_max_dim()) return 0;
-  return make_plan(kind, cplx, o.precision, batch, dmax, m, k, nmax).total;
+  return make_plan(kind, cplx, prec, batch, dmax, m, k, nmax).total;
 }
 
 fm_status fm_expm(const fm_coeffs* cs, int d, const double* A, int lda, double t, double* F,
@@ -685,6 +794,72 @@ fm_status fm_phi1mv_batched(const fm_coeffs* ce, const fm_coeffs* cphi, int batc
                  V, nullptr, nullptr, W, info_dev, s_dev, opts, stream);
 }
 
+fm_status fm_cossin(const fm_coeffs* cc, const fm_coeffs* cs, int d, const double* A, int lda,
+                    double t, double* C, int ldc, double* S, int lds, const fm_opts* opts,
+                    void* stream, int* info_host, int* s_host) {
+  if (!cs) return fail(FM_EINVAL, "fm_cossin needs both coefficient sets");
+  Call c = {};
+  c.kind = JOB_TRIG;
+  c.ce = cc;
+  c.cp = cs;
+  c.batch = 1;
+  c.dmax = d;
+  c.d1 = d;
+  c.lda = lda;
+  c.ldf = ldc;
+  c.lde = lds;
+  c.t1 = t;
+  c.A = A;
+  c.F = C;
+  c.E = S;
+  c.info_host = info_host;
+  c.s_host = s_host;
+  return run(c, opts, (cudaStream_t)stream);
+}
+
+fm_status fm_cossin_batched(const fm_coeffs* cc, const fm_coeffs* cs, int batch, int dmax,
+                            const int* d_dev, const int64_t* off_dev, const double* A,
+                            const double* t_dev, double* C, double* S, int* info_dev, int* s_dev,
+                            const fm_opts* opts, void* stream) {
+  if (!cs) return fail(FM_EINVAL, "fm_cossin_batched needs both coefficient sets");
+  return batched(JOB_TRIG, false, cc, cs, batch, dmax, d_dev, off_dev, A, t_dev, 0, nullptr,
+                 nullptr, C, S, nullptr, info_dev, s_dev, opts, stream);
+}
+
+// r(tA) with no range reduction: the exp job with s forced to 0 and the
+// theta check of kSRfun
+static fm_opts rfun_opts(const fm_opts* opts) {
+  fm_opts o = resolve_opts(opts);
+  o.s_fixed = kSRfun;
+  return o;
+}
+
+fm_status fm_rfun(const fm_coeffs* cs, int d, const double* A, int lda, double t, double* F,
+                  int ldf, const fm_opts* opts, void* stream, int* info_host) {
+  fm_opts o = rfun_opts(opts);
+  Call c = {};
+  c.kind = JOB_EXPM;
+  c.ce = cs;
+  c.batch = 1;
+  c.dmax = d;
+  c.d1 = d;
+  c.lda = lda;
+  c.ldf = ldf;
+  c.t1 = t;
+  c.A = A;
+  c.F = F;
+  c.info_host = info_host;
+  return run(c, &o, (cudaStream_t)stream);
+}
+
+fm_status fm_rfun_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
+                          const int64_t* off_dev, const double* A, const double* t_dev, double* F,
+                          int* info_dev, const fm_opts* opts, void* stream) {
+  fm_opts o = rfun_opts(opts);
+  return batched(JOB_EXPM, false, cs, nullptr, batch, dmax, d_dev, off_dev, A, t_dev, 0, nullptr,
+                 nullptr, F, nullptr, nullptr, info_dev, nullptr, &o, stream);
+}
+
 fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, const int* d_dev,
                                    const int64_t* off_dev, const double* A, const double* t_dev,
                                    const long* nsteps_dev, const int64_t* voff_dev,
@@ -695,6 +870,7 @@ fm_status fm_expmv_adjoint_batched(const fm_coeffs* cs, int batch, int dmax, con
     return fail(FM_EINVAL, "adjoint: NULL argument");
   fm_opts o = resolve_opts(opts);
   if (o.nsteps <= 0) return fail(FM_EINVAL, "adjoint: opts.nsteps must bound every nsteps_dev[b]");
+  if (cs && cs->conj_pair) return fail(FM_EINVAL, "adjoint: the set must have real nodes (conj_pair = 0)");
   Call c = {};
   c.kind = JOB_ADJ;
   c.ce = cs;
@@ -734,13 +910,17 @@ fm_status fm_trid_expmv_batched(const fm_coeffs* cs, int batch, int d, const dou
   FmCoef cf;
   s = pack(cs, nullptr, false, o.form, cf);
   if (s) return s;
+  if (cf.conj_pair)
+    return fail(FM_EINVAL, "fm_trid_expmv_batched: conjugate-pair sets are not taken (their real "
+                           "systems I - 2 Re(c) B + |c|^2 B^2 are pentadiagonal)");
   int nonzero = 0;
   for (int i = 0; i < cf.k; ++i) nonzero += cf.c_re[i] != 0.0;
   if (!nonzero) return fail(FM_EINVAL, "fm_trid_expmv_batched: the set needs a nonzero node");
   const size_t need = trid_ws_bytes(batch, d, cf.k);
   void* ws = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
-  s = get_scratch(need, &o, &ws, st);
+  std::unique_lock<std::mutex> hold;  // the scratch stays ours until the work is queued
+  s = get_scratch(need, &o, &ws, st, &hold);
   if (s) return s;
   TridJob j;
   j.batch = batch;
@@ -767,6 +947,40 @@ fm_status fm_trid_expmv_batched(const fm_coeffs* cs, int batch, int d, const dou
   return FM_OK;
 }
 
+fm_status fm_select_batched(const fm_coeffs* cs, const fm_coeffs* cphi, int job, int batch,
+                            int dmax, const int* d_dev, const int64_t* off_dev, const double* A,
+                            const double* t_dev, long* out_dev, int* info_dev, const fm_opts* opts,
+                            void* stream) {
+  memset(&g_stats, 0, sizeof g_stats);
+  fm_opts o = resolve_opts(opts);
+  fm_status s = check_opts(o);
+  if (s) return s;
+  bool cplx = false;
+  int steps = 0;
+  switch (job) {
+    case FM_JOB_EXPM: case FM_JOB_PHI1: case FM_JOB_PHI1MV: break;
+    case FM_JOB_ZEXPM: cplx = true; break;
+    case FM_JOB_EXPMV: case FM_JOB_EXPMV_ADJ: steps = 1; break;
+    case FM_JOB_ZEXPMV: cplx = true; steps = 1; break;
+    default: return fail(FM_EINVAL, "fm_select_batched: unknown job");
+  }
+  const bool two = job == FM_JOB_PHI1 || job == FM_JOB_PHI1MV;
+  if (two && !cphi) return fail(FM_EINVAL, "fm_select_batched: phi_1 needs both coefficient sets");
+  if (batch < 1 || dmax < 1) return fail(FM_ESHAPE, "fm_select_batched: batch and dmax must be >= 1");
+  if (!d_dev || !off_dev || !A || !t_dev || !out_dev || !info_dev)
+    return fail(FM_EINVAL, "fm_select_batched: NULL pointer");
+  FmCoef cf;
+  s = pack(cs, two ? cphi : nullptr, cplx, o.form, cf);
+  if (s) return s;
+  const long long fixed = steps ? (long long)o.nsteps : (long long)o.s_fixed;
+  static_assert(sizeof(long) == sizeof(long long), "out_dev holds 64-bit values");
+  cudaError_t e = launch_select(cplx, d_dev, off_dev, A, t_dev, batch, dmax, o.anorm, cf.theta,
+                                steps, fixed, (long long*)out_dev, info_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fm_select_batched launch");
+  g_stats.launches = 1;
+  return FM_OK;
+}
+
 size_t fm_trid_workspace_size(int batch, int d, int k) {
   if (k < 1 || k > FM_MAX_TERMS) return 0;
   return trid_ws_bytes(batch, d, k);
@@ -786,22 +1000,29 @@ const char* fm_version(void) { return "fm 0.1 (sm_103a)"; }
 // fm_expm_noalloc: exp(tA) for one real matrix with no device allocation.
 //
 // Some callers cannot allocate device memory at all: code running where
-// cudaMalloc is forbidden or would deadlock (inside a custom allocator, a
-// memory-pool callback, or a host function enqueued on a stream), plugins
-// whose host application owns every device byte, and setups that must never
-// grow the device footprint after start-up.  For them this entry point uses a
-// fixed scratch array that lives in the library image itself (a file-scope
-// __device__ array below): it is reserved on every GPU where the library is
-// loaded, until the process exits, and it is the only scratch this call uses.
-// Inputs and outputs are still the caller's device buffers.
+// cudaMalloc is forbidden or could deadlock (inside a custom allocator or a
+// memory-pool hook), plugins whose host application owns every device byte,
+// and setups that must never grow the device footprint after start-up.  For
+// them this entry point uses a fixed scratch array that lives in the library
+// image itself (a file-scope __device__ array below), the only scratch this
+// call uses.  Inputs and outputs are still the caller's device buffers.
+//
+// The array belongs to the library's device code, which CUDA loads on a
+// device when it is first used there (lazy loading, the default): the first
+// call on each device loads it (committing the 2 MiB) and looks up its device
+// address (cudaGetSymbolAddress) with that device current.  That first call may
+// fail with FM_ECUDA if the device is out of memory; make it once per device as
+// a warm-up, before any stream capture and outside any code that must not
+// allocate.  Later calls allocate nothing.
 //
 // Limits: d <= FM_NOALLOC_MAX_DIM (128) and the scratch the call needs must fit
 // in FM_NOALLOC_SCRATCH_BYTES (2 MiB); larger problems are rejected with
 // FM_ESHAPE.  All calls share the one array: calls that overlap on the GPU (two
 // streams, or two host threads) race on it and give wrong results; serialize
-// them.  The first call on each device looks up the array's device address
-// (cudaGetSymbolAddress) with that device current; make that first call before
-// any stream capture.
+// them.  It runs the one-CTA kernel only: opts.path = FM_PATH_GRID and
+// opts.precision = FM_BF16_IR are rejected with FM_EINVAL.  It is not for host
+// functions enqueued on a stream (cudaLaunchHostFunc): CUDA forbids every CUDA
+// call there, and this entry point launches kernels.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -838,9 +1059,14 @@ extern "C" fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A
                                      double t, double* F, int ldf, const fm_opts* optsp,
                                      void* stream, int* info_host, int* s_host) {
   cudaStream_t st = (cudaStream_t)stream;
+  memset(&g_stats, 0, sizeof g_stats);
   fm_opts o = resolve_opts(optsp);
   fm_status s = check_opts(o);
   if (s) return s;
+  if (o.path == FM_PATH_GRID || o.precision == FM_BF16_IR)
+    return fail(FM_EINVAL, "fm_expm_noalloc runs on the one-CTA kernel: opts.path must be "
+                           "FM_PATH_AUTO or FM_PATH_CTA, opts.precision not FM_BF16_IR");
+  o.precision = o.precision == FM_FP64 ? 0 : 1;
   if (d < 1 || d > FM_NOALLOC_MAX_DIM)
     return fail(FM_ESHAPE, "fm_expm_noalloc: d must be in [1, FM_NOALLOC_MAX_DIM = 128]");
   if (!A || !F) return fail(FM_EINVAL, "A or F is NULL");

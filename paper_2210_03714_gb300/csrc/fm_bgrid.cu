@@ -276,6 +276,8 @@ int BRunner<T>::run() {
   st_ = j.st;
   const int batch = j.batch;
   const bool phi = j.kind == JOB_PHI1 || j.kind == JOB_PHI1MV;
+  const bool trig = j.kind == JOB_TRIG;  // cos in F, sin in F1
+  const bool two = phi || trig;
   g_ = geometry(j.cplx, batch, j.d_host, j.off_host, j.voff_host);
   {
     int dev = 0;
@@ -283,7 +285,7 @@ int BRunner<T>::run() {
     cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev);
     if (sms_ < 1) sms_ = 1;
   }
-  L_ = carve(g_, j.cplx, batch, phi);
+  L_ = carve(g_, j.cplx, batch, two);
   if (j.ws_bytes < L_.total) {
     snprintf(msg_, len_, "batched grid path: workspace too small");
     return FM_ENOMEM;
@@ -305,7 +307,7 @@ int BRunner<T>::run() {
   Y_ = (T*)(base_ + L_.Y);
   E_ = (T*)(base_ + L_.E);
   F_ = (T*)(base_ + L_.F);
-  F1_ = phi ? (T*)(base_ + L_.F1) : nullptr;
+  F1_ = two ? (T*)(base_ + L_.F1) : nullptr;
   G_ = (T*)(base_ + L_.G);
   pxC_ = (unsigned char*)(base_ + L_.pxC);
   pxG_ = (unsigned char*)(base_ + L_.pxG);
@@ -356,34 +358,26 @@ int BRunner<T>::run() {
   int s_max = 0;
   for (int v : s_host) s_max = v > s_max ? v : s_max;
 
+  // a3-a6 plan: one system per nonzero node; a pair of nodes +c, -c of the
+  // roundoff form shares one system I - c^2 B^2, a term of a conjugate-pair set
+  // is one real system I - 2 Re(c) B + |c|^2 B^2 (Sec. 1: one product, x^2, and
+  // one inverse per pair of roots)
+  const int nf = two ? 2 : 1;
+  Sys sys[kMaxTerms];
+  double base[2];
+  const int nsys = plan_systems(cf, j.form, true, sys, base);
+  bool any_quad = false;
+  for (int q = 0; q < nsys; ++q) {
+    any_quad |= sys[q].quad != 0;
+    if (sys[q].quad)  // a quadratic system's g I (plain form) joins the multiple of I
+      for (int f = 0; f < nf; ++f) base[f] += sys[q].gr[f];
+  }
   // a6 (first part): F_f = base_f I + d1 B + d2 B^2 for each function
-  const int nf = phi ? 2 : 1;
   for (int f = 0; f < nf; ++f) {
-    double base = cf.a0[f];
-    if (j.form == 1)
-      for (int i = 0; i < cf.k; ++i)
-        if (!(cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) base -= cf.b_re[f][i];
-    grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base, f ? F1_ : F_);
+    grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base[f], f ? F1_ : F_);
     check("initial combination");
   }
-  // pairs (+c, -c) of the roundoff form share one system, as Sec. 1 pairs
-  // complex-conjugate roots (one product, x^2, and one inverse per pair):
-  //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
-  //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
-  std::vector<int> partner(cf.k, -1);
-  bool any_pair = false;
-  if (j.form == 0)
-    for (int i = 0; i < cf.k; ++i) {
-      if (partner[i] >= 0 || (cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) continue;
-      for (int q = i + 1; q < cf.k; ++q)
-        if (partner[q] < 0 && cf.c_re[q] == -cf.c_re[i] && cf.c_im[q] == -cf.c_im[i]) {
-          partner[i] = q;
-          partner[q] = i;
-          any_pair = true;
-          break;
-        }
-    }
-  const bool need_b2 = cf.d2[0] != 0 || (phi && cf.d2[1] != 0) || any_pair;
+  const bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0) || any_quad;
   if (need_b2) {
     grid::Epi e;
     prod(B_, pxG_, exG_, true, B_, e, B2_, alive_, nullptr);
@@ -395,46 +389,36 @@ int BRunner<T>::run() {
       check("hybrid terms");
     }
 
-  // a3-a6: the shifted systems (and fused pairs), ascending first index
+  // a3-a6: the shifted systems, ascending first term
   bool pair_seen = false;
   double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
-  for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
-    const double cr = cf.c_re[i], ci = cf.c_im[i];
-    if (cr == 0.0 && ci == 0.0) continue;
-    if (partner[i] >= 0 && partner[i] < i) continue;  // done with its partner
-    const int q = partner[i];
-    if (q > i) {
-      // C = c^2 B^2
-      grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B2_, cr * cr - ci * ci,
-                                                  2.0 * cr * ci, C_, Y_);
-    } else {
-      grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, cr, ci, C_, Y_);
-    }
+  for (int qs = 0; qs < nsys && err_ == cudaSuccess; ++qs) {
+    const Sys& S = sys[qs];
+    if (S.quad)  // C = u1 B + u2 B^2
+      grid::b_build_shift2<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.u1r, S.u1i, B2_, S.u2r,
+                                                   S.u2i, C_, Y_);
+    else
+      grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.cr, S.ci, C_, Y_);
     check("shift");
     correct(dmax, nb);  // Y = (I - C)^-1 C
     if (err_ != cudaSuccess) break;
     for (int f = 0; f < nf; ++f) {
       T* Ff = f ? F1_ : F_;
-      if (q > i) {
-        // (I + Y)((b+ - b-) c B + (b+ + b-) c^2 B^2) = a B + a Y B + (b+ + b-) Y
-        // with Y = (I - c^2 B^2)^-1 - I, a = (b+ - b-) c: F += (b+ + b-) Y now,
-        // G += a Y, and a B + G B after the last pair
-        const double pr = cf.b_re[f][i], pim = cf.b_im[f][i];
-        const double mr = cf.b_re[f][q], mim = cf.b_im[f][q];
-        const double dr = pr - mr, di = pim - mim;
-        const double ar = dr * cr - di * ci, ai = dr * ci + di * cr;
-        grid::b_pair_acc<T><<<gE_, NT, 0, st_>>>(mats_, alive_, pr + mr, pim + mim, ar, ai, Y_,
-                                                  !pair_seen, Ff, G_ + (size_t)f * g_.elems);
+      if (S.quad) {
+        // (I + Y)(g I + a B + b B^2) = g I + y Y + x (I + Y) B with Y = M^-1 - I:
+        // F += y Y now (g I is in base), G += x Y, and x B + G B after the last one
+        grid::b_pair_acc<T><<<gE_, NT, 0, st_>>>(mats_, alive_, S.yr[f], S.yi[f], S.xr[f], S.xi[f],
+                                                  Y_, !pair_seen, Ff, G_ + (size_t)f * g_.elems);
         check("pair combination");
-        asum_r[f] += ar;
-        asum_i[f] += ai;
+        asum_r[f] += S.xr[f];
+        asum_i[f] += S.xi[f];
       } else {
-        grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cf.b_re[f][i], cf.b_im[f][i], Y_,
+        grid::b_accumulate<T><<<gE_, NT, 0, st_>>>(mats_, alive_, S.wr[f], S.wi[f], Y_,
                                                     j.form == 1, Ff);
         check("combination");
       }
     }
-    if (q > i) pair_seen = true;
+    if (S.quad) pair_seen = true;
   }
   // the pairs' a B + G B: one product per function, F = G B + F + (sum a) B
   for (int f = 0; f < nf && pair_seen && err_ == cudaSuccess; ++f) {
@@ -449,7 +433,8 @@ int BRunner<T>::run() {
   }
   if (err_ != cudaSuccess) return FM_ECUDA;
 
-  // a7 in the deviation from the identity: E = F - I (and Psi = F1 - I)
+  // a7 in the deviation from the identity: E = F - I (and Psi = F1 - I; for
+  // cos and sin, X = C - I and S itself)
   grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F_, -1.0, E_, 0);
   check("deviation");
   if (phi) {
@@ -459,6 +444,20 @@ int BRunner<T>::run() {
   for (int q = 0; q < s_max; ++q) {
     grid::b_square_mask<<<nb, 256, 0, st_>>>(batch, alive_, s_, q, mask_s_);
     check("squaring mask");
+    if (trig) {
+      // double angle (Sec. 1): S <- 2 S C = 2S + 2 X S, X <- 2 C^2 - I - I = 4X + 2 X X
+      grid::Epi e1;
+      e1.ar = 2.0;
+      e1.Z1 = F1_;
+      e1.b1r = 2.0;
+      prod(E_, pxG_, exG_, true, F1_, e1, F1_, mask_s_, nullptr);
+      grid::Epi e;
+      e.ar = 2.0;
+      e.Z1 = E_;
+      e.b1r = 4.0;
+      prod(E_, pxG_, exG_, false, E_, e, E_, mask_s_, nullptr);
+      continue;
+    }
     if (phi) {
       // (Phi, E) <- ((E + I) Phi / 2, E^2):  Psi <- Psi + E/2 + E Psi / 2
       grid::Epi e1;
@@ -478,6 +477,13 @@ int BRunner<T>::run() {
   if (j.kind == JOB_EXPM) {
     grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.F, 1);
     check("output");
+  } else if (trig) {
+    grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.F, 1);
+    check("output");
+    if (j.E) {
+      grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F1_, 0.0, (T*)j.E, 1);
+      check("output");
+    }
   } else {
     if (j.kind == JOB_PHI1) {
       grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F1_, 1.0, (T*)j.F, 1);
@@ -515,7 +521,7 @@ int BRunner<T>::run() {
 
 size_t bgrid_ws_bytes(int kind, bool cplx, int batch, const int* d_host) {
   Geo g = geometry(cplx, batch, d_host, nullptr, nullptr);
-  return carve(g, cplx, batch, kind == JOB_PHI1 || kind == JOB_PHI1MV).total;
+  return carve(g, cplx, batch, kind == JOB_PHI1 || kind == JOB_PHI1MV || kind == JOB_TRIG).total;
 }
 
 int bgrid_run(const BGridJob& j, char* msg, size_t len) {

@@ -170,6 +170,43 @@ void set_real(Builtin& B, int k, const char* const* c, const char* const* b, con
   B.func = func;
 }
 
+// exact Taylor coefficient a_k of function func (FM_FUNC_*)
+Q taylor_q(int func, int k) {
+  switch (func) {
+    case FM_FUNC_PHI1: return factorial_inv(k + 1);
+    case FM_FUNC_PHI2: return factorial_inv(k + 2);
+    case FM_FUNC_COS: return k % 2 ? qmk(0, 1) : (((k / 2) % 2) ? qneg(factorial_inv(k)) : factorial_inv(k));
+    case FM_FUNC_SIN: return k % 2 ? ((((k - 1) / 2) % 2) ? qneg(factorial_inv(k)) : factorial_inv(k)) : qmk(0, 1);
+    case FM_FUNC_LOG1M: return k == 0 ? qmk(0, 1) : qmk(-1, k);
+    default: return factorial_inv(k);
+  }
+}
+
+// weights of function func on the given nodes: Eq. (LinearEqsbi) solved
+// exactly (Lagrange interpolation in 128-bit rationals)
+void set_derived(Builtin& B, int k, const char* const* c, int order, int func) {
+  Q cq[FM_MAX_TERMS], aq[FM_MAX_TERMS], bq[FM_MAX_TERMS];
+  for (int i = 0; i < k; ++i) {
+    cq[i] = parse_q(c[i]);
+    aq[i] = taylor_q(func, i);
+  }
+  lagrange_b(k, cq, aq, bq);
+  Q a0 = qmk(0, 1);
+  B.k = k;
+  for (int i = 0; i < k; ++i) {
+    B.c_re[i] = qdouble(cq[i]);
+    B.c_im[i] = 0.0;
+    B.b_re[i] = qdouble(bq[i]);
+    B.b_im[i] = 0.0;
+    a0 = qadd(a0, bq[i]);
+  }
+  B.conj_pair = 0;
+  B.a0 = qdouble(a0);
+  B.d1 = B.d2 = 0.0;
+  B.order = order;
+  B.func = func;
+}
+
 void set_derived_phi1(Builtin& B, int k, const char* const* c, int order) {
   Q cq[FM_MAX_TERMS], aq[FM_MAX_TERMS], bq[FM_MAX_TERMS];
   for (int i = 0; i < k; ++i) {
@@ -193,12 +230,17 @@ void set_derived_phi1(Builtin& B, int k, const char* const* c, int order) {
   B.func = 1;
 }
 
-// Taylor coefficient a_k of the target function
+// Taylor coefficient a_k of the target function (FM_FUNC_*)
 long double taylor_a(int func, int k) {
+  if (func == FM_FUNC_LOG1M) return k == 0 ? 0.0L : -1.0L / (long double)k;
+  if ((func == FM_FUNC_COS && k % 2) || (func == FM_FUNC_SIN && k % 2 == 0)) return 0.0L;
   long double f = 1.0L;
-  int top = func == 1 ? k + 1 : k;
+  int top = func == FM_FUNC_PHI1 ? k + 1 : (func == FM_FUNC_PHI2 ? k + 2 : k);
   for (int i = 2; i <= top; ++i) f *= (long double)i;
-  return 1.0L / f;
+  long double v = 1.0L / f;
+  if (func == FM_FUNC_COS && (k / 2) % 2) v = -v;
+  if (func == FM_FUNC_SIN && ((k - 1) / 2) % 2) v = -v;
+  return v;
 }
 
 void init_sets() {
@@ -220,6 +262,18 @@ void init_sets() {
                               "-3892615/11907",   "353067578125/195084288", "71873828125/195084288"};
   set_real(g_sets[FM_R8], 9, r8c, r8b, nullptr, 8, 0);
   set_derived_phi1(g_sets[FM_R8_PHI1], 9, r8c, 8);
+  // Sec. 1: cos, sin (double-angle formulae) and phi_2 on the R8 nodes
+  set_derived(g_sets[FM_R8_COS], 9, r8c, 8, FM_FUNC_COS);
+  set_derived(g_sets[FM_R8_SIN], 9, r8c, 8, FM_FUNC_SIN);
+  set_derived(g_sets[FM_R8_PHI2], 9, r8c, 8, FM_FUNC_PHI2);
+  // Sec. 2, Eq. (Frac4bi0) and the two sets printed after it: c_i = 1/(i+1)
+  static const char* f4c[] = {"1/2", "1/3", "1/4", "1/5", "1/6"};
+  static const char* f4e[] = {"1/3", "-18", "128", "-625/3", "99"};
+  static const char* f4p[] = {"7/18", "-9", "128/3", "-500/9", "45/2"};
+  static const char* f4l[] = {"-35/3", "153/2", "-160", "625/6", "-9"};
+  set_real(g_sets[FM_FRAC4_EXP], 5, f4c, f4e, nullptr, 4, FM_FUNC_EXP);
+  set_real(g_sets[FM_FRAC4_PHI1], 5, f4c, f4p, nullptr, 4, FM_FUNC_PHI1);
+  set_real(g_sets[FM_FRAC4_LOG1M], 5, f4c, f4l, nullptr, 4, FM_FUNC_LOG1M);
   // Sec. 5.1, Eq. (Frac5bi0)
   static const char* r5c[] = {"0", "1/3", "1/4", "1/5", "1/6", "1/7"};
   static const char* r5b[] = {"-43/12", "81/32", "-704/9", "23125/48", "-810", "117649/288"};
@@ -306,7 +360,8 @@ void init_sets() {
 }  // namespace
 
 extern "C" fm_status fm_theta(const fm_coeffs* cs, int func, double tol, double* theta_out) {
-  if (!cs || !theta_out || cs->k < 1 || cs->k > FM_MAX_TERMS || !(tol > 0) || func < 0 || func > 1)
+  if (!cs || !theta_out || cs->k < 1 || cs->k > FM_MAX_TERMS || !(tol > 0) || func < 0 ||
+      func > FM_FUNC_LOG1M)
     return FM_EINVAL;
   // alpha_k = sum_i b_i c_i^k (+ d_k for k <= 2, d0 = a0 - sum b_i), Sec. 3
   const int K = 200;

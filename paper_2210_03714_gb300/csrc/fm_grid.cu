@@ -55,9 +55,10 @@ Layout layout(int kind, bool cplx, int precision, int d, int m) {
   L.Y = take(nn);
   L.E = take(nn);
   L.F0 = take(nn);
-  L.F1 = take(kind == JOB_PHI1 || kind == JOB_PHI1MV ? nn : 0);
+  const bool two = kind == JOB_PHI1 || kind == JOB_PHI1MV || kind == JOB_TRIG;
+  L.F1 = take(two ? nn : 0);
   L.B2 = take(nn);
-  L.G = take((kind == JOB_PHI1 || kind == JOB_PHI1MV ? 2 : 1) * nn);
+  L.G = take((two ? 2 : 1) * nn);
   L.Tm = take(precision == 0 ? (size_t)d * w * elt : 0);
   L.colsum = take((size_t)d * 8);
   L.misc = take(256);
@@ -282,6 +283,8 @@ int Runner<T>::run() {
   const int n = n_;
   const bool act = g.kind == JOB_EXPMV || g.kind == JOB_PHI1MV;
   const bool phi = g.kind == JOB_PHI1 || g.kind == JOB_PHI1MV;
+  const bool trig = g.kind == JOB_TRIG;  // cos in F0, sin in F1
+  const bool two = phi || trig;
   L_ = layout(g.kind, g.cplx, g.precision, n, g.m);
   if (g.ws_bytes < L_.total) {
     snprintf(msg_, len_, "grid path: workspace too small");
@@ -293,7 +296,7 @@ int Runner<T>::run() {
   Y_ = (T*)(base_ + L_.Y);
   E_ = (T*)(base_ + L_.E);
   F0_ = (T*)(base_ + L_.F0);
-  F1_ = phi ? (T*)(base_ + L_.F1) : nullptr;
+  F1_ = two ? (T*)(base_ + L_.F1) : nullptr;
   B2_ = (T*)(base_ + L_.B2);
   G_ = (T*)(base_ + L_.G);
   Tm_ = tcp_ ? nullptr : (T*)(base_ + L_.Tm);
@@ -350,6 +353,9 @@ int Runner<T>::run() {
   } else {
     if (g.s_fixed >= 0) {
       s = g.s_fixed;
+    } else if (g.s_fixed == kSRfun) {
+      s = 0;  // r(tA) as it is: no range reduction
+      if (info == 0 && !(eta <= cf.theta)) info = -5;
     } else {
       while (eta > ldexp(cf.theta, s) && s < 1023) ++s;
     }
@@ -377,33 +383,23 @@ int Runner<T>::run() {
     check("scaling");
   }
 
+  // a3-a6 plan: one system per nonzero node; a pair of nodes +c, -c of the
+  // roundoff form shares one system I - c^2 B^2, a term of a conjugate-pair set
+  // is one real system I - 2 Re(c) B + |c|^2 B^2 (Sec. 1: one product, x^2, and
+  // one inverse per pair of roots)
+  const int nf = two ? 2 : 1;
+  Sys sys[kMaxTerms];
+  double base[2];
+  const int nsys = plan_systems(cf, g.form, true, sys, base);
+  bool any_quad = false;
+  for (int q = 0; q < nsys; ++q) {
+    any_quad |= sys[q].quad != 0;
+    // a quadratic system's g I (plain form) joins the starting multiple of I
+    if (sys[q].quad)
+      for (int f = 0; f < nf; ++f) base[f] += sys[q].gr[f];
+  }
   // a6 (first part): F_f = base_f I + d1 B + d2 B^2
-  const int nf = phi ? 2 : 1;
-  double base[2] = {cf.a0[0], cf.a0[1]};
-  if (g.form == 1)
-    for (int f = 0; f < nf; ++f)
-      for (int i = 0; i < cf.k; ++i)
-        if (!(cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) base[f] -= cf.b_re[f][i];
-  // (plain form: a zero node's term b_i/(1 - 0) = b_i stays in base)
-  // pairs (+c, -c) of the roundoff form share one system, as Sec. 1 pairs
-  // complex-conjugate roots (one product, x^2, and one inverse per pair):
-  //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
-  //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
-  int partner[kMaxTerms];
-  bool any_pair = false;
-  for (int i = 0; i < cf.k; ++i) partner[i] = -1;
-  if (g.form == 0)
-    for (int i = 0; i < cf.k; ++i) {
-      if (partner[i] >= 0 || (cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) continue;
-      for (int q = i + 1; q < cf.k; ++q)
-        if (partner[q] < 0 && cf.c_re[q] == -cf.c_re[i] && cf.c_im[q] == -cf.c_im[i]) {
-          partner[i] = q;
-          partner[q] = i;
-          any_pair = true;
-          break;
-        }
-    }
-  const bool need_b2 = cf.d2[0] != 0 || (phi && cf.d2[1] != 0) || any_pair;
+  const bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0) || any_quad;
   if (need_b2) {
     grid::Epi e;
     prod(n, n, n, B_, n, true, B_, n, e, B2_, n);
@@ -414,21 +410,17 @@ int Runner<T>::run() {
     check("initial combination");
   }
 
-  // a3-a5: every shifted system (or fused pair), ascending first index;
-  // a6: F_f += b_i Y_i
+  // a3-a5: every shifted system, ascending first term; a6: F_f += b_i Y_i
   const double stop = ldexp(1.0, -30) / (double)n;
   bool pair_seen = false;
   double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
-  for (int i = 0; i < cf.k && err_ == cudaSuccess; ++i) {
-    const double cr = cf.c_re[i], ci = cf.c_im[i];
-    if (cr == 0.0 && ci == 0.0) continue;
-    const int pq = partner[i];
-    if (pq >= 0 && pq < i) continue;  // done with its partner
-    const double c2r = cr * cr - ci * ci, c2i = 2.0 * cr * ci;
-    if (pq > i)  // C = c^2 B^2
-      grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B2_, c2r, c2i, C_, Y_);
+  for (int qs = 0; qs < nsys && err_ == cudaSuccess; ++qs) {
+    const Sys& S = sys[qs];
+    if (S.quad)  // C = u1 B + u2 B^2
+      grid::build_shift2<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, S.u1r, S.u1i, B2_, S.u2r,
+                                                              S.u2i, C_, Y_);
     else
-      grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, cr, ci, C_, Y_);
+      grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, S.cr, S.ci, C_, Y_);
     check("shift");
     double prev = INFINITY;
     for (int it = 0;; ++it) {
@@ -474,25 +466,21 @@ int Runner<T>::run() {
     }
     for (int f = 0; f < nf && err_ == cudaSuccess; ++f) {
       T* Ff = f ? F1_ : F0_;
-      if (pq > i) {
-        // (I + Y)((b+ - b-) c B + (b+ + b-) c^2 B^2) = a B + a Y B + (b+ + b-) Y
-        // with Y = (I - c^2 B^2)^-1 - I, a = (b+ - b-) c: F += (b+ + b-) Y now,
-        // G += a Y, and a B + G B after the last pair
-        const double dr = cf.b_re[f][i] - cf.b_re[f][pq], di = cf.b_im[f][i] - cf.b_im[f][pq];
-        const double ar = dr * cr - di * ci, ai = dr * ci + di * cr;
-        grid::pair_acc<T><<<blocks(nn), kThreads, 0, st_>>>(
-            nn, cf.b_re[f][i] + cf.b_re[f][pq], cf.b_im[f][i] + cf.b_im[f][pq], ar, ai, Y_,
-            !pair_seen, Ff, G_ + (size_t)f * nn);
+      if (S.quad) {
+        // (I + Y)(g I + a B + b B^2) = g I + y Y + x (I + Y) B with Y = M^-1 - I:
+        // F += y Y now (g I is in base), G += x Y, and x B + G B after the last one
+        grid::pair_acc<T><<<blocks(nn), kThreads, 0, st_>>>(nn, S.yr[f], S.yi[f], S.xr[f], S.xi[f],
+                                                           Y_, !pair_seen, Ff, G_ + (size_t)f * nn);
         check("pair combination");
-        asum_r[f] += ar;
-        asum_i[f] += ai;
+        asum_r[f] += S.xr[f];
+        asum_i[f] += S.xi[f];
       } else {
-        grid::accumulate<T><<<blocks(nn), kThreads, 0, st_>>>(n, cf.b_re[f][i], cf.b_im[f][i], Y_,
-                                                             g.form == 1, Ff);
+        grid::accumulate<T><<<blocks(nn), kThreads, 0, st_>>>(n, S.wr[f], S.wi[f], Y_, g.form == 1,
+                                                             Ff);
         check("combination");
       }
     }
-    if (pq > i) pair_seen = true;
+    if (S.quad) pair_seen = true;
   }
   // the pairs' a B + G B: one product per function, F = G B + F + (sum a) B
   for (int f = 0; f < nf && pair_seen && err_ == cudaSuccess; ++f) {
@@ -520,6 +508,30 @@ int Runner<T>::run() {
     for (int q = 0; q < s; ++q) square(E_);
     grid::add_identity<T><<<blocks(nn), kThreads, 0, st_>>>(n, n, E_, n, 1.0, (T*)g.F, g.ldf);
     check("output");
+  } else if (trig) {
+    // double angle (Sec. 1) with C = I + X: S <- 2 S C = 2S + 2 X S,
+    // X <- 2 C^2 - 2I = 4X + 2 X X
+    T* S = F1_;
+    for (int q = 0; q < s; ++q) {
+      grid::Epi e1;
+      e1.ar = 2.0;
+      e1.Z1 = S;
+      e1.ld1 = n;
+      e1.b1r = 2.0;
+      prod(n, n, n, E_, n, true, S, n, e1, S, n);
+      grid::Epi e2;
+      e2.ar = 2.0;
+      e2.Z1 = E_;
+      e2.ld1 = n;
+      e2.b1r = 4.0;
+      prod(n, n, n, E_, n, false, E_, n, e2, E_, n);
+    }
+    grid::add_identity<T><<<blocks(nn), kThreads, 0, st_>>>(n, n, E_, n, 1.0, (T*)g.F, g.ldf);
+    check("output");
+    if (g.E) {
+      grid::add_identity<T><<<blocks(nn), kThreads, 0, st_>>>(n, n, S, n, 0.0, (T*)g.E, g.lde);
+      check("output");
+    }
   } else if (phi) {
     // (Phi, E) <- ((E + I) Phi / 2, E^2):  Psi <- Psi + E/2 + E Psi / 2,  E <- 2E + E E
     T* Psi = F1_;

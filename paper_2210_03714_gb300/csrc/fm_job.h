@@ -18,7 +18,8 @@ constexpr int kMaxTerms = 16;
 struct FmCoef {
   int k;          // number of terms
   int nfun;       // 1 (exp) or 2 (exp, phi_1)
-  int conj_pair;  // unused by the kernels (rejected on the host for now)
+  int conj_pair;  // 1: term i stands for 2 Re(b_i c_i x / (1 - c_i x)) (real
+                  //    matrices; complex ones get the set expanded to c, conj(c))
   int pad;
   double c_re[kMaxTerms], c_im[kMaxTerms];
   double b_re[2][kMaxTerms], b_im[2][kMaxTerms];
@@ -26,7 +27,128 @@ struct FmCoef {
   double theta;   // min over the functions
 };
 
-enum { JOB_EXPM = 0, JOB_PHI1 = 1, JOB_EXPMV = 2, JOB_PHI1MV = 3, JOB_ADJ = 4 };
+// One shifted system of a call, in ascending order of its first term.
+//  single (quad == 0): M = I - c B; roundoff form Y = M^-1 (c B R), plain form
+//    Y = M^-1 R; F_f += w_f Y.
+//  quadratic (quad == 1): M = I - u1 B - u2 B^2 after one product B^2, and
+//    F_f += M^-1 (g_f I + a_f B + b_f B^2) R.  Two cases:
+//    a pair of nodes +c, -c of the roundoff form (u1 = 0, u2 = c^2):
+//      b+ cx/(1 - cx) + b- (-cx)/(1 + cx) = ((b+ - b-) c x + (b+ + b-) c^2 x^2)/(1 - c^2 x^2);
+//    a term of a conjugate-pair set (u1 = 2 Re c, u2 = -|c|^2, Sec. 1: "one
+//    product, x^2, and one inverse" per pair of complex-conjugate roots):
+//      2 Re(b cx/(1 - cx)) = (2 Re(bc) x - 2 Re(b) |c|^2 x^2) / (1 - 2 Re(c) x + |c|^2 x^2)
+//      2 Re(b/(1 - cx))    = (2 Re(b) - 2 Re(b conj(c)) x) / (same)        (plain form)
+struct Sys {
+  int node;    // first term index (reported in info for a zero pivot)
+  int quad;
+  double cr, ci;                    // single: the node
+  double u1r, u1i, u2r, u2i;        // quadratic: M = I - u1 B - u2 B^2
+  double wr[2], wi[2];              // single: weight per function
+  double gr[2], gi[2], ar[2], ai[2], br[2], bi[2];  // quadratic: right-hand side
+  // quadratic, the same term through Y = M^-1 - I (the grid paths): with
+  // (I + Y) M = I,  (I + Y)(g I + a B + b B^2) = g I + y Y + x (I + Y) B,
+  // y = g + b / u2, x = a - b u1 / u2
+  double yr[2], yi[2], xr[2], xi[2];
+};
+
+// The systems of a set.  fuse_pm: fuse +-c pairs (roundoff form only);
+// conjugate-pair terms are always quadratic (their systems stay real).
+// base[f]: the multiple of R the combination starts from (a0 in the roundoff
+// form; in the plain form a0 minus every weight a nonzero node carries, so the
+// singles' b_f M^-1 R and the quadratics' g_f terms add the rest).
+FM_HD int plan_systems(const FmCoef& cf, int form, bool fuse_pm, Sys* out, double* base) {
+  int ns = 0;
+  signed char partner[kMaxTerms];
+  for (int i = 0; i < cf.k; ++i) partner[i] = -1;
+  for (int f = 0; f < 2; ++f) base[f] = cf.a0[f];
+  if (fuse_pm && form == 0 && !cf.conj_pair)
+    for (int i = 0; i < cf.k; ++i) {
+      if (partner[i] >= 0 || (cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) continue;
+      for (int q = i + 1; q < cf.k; ++q)
+        if (partner[q] < 0 && cf.c_re[q] == -cf.c_re[i] && cf.c_im[q] == -cf.c_im[i]) {
+          partner[i] = (signed char)q;
+          partner[q] = (signed char)i;
+          break;
+        }
+    }
+  for (int i = 0; i < cf.k; ++i) {
+    const double cr = cf.c_re[i], ci = cf.c_im[i];
+    if (cr == 0.0 && ci == 0.0) continue;  // roundoff: no term; plain: b_i stays in base
+    if (partner[i] >= 0 && partner[i] < i) continue;
+    Sys& S = out[ns++];
+    S.node = i;
+    S.quad = 0;
+    S.cr = cr;
+    S.ci = ci;
+    S.u1r = S.u1i = S.u2r = S.u2i = 0.0;
+    for (int f = 0; f < 2; ++f) {
+      S.wr[f] = cf.b_re[f][i];
+      S.wi[f] = cf.b_im[f][i];
+      S.gr[f] = S.gi[f] = S.ar[f] = S.ai[f] = S.br[f] = S.bi[f] = 0.0;
+      S.yr[f] = S.yi[f] = S.xr[f] = S.xi[f] = 0.0;
+    }
+    if (cf.conj_pair) {
+      for (int f = 0; f < 2; ++f) {
+        if (form == 1) base[f] -= 2.0 * cf.b_re[f][i];
+      }
+      if (ci == 0.0) {  // a real node: 2 Re(b_i) / (1 - c x)
+        for (int f = 0; f < 2; ++f) {
+          S.wr[f] = 2.0 * cf.b_re[f][i];
+          S.wi[f] = 0.0;
+        }
+        continue;
+      }
+      S.quad = 1;
+      S.u1r = 2.0 * cr;
+      S.u2r = -(cr * cr + ci * ci);
+      for (int f = 0; f < 2; ++f) {
+        const double br = cf.b_re[f][i], bi = cf.b_im[f][i];
+        if (form == 0) {
+          S.ar[f] = 2.0 * (br * cr - bi * ci);   // 2 Re(b c)
+          S.br[f] = 2.0 * br * S.u2r;             // -2 Re(b) |c|^2
+        } else {
+          S.gr[f] = 2.0 * br;                     // 2 Re(b)
+          S.ar[f] = -2.0 * (br * cr + bi * ci);   // -2 Re(b conj(c))
+        }
+        S.yr[f] = 2.0 * br;                       // both forms
+        S.xr[f] = -2.0 * (br * cr + bi * ci);
+      }
+      continue;
+    }
+    if (form == 1)
+      for (int f = 0; f < 2; ++f) base[f] -= cf.b_re[f][i];
+    const int q = partner[i];
+    if (q < 0) continue;
+    // (b+ - b-) c and (b+ + b-) c^2, complex nodes and weights allowed
+    S.quad = 1;
+    S.u2r = cr * cr - ci * ci;
+    S.u2i = 2.0 * cr * ci;
+    for (int f = 0; f < 2; ++f) {
+      const double dr = cf.b_re[f][i] - cf.b_re[f][q], di = cf.b_im[f][i] - cf.b_im[f][q];
+      const double sr = cf.b_re[f][i] + cf.b_re[f][q], si = cf.b_im[f][i] + cf.b_im[f][q];
+      S.ar[f] = dr * cr - di * ci;
+      S.ai[f] = dr * ci + di * cr;
+      S.br[f] = sr * S.u2r - si * S.u2i;
+      S.bi[f] = sr * S.u2i + si * S.u2r;
+      S.yr[f] = sr;
+      S.yi[f] = si;
+      S.xr[f] = S.ar[f];
+      S.xi[f] = S.ai[f];
+    }
+  }
+  return ns;
+}
+
+enum { JOB_EXPM = 0, JOB_PHI1 = 1, JOB_EXPMV = 2, JOB_PHI1MV = 3, JOB_ADJ = 4, JOB_TRIG = 5 };
+
+// jobs with two functions from one set of resolvents share one scratch layout
+FM_HD int layout_kind(int kind) {
+  return (kind == JOB_PHI1MV || kind == JOB_TRIG) ? JOB_PHI1 : kind;
+}
+
+// opts.s_fixed value of fm_rfun: s = 0 (no range reduction), and info = -5
+// when ||tA||_1 exceeds theta (the result is still computed)
+constexpr int kSRfun = -2;
 
 struct FmJob {
   int kind, precision, form, max_ir;

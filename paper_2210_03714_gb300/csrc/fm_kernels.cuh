@@ -173,12 +173,31 @@ __device__ __forceinline__ void build_shift(int n, double cre, double cim, const
   __syncthreads();
 }
 
+// C = u1 B + u2 B2 (each product rounded once; C = u2 B2 when u1 = 0), M = I - C
+template <class T, class TL>
+__device__ __forceinline__ void build_shift2(int n, double u1r, double u1i, const T* B, double u2r,
+                                             double u2i, const T* B2, T* C, TL* LU, double* D,
+                                             bool mixed) {
+  const int tid = threadIdx.x;
+  const bool one = u1r == 0.0 && u1i == 0.0;
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e / n, c = e % n;
+    T cv = wmul<T>(u2r, u2i, B2[e]);
+    if (!one) cv = Tr<T>::add(wmul<T>(u1r, u1i, B[e]), cv);
+    C[e] = cv;
+    T mv = Tr<T>::sub(tdiag<T>(r, c), cv);
+    LU[e] = cvt<TL, T>(mv);
+    if (r == c) D[r] = mixed ? diag_err(cv) : 0.0;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // matrix functions: exp (JOB_EXPM), phi_1 with exp (JOB_PHI1, JOB_PHI1MV)
 // ---------------------------------------------------------------------------
 template <class T, class TL, int NB>
 __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem,
-                                        oz::Ctx* oc) {
+                                        oz::Ctx* oc, Sys* plan) {
   using TT = Tr<T>;
   using R = typename TT::R;
   const int tid = threadIdx.x;
@@ -189,8 +208,9 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   const double t = J.t ? J.t[b] : J.t1;
   const bool mixed = J.precision != 0;
   const bool two = (J.kind != JOB_EXPM);
-  const WsLayout L = ws_layout(J.kind == JOB_PHI1MV ? JOB_PHI1 : J.kind, n, J.m, cf.k, sizeof(T),
-                               sizeof(TL), 0, oc != nullptr);
+  const bool trig = J.kind == JOB_TRIG;  // cos (F) and sin (Ph)
+  const WsLayout L = ws_layout(layout_kind(J.kind), n, J.m, cf.k, sizeof(T), sizeof(TL), 0,
+                               oc != nullptr);
   oz_bind(oc, ws, L);
   int terr = 0;
   T* B = (T*)(ws + L.B);
@@ -227,38 +247,27 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   int info = 0;
   if (bad) info = -2;
   const double eta = J.anorm > 0 ? J.anorm * fabs(t) : (double)cmax;
-  const int s = J.s_fixed >= 0 ? J.s_fixed : select_s(eta, cf.theta);
+  const int s = J.s_fixed >= 0 ? J.s_fixed : (J.s_fixed == kSRfun ? 0 : select_s(eta, cf.theta));
   for (int e = tid; e < n * n; e += NT) B[e] = tscale(B[e], s);
-  // a6 (first part): F = base I (+ d1 B + d2 B^2) for each function
-  double base[2];
-  for (int f = 0; f < 2; ++f) {
-    base[f] = cf.a0[f];
-    if (J.form == 1)
-      for (int i = 0; i < cf.k; ++i) base[f] -= cf.b_re[f][i];
-  }
+  // a3-a6 plan: one system per nonzero node; in the roundoff form a pair of
+  // nodes +c, -c shares one system I - c^2 B^2, and a term of a conjugate-pair
+  // set is one real system I - 2 Re(c) B + |c|^2 B^2 (Sec. 1: one product, x^2,
+  // and one inverse per pair of roots)
+  // (the plan lives in shared memory, filled by one thread)
+  Sys* sys = plan;
+  double* pbase = (double*)(plan + kMaxTerms);
+  int* pn = (int*)(pbase + 2);
+  if (tid == 0) *pn = plan_systems(cf, J.form, true, sys, pbase);
   __syncthreads();
+  const int nsys = *pn;
+  const double base[2] = {pbase[0], pbase[1]};
+  bool any_quad = false;
+  for (int q = 0; q < nsys; ++q) any_quad |= sys[q].quad != 0;
   const bool hyb = cf.d1[0] != 0 || cf.d2[0] != 0 || (two && (cf.d1[1] != 0 || cf.d2[1] != 0));
-  // pairs (+c, -c) of the roundoff form share one system, as Sec. 1 pairs
-  // complex-conjugate roots (one product, x^2, and one inverse per pair):
-  //   b+ cB (I - cB)^-1 + b- (-cB)(I + cB)^-1
-  //     = (I - c^2 B^2)^-1 [(b+ - b-) cB + (b+ + b-) c^2 B^2]
-  signed char partner[kMaxTerms];
-  bool any_pair = false;
-  for (int i = 0; i < cf.k; ++i) partner[i] = -1;
-  if (J.form == 0)
-    for (int i = 0; i < cf.k; ++i) {
-      if (partner[i] >= 0 || (cf.c_re[i] == 0.0 && cf.c_im[i] == 0.0)) continue;
-      for (int q = i + 1; q < cf.k; ++q)
-        if (partner[q] < 0 && cf.c_re[q] == -cf.c_re[i] && cf.c_im[q] == -cf.c_im[i]) {
-          partner[i] = (signed char)q;
-          partner[q] = (signed char)i;
-          any_pair = true;
-          break;
-        }
-    }
   T* B2 = (T*)(ws + L.B2);
-  const bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0) || any_pair;
+  const bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0) || any_quad;
   if (need_b2) terr |= prod<T>(oc, n, n, n, B, n, B, n, B2, n, smem);
+  // a6 (first part): F = base I (+ d1 B + d2 B^2) for each function
   for (int e = tid; e < n * n; e += NT) {
     int r = e / n, c = e % n;
     for (int f = 0; f < (two ? 2 : 1); ++f) {
@@ -272,66 +281,50 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
   }
   __syncthreads();
   double qmax = -1.0;
-  bool any_shift = false;
-  // a3-a6: the shifted solves, ascending i
-  for (int i = 0; i < cf.k && info == 0; ++i) {
-    const double cre = cf.c_re[i], cim = cf.c_im[i];
-    if (cre == 0.0 && cim == 0.0) {
-      if (J.form == 1) {  // plain form: b_i I
+  const bool any_shift = nsys > 0;
+  // a3-a6: the shifted solves, ascending first term
+  for (int q = 0; q < nsys && info == 0; ++q) {
+    const Sys& S = sys[q];
+    if (S.quad) {
+      // one system M = I - u1 B - u2 B^2; per function the right-hand side
+      // X = g I + a B + b B^2, and F += M^-1 X
+      build_shift2<T, TL>(n, S.u1r, S.u1i, B, S.u2r, S.u2i, B2, C, LU, D, mixed);
+      int fi = cta_getrf<TL, NB>(n, LU, n, piv, (TL*)smem);
+      if (fi) { info = S.node * n + fi; break; }
+      for (int f = 0; f < (two ? 2 : 1); ++f) {
         for (int e = tid; e < n * n; e += NT) {
-          int r = e / n, c = e % n;
-          for (int f = 0; f < (two ? 2 : 1); ++f) {
-            T* Fx = f == 0 ? F : Ph;
-            Fx[e] = TT::add(Fx[e], wmul<T>(cf.b_re[f][i], cf.b_im[f][i], tdiag<T>(r, c)));
-          }
+          T v = wmul<T>(S.ar[f], S.ai[f], B[e]);
+          if (S.br[f] != 0.0 || S.bi[f] != 0.0) v = TT::add(v, wmul<T>(S.br[f], S.bi[f], B2[e]));
+          if (e / n == e % n && (S.gr[f] != 0.0 || S.gi[f] != 0.0))
+            v = TT::add(v, wmul<T>(S.gr[f], S.gi[f], TT::one()));
+          T1[e] = v;
         }
         __syncthreads();
-      }
-      continue;
-    }
-    const int pq = partner[i];
-    if (pq >= 0 && pq < i) continue;  // solved with its partner
-    any_shift = true;
-    if (pq > i) {
-      // one system I - C' with C' = c^2 B^2; per function the right-hand
-      // side X = (b+ - b-) c B + (b+ + b-) c^2 B^2, and F += (I - C')^-1 X
-      const double c2r = cre * cre - cim * cim, c2i = 2.0 * cre * cim;
-      build_shift<T, TL>(n, c2r, c2i, B2, C, LU, D, mixed);
-      int fi = cta_getrf<TL, NB>(n, LU, n, piv, (TL*)smem);
-      if (fi) { info = i * n + fi; break; }
-      for (int f = 0; f < (two ? 2 : 1); ++f) {
-        const double dr = cf.b_re[f][i] - cf.b_re[f][pq], di = cf.b_im[f][i] - cf.b_im[f][pq];
-        const double sr = cf.b_re[f][i] + cf.b_re[f][pq], si = cf.b_im[f][i] + cf.b_im[f][pq];
-        const double ar = dr * cre - di * cim, ai = dr * cim + di * cre;
-        const double br = sr * c2r - si * c2i, bi = sr * c2i + si * c2r;
-        for (int e = tid; e < n * n; e += NT)
-          T1[e] = TT::add(wmul<T>(ar, ai, B[e]), wmul<T>(br, bi, B2[e]));
-        __syncthreads();
-        double q = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL,
-                                            smem, oc, &terr);
-        qmax = fmax(qmax, q);
+        double qq = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL,
+                                             smem, oc, &terr);
+        qmax = fmax(qmax, qq);
         T* Fx = f == 0 ? F : Ph;
         for (int e = tid; e < n * n; e += NT) Fx[e] = TT::add(Fx[e], Y[e]);
         __syncthreads();
       }
       continue;
     }
-    build_shift<T, TL>(n, cre, cim, B, C, LU, D, mixed);
+    build_shift<T, TL>(n, S.cr, S.ci, B, C, LU, D, mixed);
     int fi = cta_getrf<TL, NB>(n, LU, n, piv, (TL*)smem);
-    if (fi) { info = i * n + fi; break; }
+    if (fi) { info = S.node * n + fi; break; }
     // right-hand side: C (roundoff form) or I (plain form), kept in T1
     for (int e = tid; e < n * n; e += NT) {
       int r = e / n, c = e % n;
       T1[e] = J.form == 1 ? tdiag<T>(r, c) : C[e];
     }
     __syncthreads();
-    double q = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL, smem,
-                                        oc, &terr);
-    qmax = fmax(qmax, q);
+    double qq = shifted_solve<T, TL, NB>(J, n, n, C, D, LU, piv, T1, Y, (T*)(ws + L.T2), RL, smem,
+                                         oc, &terr);
+    qmax = fmax(qmax, qq);
     for (int e = tid; e < n * n; e += NT)
       for (int f = 0; f < (two ? 2 : 1); ++f) {
         T* Fx = f == 0 ? F : Ph;
-        Fx[e] = TT::add(Fx[e], wmul<T>(cf.b_re[f][i], cf.b_im[f][i], Y[e]));
+        Fx[e] = TT::add(Fx[e], wmul<T>(S.wr[f], S.wi[f], Y[e]));
       }
     __syncthreads();
   }
@@ -343,9 +336,11 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
     // row and column, so square the deviation from the identity instead of
     // F itself: (I + E)^2 = I + (2E + E E); for phi_1 with Phi = I + Psi,
     // (E_F + I) Phi / 2 = I + (Psi + E/2 + E Psi / 2).  Same recurrence.
+    // cos and sin (double angle, Sec. 1) with C = I + X: 2 C^2 - I = I + (4X + 2 X X)
+    // and 2 S C = 2S + 2 X S (S and X commute: both are functions of B).
     for (int r = tid; r < n; r += NT) {
       F[r * n + r] = TT::sub(F[r * n + r], TT::one());
-      if (two) Ph[r * n + r] = TT::sub(Ph[r * n + r], TT::one());
+      if (two && !trig) Ph[r * n + r] = TT::sub(Ph[r * n + r], TT::one());
     }
     __syncthreads();
     for (int q = 0; q < s; ++q) {
@@ -353,6 +348,11 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
       terr |= prod<T>(oc, n, n, n, F, n, F, n, T2, n, smem);
       for (int e = tid; e < n * n; e += NT) {
         const T E = F[e];
+        if (trig) {
+          Ph[e] = TT::add(TT::rscale(Ph[e], 2.0), TT::rscale(T1[e], 2.0));
+          F[e] = TT::add(TT::rscale(E, 4.0), TT::rscale(T2[e], 2.0));
+          continue;
+        }
         if (two) Ph[e] = TT::add(TT::add(Ph[e], TT::rscale(E, 0.5)), TT::rscale(T1[e], 0.5));
         F[e] = TT::add(TT::rscale(E, 2.0), T2[e]);
       }
@@ -360,13 +360,22 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
     }
     for (int r = tid; r < n; r += NT) {
       F[r * n + r] = TT::add(F[r * n + r], TT::one());
-      if (two) Ph[r * n + r] = TT::add(Ph[r * n + r], TT::one());
+      if (two && !trig) Ph[r * n + r] = TT::add(Ph[r * n + r], TT::one());
     }
   } else if (info == 0 || info == -1) {
     for (int q = 0; q < s; ++q) {
       if (!two) {
         terr |= prod<T>(oc, n, n, n, F, n, F, n, T1, n, smem);
         T* tmp = F; F = T1; T1 = tmp;
+      } else if (trig) {
+        // (C, S) <- (2 C^2 - I, 2 S C)
+        terr |= prod<T>(oc, n, n, n, Ph, n, F, n, T1, n, smem);
+        terr |= prod<T>(oc, n, n, n, F, n, F, n, T2, n, smem);
+        for (int e = tid; e < n * n; e += NT) {
+          Ph[e] = TT::rscale(T1[e], 2.0);
+          F[e] = TT::sub(TT::rscale(T2[e], 2.0), tdiag<T>(e / n, e % n));
+        }
+        __syncthreads();
       } else {
         // Phi <- (E + I) Phi / 2, then E <- E E
         for (int r = tid; r < n; r += NT) F[r * n + r] = TT::add(F[r * n + r], TT::one());
@@ -381,8 +390,16 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
     }
   }
   __syncthreads();
+  if (J.s_fixed == kSRfun && info == 0 && !(eta <= cf.theta)) info = -5;
   // outputs
-  if (J.kind == JOB_EXPM) {
+  if (J.kind == JOB_TRIG) {
+    T* Co = (T*)J.F + off;
+    for (int e = tid; e < n * n; e += NT) Co[(size_t)(e / n) * ldf + e % n] = F[e];
+    if (J.E) {
+      T* So = (T*)J.E + off;
+      for (int e = tid; e < n * n; e += NT) So[(size_t)(e / n) * lde + e % n] = Ph[e];
+    }
+  } else if (J.kind == JOB_EXPM) {
     T* Fo = (T*)J.F + off;
     for (int e = tid; e < n * n; e += NT) Fo[(size_t)(e / n) * ldf + e % n] = F[e];
   } else if (J.kind == JOB_PHI1) {
@@ -411,7 +428,7 @@ __device__ __noinline__ void run_matfun(const FmJob& J, const FmCoef& cf, int b,
 // ---------------------------------------------------------------------------
 template <class T, class TL, int NB>
 __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b, char* ws, char* smem,
-                                        oz::Ctx* oc) {
+                                        oz::Ctx* oc, Sys* plan) {
   using TT = Tr<T>;
   using R = typename TT::R;
   const int tid = threadIdx.x;
@@ -477,27 +494,43 @@ __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b,
     B[e] = TT::rscale(A[(size_t)r * lda + c], h);
   }
   __syncthreads();
-  double base = cf.a0[0];
-  if (J.form == 1)
-    for (int i = 0; i < k; ++i) base -= cf.b_re[0][i];
-  // a3: factor every shifted matrix once
-  for (int i = 0; i < k && info == 0; ++i) {
-    const double cre = cf.c_re[i], cim = cf.c_im[i];
-    if (cre == 0.0 && cim == 0.0) continue;
+  // one system per nonzero node (the +-c pairs stay apart here: each step's
+  // solves already share the one product B W); a term of a conjugate-pair set
+  // is one real system I - 2 Re(c) B + |c|^2 B^2 (Sec. 1)
+  Sys* sys = plan;
+  double* pbase = (double*)(plan + kMaxTerms);
+  int* pn = (int*)(pbase + 2);
+  if (tid == 0) *pn = plan_systems(cf, J.form, false, sys, pbase);
+  __syncthreads();
+  const int nsys = *pn;
+  const double base = pbase[0];
+  bool any_quad = false, quad_b2 = false;
+  for (int q = 0; q < nsys; ++q) {
+    any_quad |= sys[q].quad != 0;
+    quad_b2 |= sys[q].quad != 0 && (sys[q].br[0] != 0.0 || sys[q].bi[0] != 0.0);
+  }
+  T* B2 = (T*)(ws + L.C);  // B^2 for the quadratic systems (C is unused here)
+  if (any_quad && info == 0) terr |= prod<T>(oc, n, n, n, B, n, B, n, B2, n, smem);
+  // a3: factor every shifted matrix once (slot = the system's first term)
+  for (int q = 0; q < nsys && info == 0; ++q) {
+    const Sys& S = sys[q];
+    const int i = S.node;
     T* Ci = (T*)(ws + L.Cs) + (size_t)i * n * n;
     TL* LUi = (TL*)(ws + L.LUs) + (size_t)i * n * n;
     int* pivi = (int*)(ws + L.pivs) + (size_t)i * n;
     double* Di = (double*)(ws + L.Ds) + (size_t)i * n;
-    build_shift<T, TL>(n, cre, cim, B, Ci, LUi, Di, mixed);
+    if (S.quad) build_shift2<T, TL>(n, S.u1r, S.u1i, B, S.u2r, S.u2i, B2, Ci, LUi, Di, mixed);
+    else build_shift<T, TL>(n, S.cr, S.ci, B, Ci, LUi, Di, mixed);
     int fi = cta_getrf<TL, NB>(n, LUi, n, pivi, (TL*)smem);
     if (fi) info = i * n + fi;
   }
   double qmax = -1.0;
-  bool any_shift = false;
+  const bool any_shift = nsys > 0;
+  const bool need_u2 = cf.d2[0] != 0 || quad_b2;
   // a4-a7: N steps W <- r(B) W
   for (long long q = 0; q < N && info == 0; ++q) {
     terr |= prod<T>(oc, n, m, n, B, n, Wc, m, U, m, smem);
-    if (cf.d2[0] != 0) terr |= prod<T>(oc, n, m, n, B, n, U, m, U2, m, smem);
+    if (need_u2) terr |= prod<T>(oc, n, m, n, B, n, U, m, U2, m, smem);
     for (size_t e = tid; e < nm; e += NT) {
       T v = TT::rscale(Wc[e], base);
       if (cf.d1[0] != 0) v = TT::add(v, TT::rscale(U[e], cf.d1[0]));
@@ -505,27 +538,32 @@ __device__ __noinline__ void run_action(const FmJob& J, const FmCoef& cf, int b,
       Wn[e] = v;
     }
     __syncthreads();
-    for (int i = 0; i < k; ++i) {
-      const double cre = cf.c_re[i], cim = cf.c_im[i];
-      const double br = cf.b_re[0][i], bi = cf.b_im[0][i];
-      if (cre == 0.0 && cim == 0.0) {
-        if (J.form == 1) {
-          for (size_t e = tid; e < nm; e += NT) Wn[e] = TT::add(Wn[e], wmul<T>(br, bi, Wc[e]));
-          __syncthreads();
-        }
-        continue;
-      }
-      any_shift = true;
+    for (int qs = 0; qs < nsys; ++qs) {
+      const Sys& S = sys[qs];
+      const int i = S.node;
       const T* Ci = (const T*)(ws + L.Cs) + (size_t)i * n * n;
       const TL* LUi = (const TL*)(ws + L.LUs) + (size_t)i * n * n;
       const int* pivi = (const int*)(ws + L.pivs) + (size_t)i * n;
       const double* Di = (const double*)(ws + L.Ds) + (size_t)i * n;
-      for (size_t e = tid; e < nm; e += NT) RHS[e] = J.form == 1 ? Wc[e] : wmul<T>(cre, cim, U[e]);
+      if (S.quad) {
+        // right-hand side g W + a B W + b B^2 W
+        for (size_t e = tid; e < nm; e += NT) {
+          T v = wmul<T>(S.ar[0], S.ai[0], U[e]);
+          if (S.br[0] != 0.0 || S.bi[0] != 0.0) v = TT::add(v, wmul<T>(S.br[0], S.bi[0], U2[e]));
+          if (S.gr[0] != 0.0 || S.gi[0] != 0.0) v = TT::add(v, wmul<T>(S.gr[0], S.gi[0], Wc[e]));
+          RHS[e] = v;
+        }
+      } else {
+        for (size_t e = tid; e < nm; e += NT) RHS[e] = J.form == 1 ? Wc[e] : wmul<T>(S.cr, S.ci, U[e]);
+      }
       __syncthreads();
       double qq = shifted_solve<T, TL, NB>(J, n, m, Ci, Di, LUi, pivi, RHS, Y, P, RL, smem, oc,
                                            &terr);
       qmax = fmax(qmax, qq);
-      for (size_t e = tid; e < nm; e += NT) Wn[e] = TT::add(Wn[e], wmul<T>(br, bi, Y[e]));
+      if (S.quad)
+        for (size_t e = tid; e < nm; e += NT) Wn[e] = TT::add(Wn[e], Y[e]);
+      else
+        for (size_t e = tid; e < nm; e += NT) Wn[e] = TT::add(Wn[e], wmul<T>(S.wr[0], S.wi[0], Y[e]));
       __syncthreads();
     }
     T* tmp = Wc; Wc = Wn; Wn = tmp;
@@ -705,6 +743,9 @@ __global__ void __launch_bounds__(NT, TCK ? 1 : 2) fm_persistent(FmJob J, FmCoef
   __shared__ oz::Ctx s_oz;
   __shared__ __align__(8) uint64_t s_bars[4];
   __shared__ uint32_t s_tmem;
+  // the shifted systems of the coefficient set (filled per matrix by one thread),
+  // then base[2] and the system count
+  __shared__ __align__(16) Sys s_plan[kMaxTerms + 1];
   char* ws = J.ws + (size_t)blockIdx.x * J.ws_stride;
   const int limit = J.order ? *(volatile int*)(J.counter + 1) : J.batch;
   oz::Ctx* oc = nullptr;
@@ -736,10 +777,10 @@ __global__ void __launch_bounds__(NT, TCK ? 1 : 2) fm_persistent(FmJob J, FmCoef
       if (s_oz.err) break;  // a tensor-core wait timed out: stop taking work
     }
     const int b = J.order ? J.order[item] : item;
-    if (J.kind == JOB_EXPM || J.kind == JOB_PHI1 || J.kind == JOB_PHI1MV)
-      run_matfun<T, TL, NB>(J, cf, b, ws, smem + 1024, oc);
+    if (J.kind == JOB_EXPM || J.kind == JOB_PHI1 || J.kind == JOB_PHI1MV || J.kind == JOB_TRIG)
+      run_matfun<T, TL, NB>(J, cf, b, ws, smem + 1024, oc, s_plan);
     else if (J.kind == JOB_EXPMV)
-      run_action<T, TL, NB>(J, cf, b, ws, smem + 1024, oc);
+      run_action<T, TL, NB>(J, cf, b, ws, smem + 1024, oc, s_plan);
     else if constexpr (sizeof(T) == 8 && sizeof(TL) == 8)
       run_adjoint<NB>(J, cf, b, ws, smem + 1024);
   }

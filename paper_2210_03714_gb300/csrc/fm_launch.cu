@@ -50,6 +50,78 @@ __global__ void fm_order_kernel(const int* __restrict__ d, int batch, int dmax, 
   }
 }
 
+// Step a1 alone: eta = ||t_b A_b||_1 (column sums of |t a| with the rows in
+// ascending order, as every path forms them) or anorm |t_b|; then s (smallest
+// s >= 0 with eta / 2^s <= theta) or N = max(1, ceil(eta / theta)).  One block
+// per matrix.
+template <class T>
+__global__ void fm_select_kernel(const int* __restrict__ d, const int64_t* __restrict__ off,
+                                 const T* __restrict__ A, const double* __restrict__ t, int dmax,
+                                 double anorm, double theta, int steps, long long fixed,
+                                 long long* out, int* info) {
+  __shared__ double red[32];
+  using TT = Tr<T>;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int n = d[b];
+  if (n < 1 || n > dmax) {
+    if (tid == 0) {
+      info[b] = -4;
+      out[b] = 0;
+    }
+    return;
+  }
+  const T* Ab = A + off[b];
+  const double tb = t[b];
+  int bad = !isfinite(tb);
+  double cmax = 0;
+  for (int c = tid; c < n; c += blockDim.x) {
+    double sc = 0;
+    for (int r = 0; r < n; ++r) {
+      const T a = Ab[(size_t)r * n + c];
+      bad |= !TT::finite(a);
+      sc += (double)TT::mag(TT::rscale(a, tb));
+    }
+    cmax = (sc > cmax || isnan(sc)) ? sc : cmax;
+  }
+  bad = __syncthreads_or(bad);
+  for (int o = 16; o; o >>= 1) {
+    const double v = __shfl_xor_sync(0xffffffffu, cmax, o);
+    cmax = (v > cmax || isnan(v)) ? v : cmax;
+  }
+  if ((tid & 31) == 0) red[tid >> 5] = cmax;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = (red[w] > m || isnan(red[w])) ? red[w] : m;
+    const double eta = anorm > 0 ? anorm * fabs(tb) : m;
+    long long v;
+    if (fixed > 0 || (!steps && fixed == 0)) {
+      v = fixed;
+    } else if (steps) {
+      const double qn = ceil(eta / theta);
+      v = qn < 1.0 ? 1 : (long long)qn;
+    } else {
+      int s = 0;
+      while (eta > ldexp(theta, s) && s < 1023) ++s;
+      v = s;
+    }
+    out[b] = v;
+    info[b] = bad ? -2 : 0;
+  }
+}
+
+cudaError_t launch_select(bool cplx, const int* d, const int64_t* off, const void* A,
+                          const double* t, int batch, int dmax, double anorm, double theta,
+                          int steps, long long fixed, long long* out, int* info, cudaStream_t st) {
+  if (cplx)
+    fm_select_kernel<zd><<<batch, 256, 0, st>>>(d, off, (const zd*)A, t, dmax, anorm, theta, steps,
+                                                fixed, out, info);
+  else
+    fm_select_kernel<double><<<batch, 256, 0, st>>>(d, off, (const double*)A, t, dmax, anorm, theta,
+                                                    steps, fixed, out, info);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_order(const int* d, int batch, int dmax, int* order, int* counter, int* info,
                          cudaStream_t st) {
   fm_order_kernel<<<1, 1024, (size_t)(dmax + 1) * sizeof(int), st>>>(d, batch, dmax, order,

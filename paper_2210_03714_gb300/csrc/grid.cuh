@@ -148,6 +148,20 @@ __global__ void build_shift(size_t count, const T* B, double cr, double ci, T* C
   }
 }
 
+// C = u1 B + u2 B2 (each product rounded once; C = u2 B2 when u1 = 0); Y = C
+template <class T>
+__global__ void build_shift2(size_t count, const T* B, double u1r, double u1i, const T* B2,
+                             double u2r, double u2i, T* C, T* Y) {
+  const bool one = u1r == 0.0 && u1i == 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+       e += (size_t)gridDim.x * blockDim.x) {
+    T v = cmul<T>(u2r, u2i, B2[e]);
+    if (!one) v = Tr<T>::add(cmul<T>(u1r, u1i, B[e]), v);
+    C[e] = v;
+    Y[e] = v;
+  }
+}
+
 // a fused +-c pair with Y = (I - c^2 B^2)^-1 - I: F += s Y and G += a Y
 // (G = a Y for the first pair), s = b+ + b-, a = (b+ - b-) c
 template <class T>

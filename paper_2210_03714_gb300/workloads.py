@@ -59,15 +59,30 @@ def batch_flat(dims, norms, seed=1000):
     return out
 
 
-def hermitian_action(d=4096, m=256, rho=20.0, seed=2000):
-    """A = -iH, H = (G + G^H)/2 with G complex N(0,1)/sqrt(d), scaled so that its
-    spectral radius is rho; V complex N(0,1), d x m.  Returns (A, V, rho)."""
+def hermitian_parts(d=4096, m=256, seed=2000):
+    """H = (G + G^H)/2 with G complex N(0,1)/sqrt(d), and V complex N(0,1), d x m,
+    before any scaling (the same draws on every machine)."""
     g = _rng(seed)
     G = (g.standard_normal((d, d)) + 1j * g.standard_normal((d, d))) / np.sqrt(d)
     H = (G + G.conj().T) / 2
-    lam = np.linalg.eigvalsh(H)
-    H *= rho / np.abs(lam).max()
     V = g.standard_normal((d, m)) + 1j * g.standard_normal((d, m))
+    return H, V
+
+
+def hermitian_scale(H, rho):
+    """The factor that gives H spectral radius rho (an eigenvalue routine: its
+    last bits may differ between machines)."""
+    return rho / np.abs(np.linalg.eigvalsh(H)).max()
+
+
+def hermitian_action(d=4096, m=256, rho=20.0, seed=2000, scale=None):
+    """A = -iH, H = (G + G^H)/2 with G complex N(0,1)/sqrt(d), scaled so that its
+    spectral radius is rho (or by the given scale, which rebuilds the same A
+    bit for bit); V complex N(0,1), d x m.  Returns (A, V, rho)."""
+    H, V = hermitian_parts(d, m, seed)
+    if scale is None:
+        scale = hermitian_scale(H, rho)
+    H *= scale
     return -1j * H, V, rho
 
 

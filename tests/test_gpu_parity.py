@@ -368,7 +368,7 @@ def test_status_codes(fm):
     # argument errors raise
     with pytest.raises(fm.FmError):
         fm.expm(T(np.eye(3)), 1.0, {"c_re": [0.1], "b_re": [1.0], "a0": 1.0, "theta": -1.0,
-                                    "conj_pair": 1})
+                                    "conj_pair": 2})
 
 
 def test_invariant_full_size(fm):
