@@ -411,11 +411,25 @@ def run_trid(args, emit=True):
     fm.lib()
     batch, d, eta = args.trid_batch, 1000, 8.0
     form = "plain" if args.form == "plain" else "roundoff"
-    dl, dd, du, v, t = wl.trid_batch(batch, d, eta=eta, seed=5000)
-    Dl, Dd, Du, Vd, Td = (torch.tensor(x, dtype=torch.float64, device=dev)
-                          for x in (dl, dd, du, v, t))
+    penta = args.workload == "penta"
+    if penta:  # half bandwidth 2: fm_band_expmv_batched
+        diags, v, t = wl.penta_batch(batch, d, eta=eta, seed=6000)
+        Dg, Vd, Td = (torch.tensor(x, dtype=torch.float64, device=dev) for x in (diags, v, t))
+        dense_of = lambda b: wl.band_dense(diags, b)
+        host_in = (diags, v, t)
+        dev_in = (Dg, Vd, Td)
+    else:
+        dl, dd, du, v, t = wl.trid_batch(batch, d, eta=eta, seed=5000)
+        Dl, Dd, Du, Vd, Td = (torch.tensor(x, dtype=torch.float64, device=dev)
+                              for x in (dl, dd, du, v, t))
+        dense_of = lambda b: wl.trid_dense(dl, dd, du, b)
+        host_in = (dl, dd, du, v, t)
+        dev_in = (Dl, Dd, Du, Vd, Td)
     cs = fm.Coeffs("R10")
-    call = lambda: fm.trid_expmv_batched(Dl, Dd, Du, Vd, Td, cs, form=form)
+    if penta:
+        call = lambda: fm.band_expmv_batched(Dg, Vd, Td, cs, form=form)
+    else:
+        call = lambda: fm.trid_expmv_batched(Dl, Dd, Du, Vd, Td, cs, form=form)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         call()
@@ -437,9 +451,15 @@ def run_trid(args, emit=True):
     # solves of 13d flops (roundoff: B v and the Thomas solve) or 8d (plain);
     # the kernel's traffic per step: per node and element three factors read
     # and z written and read back, plus v, the diagonals and the output
-    per_solve = 13.0 if form == "roundoff" else 8.0
+    # pentadiagonal (Sec. 1): 15d per solve and 9d per product; per step and
+    # node the kernel reads five factors and writes and reads z
+    if penta:
+        per_solve = 24.0 if form == "roundoff" else 15.0
+        nbytes = float(Ns.sum()) * d * 8.0 * (7 * k + 8) + batch * d * 8.0 * (5 * k + 6)
+    else:
+        per_solve = 13.0 if form == "roundoff" else 8.0
+        nbytes = float(Ns.sum()) * d * 8.0 * (5 * k + 6) + batch * d * 8.0 * (3 * k + 4)
     flops = float(Ns.sum()) * k * per_solve * d
-    nbytes = float(Ns.sum()) * d * 8.0 * (5 * k + 6) + batch * d * 8.0 * (3 * k + 4)
     peaks = load_peaks()
     pk = pipe_peaks(peaks)
     sec = ms / 1000.0
@@ -452,7 +472,8 @@ def run_trid(args, emit=True):
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
     bound = "hbm" if hbm["frac"] > fp64["frac"] else "alu"
     b = hbm if bound == "hbm" else fp64
-    roofline = {"bound": bound, "kernel": "trid_steps", "achieved": b["achieved"],
+    roofline = {"bound": bound, "kernel": "band_steps" if penta else "trid_steps",
+                "achieved": b["achieved"],
                 "peak": b["peak"], "unit": b["unit"], "frac": b["frac"], "traffic": None,
                 "pipes": {"fp64": fp64, "hbm": hbm},
                 "note": "whole call (the factorization launch included); fp64: the paper's "
@@ -460,11 +481,11 @@ def run_trid(args, emit=True):
                         "traffic over the measured copy bandwidth"}
     # one sampled system against the oracle (dense LU of the same matrix)
     Wh = W[:, 7].cpu().numpy()
-    ref, Nr, _ = oracle.expmv(wl.trid_dense(dl, dd, du, 7), v[:, 7], t[7], "R10",
+    ref, Nr, _ = oracle.expmv(dense_of(7), v[:, 7], t[7], "R10",
                               oracle.PLAIN if form == "plain" else oracle.ROUNDOFF)
     err = float(np.linalg.norm(Wh - ref) / np.linalg.norm(ref))
     # end to end with host buffers: inputs in, result and status out, per step
-    pins = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (dl, dd, du, v, t)]
+    pins = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in host_in]
     W_host = torch.empty((d, batch), dtype=torch.float64).pin_memory()
     info_host = torch.empty(batch, dtype=torch.int32).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
@@ -473,7 +494,7 @@ def run_trid(args, emit=True):
             torch.cuda.synchronize()
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-        for dst, src in zip((Dl, Dd, Du, Vd, Td), pins):
+        for dst, src in zip(dev_in, pins):
             dst.copy_(src, non_blocking=True)
         W, info, N = call()
         W_host.copy_(W, non_blocking=True)
@@ -487,18 +508,23 @@ def run_trid(args, emit=True):
     cpu = None
     if not args.no_cpu_baseline:
         t0 = time.perf_counter()
-        oracle.expmv(wl.trid_dense(dl, dd, du, 8), v[:, 8], t[8], "R10",
+        oracle.expmv(dense_of(8), v[:, 8], t[8], "R10",
                      oracle.PLAIN if form == "plain" else oracle.ROUNDOFF)
         cs_ = time.perf_counter() - t0
         cpu = {"value": 1.0 / cs_, "unit": "systems/s", "cores": oracle.num_threads(),
                "kind": "oracle", "sample": "1 system of the batch (dense LU of the same matrix)"}
-    line = {"metric": "tridiagonal action evals/sec (systems/s) at <=1e-12 rel err",
+    kind_name = "pentadiagonal" if penta else "tridiagonal"
+    line = {"metric": "%s action evals/sec (systems/s) at <=1e-12 rel err" % kind_name,
             "value": batch / sec, "unit": "systems/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "replicas", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "exp(t A) v: %d tridiagonal A of order 1000, "
-                                   "A = -trid{1+e, 2(1+e), 1+e} (e ~ 0.05 N(0,1)), v unit "
-                                   "random, ||t A||_1 = 8, R10 %s form (N = 36)" % (batch, form),
+            "config": {"workload": (("exp(t A) v: %d pentadiagonal A of order 1000, the "
+                                    "fourth-order stencil (-1, 16, -30, 16, -1)/12 with each "
+                                    "entry times 1 + 0.05 N(0,1), v unit random, ||t A||_1 = 8, "
+                                    "R10 %s form" % (batch, form)) if penta else
+                                   ("exp(t A) v: %d tridiagonal A of order 1000, "
+                                    "A = -trid{1+e, 2(1+e), 1+e} (e ~ 0.05 N(0,1)), v unit "
+                                    "random, ||t A||_1 = 8, R10 %s form (N = 36)" % (batch, form))),
                        "l2": "working set (GBs) larger than L2"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "status_nonzero": bad, "rel_err_vs_oracle_sample": err, "cpu_baseline": cpu,
@@ -714,7 +740,8 @@ def other_configs(args):
             ("gradient_256x128", "adjoint", run_small, dict(steps=3, warmup=1)),
             ("hermitian_action_d4096", "hermitian", run_single, dict(steps=2, warmup=1)),
             ("diffusion_phi1_512x512", "diffusion", run_single, dict(steps=2, warmup=1)),
-            ("trid_action_32768x1000", "trid", run_trid, dict(steps=3, warmup=1)))
+            ("trid_action_32768x1000", "trid", run_trid, dict(steps=3, warmup=1)),
+            ("penta_action_32768x1000", "penta", run_trid, dict(steps=3, warmup=1)))
     for name, wl_name, fn, kw in plan:
         a = copy.copy(args)
         a.workload = wl_name
@@ -749,13 +776,14 @@ def main():
     ap.add_argument("--dims", default=None,
                     help="comma-separated orders d is drawn from (default 16,32,...,256)")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "hermitian", "dense", "diffusion", "trid", "single",
-                             "adjoint"],
+                    choices=["batch", "hermitian", "dense", "diffusion", "trid", "penta",
+                             "single", "adjoint"],
                     help="batch: the 4096-matrix exp batch (default); hermitian: exp(-iH)V, "
                          "d = 4096, V 4096 x 256, N = 206 steps; dense: exp(A), one real "
                          "matrix of order --dim (both on the grid path); diffusion: phi_1 "
                          "of 512 matrices of order 512 (batched grid path); trid: exp(tA)v "
-                         "for 32768 tridiagonal A of order 1000 (Thomas solves); single: exp "
+                         "for 32768 tridiagonal A of order 1000 (Thomas solves); penta: the "
+                         "same with pentadiagonal A (banded LU); single: exp "
                          "of one d = 64 matrix; adjoint: the gradient batch (256 x 128^2)")
     ap.add_argument("--trid-batch", type=int, default=32768,
                     help="systems of order 1000 for --workload trid")
@@ -772,7 +800,7 @@ def main():
         print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the "
                           "oracle on the default batch workload only"}), flush=True)
         return 0
-    if args.workload == "trid":
+    if args.workload in ("trid", "penta"):
         run_trid(args)
         return 0
     if args.workload in ("single", "adjoint"):

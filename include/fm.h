@@ -180,8 +180,10 @@ enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       
  * this path synchronize their stream (s or N, the batch orders and the
  * iteration counts are read on the host).
  * FM_PATH_AUTO: FM_BF16_IR calls, single-matrix calls with d > fm_max_dim(),
- * and batched exp, phi_1 and phi_1 V in FM_MIXED with dmax >= 64 take the grid
- * path; everything else the one-CTA kernels.  A precision value and a path
+ * and batched exp, phi_1, phi_1 V and cos/sin in FM_MIXED with dmax >= 64 take
+ * the grid path; everything else the one-CTA kernels.  After fm_autotune (or
+ * with its FM_TUNE_CACHE), batched matrix functions in FM_MIXED are split at
+ * the measured order d* instead.  A precision value and a path
  * that do not go together (FM_FP32_IR with FM_PATH_GRID, FM_BF16_IR with
  * FM_PATH_CTA, a batched action on the grid path) give FM_EINVAL. */
 enum { FM_PATH_AUTO = 0, FM_PATH_CTA = 1, FM_PATH_GRID = 2 };
@@ -386,20 +388,82 @@ fm_status fm_trid_expmv_batched(const fm_coeffs* cs, int batch, int d, const dou
  * d and a set of k terms (0 for a bad argument). */
 size_t fm_trid_workspace_size(int batch, int d, int k);
 
+/* ---- autotuner: which kernels take which orders of a batch -------------- */
+/* The paper has no counterpart (it has no hardware): this measures, on the
+ * current device, batches of matrix functions (job FM_JOB_EXPM, FM_JOB_PHI1 or
+ * FM_JOB_COSSIN with sets ce, cp) of each probe order d in {16, 32, 48, 64, 96,
+ * 128, ..., 1024} up to dmax, on the one-CTA kernels (FM_FP32_IR) and on the
+ * batched grid path (FM_BF16_IR): synthetic matrices with ||A||_1 about 4,
+ * the best of two calls timed with CUDA events on the stream.  It records d*,
+ * the smallest probe order from which the grid path is at least as fast at
+ * every larger probe (1: the grid path everywhere; dmax + 1: nowhere).  From
+ * then on, batched calls of that job in FM_MIXED with FM_PATH_AUTO on this
+ * device run the orders below d* on the one-CTA kernels and the rest on the
+ * grid path (two launches one after the other; each leaves the other's
+ * matrices and status alone).  If the environment variable FM_TUNE_CACHE
+ * names a file, the result is appended to it as "device|job|d*" and read back
+ * by the first batched call of a later process.  table_out (nullable, host,
+ * 3 x 16 doubles): per probe (d, microseconds per matrix on the one-CTA
+ * kernels, on the grid path); nprobe_out: the number of probes.  Allocates its
+ * probe batches (cudaMallocAsync) and synchronizes the stream.  Errors:
+ * FM_EINVAL (job, sets), FM_ESHAPE (dmax), FM_ECUDA, FM_ENOMEM. */
+fm_status fm_autotune(const fm_coeffs* ce, const fm_coeffs* cp, int job, int dmax,
+                      const fm_opts* opts, void* stream, int* dstar_out, double* table_out,
+                      int* nprobe_out);
+
+/* Forget every tuned d* of this process: FM_PATH_AUTO takes the fixed rule
+ * again, unless FM_TUNE_CACHE (read again by the next batched call) names a
+ * file with entries for this device. */
+void fm_autotune_reset(void);
+
+/* ---- actions of banded matrices (Sec. 1, Sec. 5.1) ----------------------- */
+/* W_b = r(B_b)^(N_b) V_b ~ exp(t_b A_b) V_b for a batch of banded A_b of one
+ * order d and half bandwidth p (1: tridiagonal, 2: pentadiagonal): the
+ * action recurrence of Sec. 1 as in fm_trid_expmv_batched.  Every shifted
+ * matrix I - c_i B_b is banded with the same p (Sec. 1: a pentadiagonal system
+ * is solved in 15d flops and the product A v costs 9d), factored once per call
+ * by banded LU without pivoting (|c_i| ||B||_1 is far below 1/2 at
+ * ||B||_1 <= theta: diagonally dominant) and solved in every step.  p = 1 runs
+ * fm_trid_expmv_batched on the same layout.
+ *
+ * Layout (DEVICE, double, batch-interleaved): diagonal j = 0 .. 2p (offset
+ * o = j - p) holds A[k][k + o] of system b at (j d + k) batch + b; entries
+ * with k + o outside [0, d) are not read.  V, W, t_dev, info_dev, nsteps_dev and
+ * the status values as fm_trid_expmv_batched (info: 0, -2 non-finite entry,
+ * or i d + row for an exactly zero pivot of term i).  Double precision; the set
+ * must have real nodes (conj_pair = 0), at least one nonzero, and one function.
+ * Scratch: fm_band_workspace_size bytes.  Stream-ordered, no host
+ * synchronization.  Errors: FM_EINVAL (NULL pointer, p not 1 or 2, bad set),
+ * FM_ESHAPE (batch or d < 1), FM_ENOMEM, FM_ECUDA. */
+fm_status fm_band_expmv_batched(const fm_coeffs* cs, int batch, int d, int p,
+                                const double* diags, const double* t_dev, const double* V,
+                                double* W, int* info_dev, int* nsteps_dev, const fm_opts* opts,
+                                void* stream);
+
+/* Bytes of device scratch of fm_band_expmv_batched (0 for a bad argument). */
+size_t fm_band_workspace_size(int batch, int d, int p, int k);
+
 /* ---- exp(tA) without any device allocation ------------------------------ */
 /* The paper has no counterpart: this is a deployment variant of fm_expm for
  * callers that cannot allocate device memory (code that runs where cudaMalloc
- * is forbidden or could deadlock, such as allocator or stream callbacks, and
- * hosts that own every device byte).  Same arguments and results as fm_expm
- * (real, one matrix), but its scratch is a fixed array inside the library
- * image, reserved on every GPU that loads the library until the process exits;
- * opts.workspace is ignored and nothing is allocated.
+ * is forbidden or could deadlock, such as a custom allocator or a memory-pool
+ * hook, and hosts that own every device byte).  Same arguments and results as
+ * fm_expm on the one-CTA kernel (real, one matrix), but its scratch is a fixed
+ * array inside the library image; opts.workspace is ignored.
  *   - d <= FM_NOALLOC_MAX_DIM and the scratch the call needs must fit in
  *     FM_NOALLOC_SCRATCH_BYTES, else FM_ESHAPE with a message.
+ *   - opts.path = FM_PATH_GRID and opts.precision = FM_BF16_IR are rejected
+ *     (FM_EINVAL): there is no grid form without scratch.
  *   - Every call uses the same array: calls that overlap on the GPU (several
  *     streams or host threads) race and give wrong results; serialize them.
- *   - The first call on a device looks up the array's device address with
- *     that device current; make it before any stream capture.
+ *   - CUDA loads the library's device code, the array included, on a device
+ *     when it is first used there: the first call on each device commits the
+ *     array and looks up its device address with that device current, and can
+ *     fail with FM_ECUDA when the device is out of memory.  Make that first call
+ *     once per device as a warm-up, before any stream capture and outside any
+ *     code that must not allocate; later calls allocate nothing.
+ *   - Not for host functions enqueued on a stream (cudaLaunchHostFunc): CUDA
+ *     allows no CUDA call there, and this entry point launches kernels.
  *   - info_host / s_host (nullable) make the call synchronize the stream. */
 #define FM_NOALLOC_MAX_DIM 128
 #define FM_NOALLOC_SCRATCH_BYTES (2u << 20)

@@ -8,9 +8,11 @@ from ._ffi import lib, FmError, BUILTIN, default_opts, exported_symbols, last_st
 from .api import (Coeffs, Packed, expm, phi1, expmv, phi1mv, expm_batched,  # noqa: F401
                   phi1_batched, expmv_batched, phi1mv_batched, expmv_adjoint_batched,
                   select_batched, ExpmvFn, trid_expmv_batched, cossin, cossin_batched, rfun,
-                  rfun_batched)
+                  rfun_batched, band_expmv_batched,
+                  autotune)
 
 __all__ = ["lib", "FmError", "Coeffs", "Packed", "expm", "phi1", "expmv", "phi1mv",
            "expm_batched", "phi1_batched", "expmv_batched", "phi1mv_batched",
            "expmv_adjoint_batched", "select_batched", "ExpmvFn", "trid_expmv_batched", "cossin",
-           "cossin_batched", "rfun", "rfun_batched"]
+           "cossin_batched", "rfun", "rfun_batched", "band_expmv_batched",
+           "autotune"]

@@ -102,6 +102,9 @@ _SIGS = {
     "fm_trid_expmv_batched": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, C.c_int, _P, _P, _P, _P,
                                         _P, _P, _P, _P, C.POINTER(fm_opts), _P]),
     "fm_trid_workspace_size": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+    "fm_band_expmv_batched": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, C.c_int, C.c_int, _P, _P,
+                                        _P, _P, _P, _P, C.POINTER(fm_opts), _P]),
+    "fm_band_workspace_size": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int]),
     "fm_cossin": (C.c_int, [C.POINTER(fm_coeffs), C.POINTER(fm_coeffs), C.c_int, _P, C.c_int,
                             C.c_double, _P, C.c_int, _P, C.c_int, C.POINTER(fm_opts), _P, c_ip,
                             c_ip]),
@@ -111,6 +114,9 @@ _SIGS = {
                           C.POINTER(fm_opts), _P, c_ip]),
     "fm_rfun_batched": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, C.c_int, _P, _P, _P, _P, _P, _P,
                                   C.POINTER(fm_opts), _P]),
+    "fm_autotune": (C.c_int, [C.POINTER(fm_coeffs), C.POINTER(fm_coeffs), C.c_int, C.c_int,
+                              C.POINTER(fm_opts), _P, c_ip, c_dp, c_ip]),
+    "fm_autotune_reset": (None, []),
     "fm_select_batched": (C.c_int, [C.POINTER(fm_coeffs), C.POINTER(fm_coeffs), C.c_int, C.c_int,
                                     C.c_int, _P, _P, _P, _P, _P, _P, C.POINTER(fm_opts), _P]),
     "fm_expm_noalloc": (C.c_int, [C.POINTER(fm_coeffs), C.c_int, _P, C.c_int, C.c_double, _P,

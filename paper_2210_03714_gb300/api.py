@@ -348,6 +348,32 @@ def trid_expmv_batched(dl, dd, du, V, t=1.0, coeffs="R10", form="roundoff", **kw
     return W, info, ns
 
 
+def band_expmv_batched(diags, V, t=1.0, coeffs="R10", form="roundoff", **kw):
+    """exp(t_b A_b) v_b for a batch of banded A_b (fm_band_expmv_batched).
+
+    diags: float64 CUDA tensor of shape (2p + 1, d, batch): diags[j, k, b] =
+    A_b[k][k + j - p] (half bandwidth p = 1 or 2); V: (d, batch).  Returns
+    (W (d, batch), info, N)."""
+    _need(V, torch.float64, "V")
+    if not isinstance(diags, torch.Tensor) or not diags.is_cuda or diags.dtype != torch.float64:
+        raise TypeError("diags must be a float64 CUDA tensor")
+    if diags.dim() != 3 or diags.shape[0] not in (3, 5) or not diags.is_contiguous():
+        raise ValueError("diags must be a contiguous (2p + 1, d, batch) tensor, p = 1 or 2")
+    p = (diags.shape[0] - 1) // 2
+    d, n = V.shape
+    if tuple(diags.shape[1:]) != (d, n) or not V.is_contiguous():
+        raise ValueError("V must be a contiguous (d, batch) tensor matching diags")
+    W = torch.empty_like(V)
+    info = torch.empty(n, dtype=torch.int32, device=V.device)
+    ns = torch.empty(n, dtype=torch.int32, device=V.device)
+    td = _tdev(t, n, V.device)
+    cs = _cs(coeffs)
+    o = _opts("fp64", form=form, **kw)
+    check(lib().fm_band_expmv_batched(cs.ptr(), n, d, p, _p(diags), _p(td), _p(V), _p(W),
+                                      _p(info), _p(ns), C.byref(o), _stream()))
+    return W, info, ns
+
+
 def expmv_adjoint_batched(P, v, wbar, nsteps, t=1.0, coeffs="R8"):
     """Forward w_N and gradients (Abar flat, vbar flat) of <wbar, w_N> for
     N = nsteps[b] steps (fixed); always double precision."""
@@ -385,6 +411,20 @@ def select_batched(P, t=1.0, coeffs="R8", job="expmv", cphi=None, **kw):
                                   P.dmax, _p(P.d_dev), _p(P.off_dev), _p(P.flat), _p(td), _p(out),
                                   _p(info), C.byref(o), _stream()))
     return out, info
+
+
+def autotune(job="expm", coeffs="R8", cphi=None, dmax=256, **kw):
+    """fm_autotune on the current device and stream: returns (d*, table) where
+    table lists (d, microseconds per matrix on the one-CTA kernels, on the
+    batched grid path) per probe order."""
+    cs = _cs(coeffs)
+    cp = _cs(cphi) if cphi is not None else None
+    o = _opts("mixed", **kw)
+    dstar, n = C.c_int(0), C.c_int(0)
+    tab = (C.c_double * 48)()
+    check(lib().fm_autotune(cs.ptr(), cp.ptr() if cp is not None else None, _ffi.JOB[job], dmax,
+                            C.byref(o), _stream(), C.byref(dstar), tab, C.byref(n)))
+    return dstar.value, [(int(tab[3 * i]), tab[3 * i + 1], tab[3 * i + 2]) for i in range(n.value)]
 
 
 def _raise_info(info, what):

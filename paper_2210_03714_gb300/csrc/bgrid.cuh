@@ -40,10 +40,12 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
   __shared__ double red[32];
   const BMat M = mats[blockIdx.x];
   const int n = M.d, tid = threadIdx.x;
-  if (n == 0) {  // order outside [1, dmax]: left out of the call
+  if (n <= 0) {  // order outside [1, dmax] (0), or the other part of a split batch (-1)
     if (tid == 0) {
-      if (s_out) s_out[blockIdx.x] = 0;
-      info[blockIdx.x] = -4;
+      if (n == 0) {
+        if (s_out) s_out[blockIdx.x] = 0;
+        info[blockIdx.x] = -4;
+      }
       alive[blockIdx.x] = 0;
     }
     return;

@@ -6,12 +6,16 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "../../include/fm.h"
+#include "fm_band.h"
 #include "fm_bgrid.h"
 #include "fm_grid.h"
 #include "fm_job.h"
@@ -327,6 +331,9 @@ struct Call {
   int* info_host;
   int* s_host;
   long* n_host;
+  // a part of a split batch: only orders in [part_lo, part_hi] (0: no bound);
+  // the others are left to the other part, their status untouched
+  int part_lo, part_hi;
 };
 
 // single matrix over the whole GPU (fm_grid.cu)
@@ -402,9 +409,13 @@ fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "reading the batch orders");
   // a matrix whose order is outside [1, dmax] is left out (order 0 in the
-  // tables: no tiles, no elements) and gets info = -4, as on the one-CTA path
-  for (int b = 0; b < c.batch; ++b)
+  // tables: no tiles, no elements) and gets info = -4, as on the one-CTA path;
+  // one that belongs to the other part of a split batch is left out (order -1)
+  // without a status
+  for (int b = 0; b < c.batch; ++b) {
     if (d[b] < 1 || d[b] > c.dmax) d[b] = 0;
+    else if ((c.part_lo > 0 && d[b] < c.part_lo) || (c.part_hi > 0 && d[b] > c.part_hi)) d[b] = -1;
+  }
   j.kind = c.kind;
   j.cplx = c.cplx;
   j.form = o.form;
@@ -433,6 +444,87 @@ fm_status run_bgrid(const Call& c, const fm_opts& o, cudaStream_t st) {
   return (fm_status)bgrid_run(j, g_err, sizeof g_err);
 }
 
+// ---- autotuned split of batched matrix functions -----------------------
+// fm_autotune records, per device and job, the order d* from which the
+// batched grid path beats the one-CTA kernels; FM_PATH_AUTO batches in
+// FM_MIXED then run orders below d* on the one-CTA kernels and the rest on the
+// grid path.  d* <= 1: everything on the grid path.
+struct TuneRec {
+  bool have[3] = {false, false, false};
+  int dstar[3] = {0, 0, 0};
+};
+std::mutex g_tune_mu;
+std::vector<TuneRec> g_tune;
+bool g_tune_loaded = false;
+
+int tune_slot(int kind) {
+  switch (kind) {
+    case JOB_EXPM: return 0;
+    case JOB_PHI1: case JOB_PHI1MV: return 1;
+    case JOB_TRIG: return 2;
+    default: return -1;
+  }
+}
+
+std::string device_key(int dev) {
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string k = pr.name;
+  for (char& ch : k)
+    if (ch == ' ' || ch == '|') ch = '_';
+  return k;
+}
+
+// the table of FM_TUNE_CACHE (lines "device|slot|dstar"), read once
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("FM_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    fclose(f);
+    return;
+  }
+  if ((int)g_tune.size() < ndev) g_tune.resize(ndev);
+  char line[256];
+  while (fgets(line, sizeof line, f)) {
+    char name[200];
+    int slot = -1, dstar = 0;
+    if (sscanf(line, "%199[^|]|%d|%d", name, &slot, &dstar) != 3 || slot < 0 || slot > 2) continue;
+    for (int dv = 0; dv < ndev; ++dv)
+      if (device_key(dv) == name) {
+        g_tune[dv].have[slot] = true;
+        g_tune[dv].dstar[slot] = dstar;
+      }
+  }
+  fclose(f);
+}
+
+// d* for this device and job, or 0 when not tuned
+int tuned_dstar(int kind) {
+  const int slot = tune_slot(kind);
+  if (slot < 0) return 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  if ((int)g_tune.size() <= dev || !g_tune[dev].have[slot]) return 0;
+  const int v = g_tune[dev].dstar[slot];
+  return v < 1 ? 1 : v;
+}
+
+fm_status run_cta(const Call& c, fm_opts o, cudaStream_t st);
+
 fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   memset(&g_stats, 0, sizeof g_stats);
   fm_opts o = resolve_opts(optsp);
@@ -442,12 +534,33 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   if (c.batch < 1) return fail(FM_ESHAPE, "batch must be >= 1");
   const bool single = c.d_dev == nullptr && c.kind != JOB_ADJ;
   const char* why = "";
-  const Route r = route(c.kind, single, c.dmax, o.precision, o.path, &why);
+  Route r = route(c.kind, single, c.dmax, o.precision, o.path, &why);
   if (r == R_BAD) return fail(FM_EINVAL, why);
+  // batches of matrix functions in FM_MIXED with a tuned split order
+  int dstar = 0;
+  if (!single && o.path == FM_PATH_AUTO && o.precision == FM_MIXED && !c.cplx &&
+      c.dmax <= fm_max_dim() && tune_slot(c.kind) >= 0 && c.part_lo == 0 && c.part_hi == 0)
+    dstar = tuned_dstar(c.kind);
   // the kernels see 0 (double) or 1 (single factors / tensor-core products)
   o.precision = o.precision == FM_FP64 ? 0 : 1;
+  if (dstar > 0) {
+    if (dstar <= 1) return run_bgrid(c, o, st);
+    if (dstar > c.dmax) return run_cta(c, o, st);
+    Call lo = c, hi = c;
+    lo.part_hi = dstar - 1;
+    hi.part_lo = dstar;
+    s = run_cta(lo, o, st);
+    if (s) return s;
+    return run_bgrid(hi, o, st);
+  }
   if (r == R_BGRID) return run_bgrid(c, o, st);
   if (r == R_GRID && c.dmax >= 1) return run_grid(c, o, st);
+  return run_cta(c, o, st);
+}
+
+// the one-CTA kernels (o.precision already 0 or 1)
+fm_status run_cta(const Call& c, fm_opts o, cudaStream_t st) {
+  fm_status s;
   if (c.dmax < 1 || c.dmax > fm_max_dim()) return fail(FM_ESHAPE, "d (or dmax) must be in [1, fm_max_dim()]");
   if ((c.kind == JOB_EXPMV || c.kind == JOB_PHI1MV) && c.m < 1) return fail(FM_ESHAPE, "m must be >= 1");
   if (!c.A) return fail(FM_EINVAL, "A is NULL");
@@ -473,7 +586,9 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   s = pack(c.ce, c.cp, c.cplx, o.form, cf);
   if (s) return s;
 
-  Plan p = make_plan(c.kind, c.cplx, o.precision, c.batch, c.dmax, c.m, cf.k, c.nsteps_max);
+  // the lower part of a split batch only holds orders up to part_hi
+  const int dplan = c.part_hi > 0 && c.part_hi < c.dmax ? c.part_hi : c.dmax;
+  Plan p = make_plan(c.kind, c.cplx, o.precision, c.batch, dplan, c.m, cf.k, c.nsteps_max);
   void* ws = nullptr;
   std::unique_lock<std::mutex> hold;  // the scratch stays ours until the work is queued
   s = get_scratch(p.total, &o, &ws, st, &hold);
@@ -524,7 +639,8 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
 
   cudaError_t e;
   if (c.d_dev) {
-    e = launch_order(c.d_dev, c.batch, c.dmax, (int*)J.order, J.counter, c.info_dev, st);
+    e = launch_order(c.d_dev, c.batch, c.dmax, c.part_lo > 0 ? c.part_lo : 1,
+                     c.part_hi > 0 ? c.part_hi : c.dmax, (int*)J.order, J.counter, c.info_dev, st);
     if (e != cudaSuccess) return cuda_fail(e, "order kernel launch");
   } else {
     int hdr[4] = {0, 1, 0, 0};
@@ -979,6 +1095,220 @@ fm_status fm_select_batched(const fm_coeffs* cs, const fm_coeffs* cphi, int job,
   if (e != cudaSuccess) return cuda_fail(e, "fm_select_batched launch");
   g_stats.launches = 1;
   return FM_OK;
+}
+
+fm_status fm_band_expmv_batched(const fm_coeffs* cs, int batch, int d, int p,
+                                const double* diags, const double* t_dev, const double* V,
+                                double* W, int* info_dev, int* nsteps_dev, const fm_opts* opts,
+                                void* stream) {
+  if (p == 1) {  // the tridiagonal path, on the same layout
+    const size_t plane = (size_t)d * (size_t)(batch > 0 ? batch : 0);
+    return fm_trid_expmv_batched(cs, batch, d, diags, diags ? diags + plane : nullptr,
+                                 diags ? diags + 2 * plane : nullptr, t_dev, V, W, info_dev,
+                                 nsteps_dev, opts, stream);
+  }
+  memset(&g_stats, 0, sizeof g_stats);
+  if (p != 2) return fail(FM_EINVAL, "fm_band_expmv_batched: half bandwidth p must be 1 or 2");
+  fm_opts o = resolve_opts(opts);
+  fm_status s = check_opts(o);
+  if (s) return s;
+  if (batch < 1 || d < 1) return fail(FM_ESHAPE, "fm_band_expmv_batched: batch and d must be >= 1");
+  if (!diags || !t_dev || !V || !W || !info_dev)
+    return fail(FM_EINVAL, "fm_band_expmv_batched: NULL pointer");
+  FmCoef cf;
+  s = pack(cs, nullptr, false, o.form, cf);
+  if (s) return s;
+  if (cf.conj_pair)
+    return fail(FM_EINVAL, "fm_band_expmv_batched: the set must have real nodes (conj_pair = 0)");
+  int nonzero = 0;
+  for (int i = 0; i < cf.k; ++i) nonzero += cf.c_re[i] != 0.0;
+  if (!nonzero) return fail(FM_EINVAL, "fm_band_expmv_batched: the set needs a nonzero node");
+  const size_t need = penta_ws_bytes(batch, d, cf.k);
+  void* ws = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::unique_lock<std::mutex> hold;  // the scratch stays ours until the work is queued
+  s = get_scratch(need, &o, &ws, st, &hold);
+  if (s) return s;
+  PentaJob j;
+  j.batch = batch;
+  j.d = d;
+  j.form = o.form;
+  j.diags = diags;
+  j.t = t_dev;
+  j.V = V;
+  j.W = W;
+  j.info = info_dev;
+  j.nsteps = nsteps_dev;
+  j.anorm = o.anorm;
+  j.nsteps_fixed = o.nsteps;
+  j.cf = cf;
+  j.ws = ws;
+  j.ws_bytes = o.workspace ? o.workspace_bytes : need;
+  j.st = st;
+  char msg[256];
+  const int r = penta_run(j, msg, sizeof msg);
+  if (r) return fail((fm_status)r, msg);
+  g_stats.launches = 2;
+  return FM_OK;
+}
+
+size_t fm_band_workspace_size(int batch, int d, int p, int k) {
+  if (k < 1 || k > FM_MAX_TERMS) return 0;
+  if (p == 1) return trid_ws_bytes(batch, d, k);
+  if (p == 2) return penta_ws_bytes(batch, d, k);
+  return 0;
+}
+
+fm_status fm_autotune(const fm_coeffs* ce, const fm_coeffs* cp, int job, int dmax,
+                      const fm_opts* opts, void* stream, int* dstar_out, double* table_out,
+                      int* nprobe_out) {
+  memset(&g_stats, 0, sizeof g_stats);
+  int kind;
+  switch (job) {
+    case FM_JOB_EXPM: kind = JOB_EXPM; break;
+    case FM_JOB_PHI1: kind = JOB_PHI1; break;
+    case FM_JOB_COSSIN: kind = JOB_TRIG; break;
+    default: return fail(FM_EINVAL, "fm_autotune: job must be FM_JOB_EXPM, FM_JOB_PHI1 or FM_JOB_COSSIN");
+  }
+  const bool two = kind != JOB_EXPM;
+  if (two && !cp) return fail(FM_EINVAL, "fm_autotune: this job needs both coefficient sets");
+  if (dmax < 1 || dmax > fm_max_dim()) return fail(FM_ESHAPE, "fm_autotune: dmax must be in [1, fm_max_dim()]");
+  fm_opts base = resolve_opts(opts);
+  fm_status s = check_opts(base);
+  if (s) return s;
+  base.workspace = nullptr;
+  base.workspace_bytes = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  static const int kProbe[] = {16, 32, 48, 64, 96, 128, 160, 192, 224, 256, 384, 512, 768, 1024};
+  std::vector<int> probes;
+  for (int d : kProbe)
+    if (d <= dmax) probes.push_back(d);
+  if (probes.empty()) probes.push_back(dmax);
+  std::vector<double> tc(probes.size()), tg(probes.size());
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return cuda_fail(e, "fm_autotune: cudaEventCreate");
+  fm_status result = FM_OK;
+  for (size_t pi = 0; pi < probes.size() && result == FM_OK; ++pi) {
+    const int d = probes[pi];
+    long long P = (1LL << 22) / ((long long)d * d);
+    P = P < 8 ? 8 : (P > 512 ? 512 : P);
+    const size_t nn = (size_t)d * d;
+    double *A = nullptr, *F = nullptr, *E = nullptr, *t = nullptr;
+    int *dd = nullptr, *info = nullptr, *sv = nullptr;
+    int64_t* off = nullptr;
+    e = cudaMallocAsync((void**)&A, P * nn * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&F, P * nn * 8, st);
+    if (e == cudaSuccess && two) e = cudaMallocAsync((void**)&E, P * nn * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&t, P * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&dd, P * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&info, P * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&sv, P * 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&off, P * 8, st);
+    std::vector<int> hd(P, d);
+    std::vector<int64_t> ho(P);
+    std::vector<double> ht(P, 1.0);
+    for (long long b = 0; b < P; ++b) ho[b] = b * (int64_t)nn;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, hd.data(), P * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(off, ho.data(), P * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t, ht.data(), P * 8, cudaMemcpyHostToDevice, st);
+    // ||A||_1 about 4 (entries uniform in [-8/d, 8/d)): a few squarings, as in use
+    if (e == cudaSuccess) e = launch_probe_fill(A, (long long)(P * nn), 1234567ULL + d, 8.0 / d, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      result = cuda_fail(e, "fm_autotune: probe set-up");
+    }
+    for (int path = 0; path < 2 && result == FM_OK; ++path) {
+      fm_opts o = base;
+      o.path = path == 0 ? FM_PATH_CTA : FM_PATH_GRID;
+      o.precision = path == 0 ? FM_FP32_IR : FM_BF16_IR;
+      Call c = {};
+      c.kind = kind;
+      c.ce = ce;
+      c.cp = two ? cp : nullptr;
+      c.batch = (int)P;
+      c.dmax = d;
+      c.d_dev = dd;
+      c.off = off;
+      c.t_dev = t;
+      c.A = A;
+      c.F = F;
+      c.E = E;
+      c.info_dev = info;
+      c.s_dev = sv;
+      double best = 1e300;
+      for (int rep = 0; rep < 3 && result == FM_OK; ++rep) {
+        if (rep > 0) cudaEventRecord(e0, st);
+        fm_status r = run(c, &o, st);
+        if (r != FM_OK) {
+          result = r;
+          break;
+        }
+        if (rep > 0) {
+          cudaEventRecord(e1, st);
+          e = cudaEventSynchronize(e1);
+          float ms = 0;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) {
+            result = cuda_fail(e, "fm_autotune: timing");
+            break;
+          }
+          best = fmin(best, (double)ms);
+        }
+      }
+      (path == 0 ? tc : tg)[pi] = best * 1000.0 / (double)P;  // microseconds per matrix
+    }
+    cudaFreeAsync(A, st);
+    cudaFreeAsync(F, st);
+    if (E) cudaFreeAsync(E, st);
+    cudaFreeAsync(t, st);
+    cudaFreeAsync(dd, st);
+    cudaFreeAsync(info, st);
+    cudaFreeAsync(sv, st);
+    cudaFreeAsync(off, st);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != FM_OK) return result;
+  // d*: the smallest probe from which the grid path is at least as fast at
+  // every larger probe (orders below it take the one-CTA kernels)
+  size_t i = probes.size();
+  while (i > 0 && tg[i - 1] <= tc[i - 1]) --i;
+  const int dstar = i == 0 ? 1 : (i == probes.size() ? dmax + 1 : probes[i]);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    if ((int)g_tune.size() <= dev) g_tune.resize(dev + 1);
+    const int slot = tune_slot(kind);
+    g_tune[dev].have[slot] = true;
+    g_tune[dev].dstar[slot] = dstar;
+    const char* path = getenv("FM_TUNE_CACHE");
+    if (path && *path) {
+      FILE* f = fopen(path, "a");
+      if (f) {
+        fprintf(f, "%s|%d|%d\n", device_key(dev).c_str(), slot, dstar);
+        fclose(f);
+      }
+    }
+  }
+  if (dstar_out) *dstar_out = dstar;
+  if (nprobe_out) *nprobe_out = (int)probes.size();
+  if (table_out)
+    for (size_t q = 0; q < probes.size(); ++q) {
+      table_out[3 * q] = probes[q];
+      table_out[3 * q + 1] = tc[q];
+      table_out[3 * q + 2] = tg[q];
+    }
+  return FM_OK;
+}
+
+void fm_autotune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  g_tune_loaded = false;  // the next batched call reads FM_TUNE_CACHE again
 }
 
 size_t fm_trid_workspace_size(int batch, int d, int k) {

@@ -35,8 +35,8 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
   const int parts = cplx ? 2 : 1;
   for (int b = 0; b < batch; ++b) {
     grid::BMat& M = g.mats[b];
-    const int n = d[b];
-    M.d = n;
+    const int n = d[b] > 0 ? d[b] : 0;  // 0: bad order, -1: the other part of a split batch
+    M.d = d[b] > 0 ? n : d[b];
     M.mtn = (n + oz::TM - 1) / oz::TM;
     M.ntn = (n + oz::TN - 1) / oz::TN;
     M.kc = (n + grid::GKC - 1) / grid::GKC;

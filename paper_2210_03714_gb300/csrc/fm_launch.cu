@@ -21,16 +21,21 @@ cudaError_t launch_persistent(bool cplx, int precision, int nb, const FmJob& J, 
 
 // Counting sort of the batch by d, largest first (longest jobs start first so
 // the persistent CTAs finish together).  Matrices with d outside [1, dmax] get
-// info = -4 and are left out of the queue.
-__global__ void fm_order_kernel(const int* __restrict__ d, int batch, int dmax, int* order,
-                                int* counter, int* info) {
+// info = -4 and are left out of the queue; matrices with d in [1, dmax] but
+// outside [lo, hi] belong to another part of a split batch and are left out
+// without a status.
+__global__ void fm_order_kernel(const int* __restrict__ d, int batch, int dmax, int lo, int hi,
+                                int* order, int* counter, int* info) {
   extern __shared__ int hist[];
   for (int i = threadIdx.x; i <= dmax; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   for (int b = threadIdx.x; b < batch; b += blockDim.x) {
     const int dd = d[b];
-    if (dd >= 1 && dd <= dmax) atomicAdd(&hist[dmax - dd], 1);
-    else if (info) info[b] = -4;
+    if (dd >= 1 && dd <= dmax) {
+      if (dd >= lo && dd <= hi) atomicAdd(&hist[dmax - dd], 1);
+    } else if (info) {
+      info[b] = -4;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -46,7 +51,7 @@ __global__ void fm_order_kernel(const int* __restrict__ d, int batch, int dmax, 
   __syncthreads();
   for (int b = threadIdx.x; b < batch; b += blockDim.x) {
     const int dd = d[b];
-    if (dd >= 1 && dd <= dmax) order[atomicAdd(&hist[dmax - dd], 1)] = b;
+    if (dd >= 1 && dd <= dmax && dd >= lo && dd <= hi) order[atomicAdd(&hist[dmax - dd], 1)] = b;
   }
 }
 
@@ -122,10 +127,29 @@ cudaError_t launch_select(bool cplx, const int* d, const int64_t* off, const voi
   return cudaGetLastError();
 }
 
-cudaError_t launch_order(const int* d, int batch, int dmax, int* order, int* counter, int* info,
-                         cudaStream_t st) {
-  fm_order_kernel<<<1, 1024, (size_t)(dmax + 1) * sizeof(int), st>>>(d, batch, dmax, order,
-                                                                       counter, info);
+// probe matrices for the autotuner: entries from a counter hash (SplitMix64),
+// uniform in [-1, 1), times scale
+__global__ void fm_probe_fill(double* A, long long count, unsigned long long seed, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    A[i] = scale * ((double)(z >> 11) * 0x1.0p-52 - 1.0);
+  }
+}
+
+cudaError_t launch_probe_fill(double* A, long long count, unsigned long long seed, double scale,
+                              cudaStream_t st) {
+  fm_probe_fill<<<1024, 256, 0, st>>>(A, count, seed, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const int* d, int batch, int dmax, int lo, int hi, int* order,
+                         int* counter, int* info, cudaStream_t st) {
+  fm_order_kernel<<<1, 1024, (size_t)(dmax + 1) * sizeof(int), st>>>(d, batch, dmax, lo, hi,
+                                                                       order, counter, info);
   return cudaGetLastError();
 }
 

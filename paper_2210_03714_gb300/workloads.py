@@ -146,3 +146,45 @@ def trid_dense(dl, dd, du, b):
     if d > 1:
         A += np.diag(dl[1:, b], -1) + np.diag(du[:-1, b], 1)
     return A
+
+
+def penta_batch(batch, d, eta=8.0, seed=6000, spread=0.1):
+    """A batch of pentadiagonal systems: the fourth-order central stencil of the
+    second derivative, (-1, 16, -30, 16, -1) / 12 (so exp(tA) decays as in a
+    diffusion step), each entry perturbed by a factor 1 + spread N(0,1)/2;
+    v_b = w / ||w||_2, w ~ N(0,1); t_b = eta / ||A_b||_1.  Returned as diags of
+    shape (5, d, batch), diags[j, k, b] = A_b[k][k + j - 2] (zero outside the
+    matrix), and v, t."""
+    g = _rng(seed)
+    h = spread / 2
+    stencil = np.array([-1.0, 16.0, -30.0, 16.0, -1.0]) / 12.0
+    diags = stencil[:, None, None] * (1.0 + h * g.standard_normal((5, d, batch)))
+    for j in range(5):
+        o = j - 2
+        for k in range(d):
+            if not 0 <= k + o < d:
+                diags[j, k, :] = 0.0
+    w = g.standard_normal((d, batch))
+    v = w / np.linalg.norm(w, axis=0)
+    col = np.zeros((d, batch))
+    for j in range(5):  # column k + o gets |A[k][k + o]|
+        o = j - 2
+        for k in range(d):
+            if 0 <= k + o < d:
+                col[k + o] += np.abs(diags[j, k])
+    t = eta / col.max(axis=0)
+    return diags, v, t
+
+
+def band_dense(diags, b):
+    """System b of a batch-interleaved banded batch (diags (2p+1, d, batch)) as a
+    dense matrix."""
+    q, d, _ = diags.shape
+    p = (q - 1) // 2
+    A = np.zeros((d, d))
+    for j in range(q):
+        o = j - p
+        for k in range(d):
+            if 0 <= k + o < d:
+                A[k, k + o] = diags[j, k, b]
+    return A
