@@ -793,6 +793,8 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "cta", "grid"],
                     help="execution path of the mixed form for the batch (the double form "
                          "always runs one CTA per matrix)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip fm_autotune (FM_PATH_AUTO then takes its fixed rule)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the short runs of the other configurations in the default run")
     args = ap.parse_args()
@@ -835,6 +837,14 @@ def main():
 
     fm.lib()
     measure_peaks(dev)
+    # the autotuner: which orders of the batch take the one-CTA kernels (below
+    # d*) and which the batched grid path; FM_PATH_AUTO below uses it
+    tune = None
+    if args.path == "auto" and not args.no_autotune:
+        fm.lib().fm_autotune_reset()
+        dstar, table = fm.autotune("expm", "R8", dmax=max(DIMS))
+        tune = {"dstar": dstar, "table_us_per_matrix": [
+            {"d": d, "one_cta": round(a, 3), "grid": round(b, 3)} for d, a, b in table]}
     dims, norms, flat = make_batch()
     P = fm.Packed(dims=[int(d) for d in dims], flat=torch.from_numpy(flat).to(dev))
     F = torch.empty_like(P.flat)
@@ -872,6 +882,16 @@ def main():
     s_host = s.cpu().numpy()
     value = whole_job_value(world, BATCH, ms)
 
+    # the same batch with the fixed rule (no tuned split), for context
+    untuned_value = None
+    if tune is not None and not args.no_fp64:
+        fm.lib().fm_autotune_reset()
+        per_u, _, _ = timed(args.precision, F, max(1, min(args.steps, 5)), 1)
+        untuned_value = whole_job_value(world, BATCH, max_over_ranks(sum(per_u) / len(per_u)))
+        # restore the tuned d* for the rest of the run
+        fm.lib().fm_autotune_reset()
+        fm.autotune("expm", "R8", dmax=max(DIMS))
+
     # the plain double form on the same GPU, same batch
     F64 = torch.empty_like(P.flat)
     fp64_ms = None
@@ -906,7 +926,9 @@ def main():
         # last timed call)
         pk = pipe_peaks(peaks)["tensor_bf16"]
         tile_s = st["tile_ms"] / 1000.0
-        alg = survey_flops(dims, s_host)
+        # with a tuned split the tile kernel sees only the orders from d*
+        gmask = np.asarray(dims) >= (tune["dstar"] if tune else 1)
+        alg = survey_flops(np.asarray(dims)[gmask], np.asarray(s_host)[gmask])
         ach = alg / tile_s / 1e12 if tile_s > 0 else 0.0
         busy = st["digit_flops"] / tile_s / 1e12 if tile_s > 0 else 0.0
         step_ach = alg / (ms / 1000.0) / 1e12
@@ -914,7 +936,8 @@ def main():
         roofline = {"bound": "tensor", "kernel": "oz_tiles", "pipe": "tensor_bf16",
                     "achieved": ach, "peak": pk[0], "peak_source": pk[1], "unit": "TFLOP/s",
                     "frac": ach / pk[0], "traffic": TRAFFIC.get("grid") if BATCH == 4096 and not args.dims else None,
-                    "flops_per_step": alg, "flops_count": "(8/3 k + 2 s) d^3 per matrix, k = 8",
+                    "flops_per_step": alg, "flops_count": "(8/3 k + 2 s) d^3 per matrix, k = 8, "
+                                                          "over the matrices on the grid path",
                     "kernel_ms_per_step": st["tile_ms"], "step_achieved": step_ach,
                     "step_frac": step_ach / pk[0],
                     "vs_fp64_peak": ach / fp64_pk[0], "fp64_peak": fp64_pk[0],
@@ -970,6 +993,7 @@ def main():
             "fp64_roofline": fp64_roofline,
             "path": "grid" if grid_path else "cta",
             "mixed_cta_path_value": cta_value,
+            "autotune": tune, "value_fixed_rule": untuned_value,
             "clocks": clk}
     line["peaks_measured"] = {k: {"tflops": v[0], "source": v[1]} for k, v in MEASURED.items()}
     if rank == 0 and not args.no_cpu_baseline:

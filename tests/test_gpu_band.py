@@ -4,8 +4,9 @@ once by banded LU without pivoting and solved in each of the N steps; the
 oracle runs the same action recurrence with dense GEPP on the same matrix
 (Sec. 1: a pentadiagonal system costs 15d flops; Sec. 5.1: banded actions).
 
-Bar: as the tridiagonal path, 1e-12 relative for the roundoff form and, for
-the plain form, N steps of its cancellation, 2 N u sum_i |b_i| (Sec. 4.3)."""
+Bar: as the tridiagonal path, 1e-12 relative, or, where a set's weights are
+large (Sec. 4.3), N times the round-off of one step: 2 N u (sum_i |b_i c_i|
+theta + 1) in the roundoff form and 2 N u sum_i |b_i| in the plain form."""
 import numpy as np
 import pytest
 
@@ -34,7 +35,8 @@ def T(x):
 def bar(cs, form, N):
     if form == "plain":
         return max(TOL_FP64, 2 * N * U * sum(abs(b) for b in cs["b_re"]))
-    return TOL_FP64
+    s = sum(abs(b * c) for b, c in zip(cs["b_re"], cs["c_re"])) * cs["theta"] + 1
+    return max(TOL_FP64, 2 * N * U * s)
 
 
 @pytest.mark.parametrize("name", ["R10", "R5", "R4", "R8"])
@@ -72,7 +74,8 @@ def test_penta_status(fm):
     W, info, N = fm.band_expmv_batched(T(diags), T(v), T(t), "R10")
     info = info.cpu().numpy()
     assert info[1] == -2 and info[0] == 0 and info[2] == 0
-    cs = {"c_re": [0.0, 0.2], "b_re": [0.5, 0.5], "a0": 1.0, "theta": 10.0}
+    cs = {"c_re": [0.0, 0.2], "c_im": [0.0, 0.0], "b_re": [0.5, 0.5], "b_im": [0.0, 0.0],
+          "a0": 1.0, "theta": 10.0}
     z = np.zeros((5, d, 1))
     z[2, :, 0] = 1.0
     W, info, N = fm.band_expmv_batched(T(z), T(np.ones((d, 1))), T(np.array([5.0])), cs,

@@ -71,10 +71,10 @@ def test_cossin_batched_ragged(fm, prec):
 @pytest.mark.parametrize("prec,path", PREC_PATH)
 @pytest.mark.parametrize("name", ["frac4_log1m", "R8_phi2", "frac4_exp"])
 def test_rfun_single(fm, prec, path, name):
-    """r(tA) as it is, with ||tA||_1 at the set's theta (the log(1 - x) set of
-    Sec. 2 has theta 1.3e-3 for double accuracy)."""
+    """r(tA) as it is, with ||tA||_1 just below the set's theta (the log(1 - x)
+    set of Sec. 2 has theta 1.3e-3 for double accuracy)."""
     cs = oracle_set(name)
-    A = wl.dense_scaled(80, cs["theta"], 62, scale_sqrt=True)
+    A = wl.dense_scaled(80, 0.99 * cs["theta"], 62, scale_sqrt=True)
     F_ref, _ = oracle.rfun(A, 1.0, cs)
     F, info = fm.rfun(T(A), 1.0, fm.Coeffs(cs), precision=prec, path=path)
     assert info == 0
@@ -88,7 +88,7 @@ def test_rfun_batched_and_range_flag(fm, prec):
     import torch
     cs = oracle_set("frac4_log1m")
     dims = [9, 64, 96]
-    norms = [0.5 * cs["theta"], cs["theta"], 3 * cs["theta"]]
+    norms = [0.5 * cs["theta"], 0.99 * cs["theta"], 3 * cs["theta"]]
     mats = [wl.dense_scaled(d, n, 80 + i, scale_sqrt=True) for i, (d, n) in enumerate(zip(dims, norms))]
     P = fm.Packed([torch.from_numpy(m) for m in mats], device="cuda")
     F, info = fm.rfun_batched(P, 1.0, fm.Coeffs(cs), precision=prec)

@@ -193,29 +193,31 @@ def _hermitian_golden():
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_hermitian_action_d4096_oracle_n4(fm, prec):
+def test_hermitian_action_d4096_oracle_n16(fm, prec):
     """The Hermitian action at full size (d = 4096, V 4096 x 256, the K-split
-    tile products and the 4096 x 256 block) with N = 4 steps against the
-    oracle's result on three columns (the action treats each column on its
+    tile products and the 4096 x 256 block) with N = 16 steps forced against
+    the oracle's result on three columns (the action treats each column on its
     own), per result at 1e-12."""
     A, V, rho, g = _hermitian_golden()
-    W, info, N = fm.expmv(T(A), T(V), 1.0, "R8", precision=prec, nsteps=4)
-    assert info == 0 and N == int(g["N_n4"]) == 4
+    W, info, N = fm.expmv(T(A), T(V), 1.0, "R8", precision=prec, nsteps=16)
+    assert info == 0 and N == int(g["N_n16"]) == 16
     W = W.cpu().numpy()[:, g["cols"]]
-    assert relerr(W, g["W_n4"]) <= TOL_FP64
     for j in range(len(g["cols"])):
-        assert relerr(W[:, j], g["W_n4"][:, j]) <= TOL_FP64
+        assert relerr(W[:, j], g["W_n16"][:, j]) <= TOL_FP64
 
 
 def test_hermitian_action_d4096(fm):
     """The Hermitian action at full size: A = -iH, d = 4096, V 4096 x 256,
     spectral radius 20 (anorm = 20 gives N = 206).  Checked against (1) the
-    oracle's N = 206 result on three columns, per column at 1e-12, for both
-    forms, (2) the mixed and the double grid forms agreeing at 1e-12 on every
-    column, (3) unitarity: every column keeps its norm to N u-level, (4) the
-    closed form Q exp(-i Lambda) Q^H V from a double eigendecomposition, within
-    its own rounding (d u ||H|| per entry of the decomposition, about 1e-12
-    relative here)."""
+    oracle's N = 206 result on three columns, per column, for both forms: N
+    steps carry N times the round-off of one (the roundoff form cancels
+    sum_i |b_i c_i| theta + 1 = 52 units per step, Sec. 4.3), and the oracle on
+    A and on P A P^T already differ by the stored spread (about 2e-12 at this
+    size); the bar is twice that spread; (2) the mixed and the double grid
+    forms agreeing at 1e-12 on every column, (3) unitarity: every column keeps
+    its norm to N u-level, (4) the closed form Q exp(-i Lambda) Q^H V from a
+    double eigendecomposition, within its own rounding (d u ||H|| per entry of
+    the decomposition, about 1e-12 relative here)."""
     import torch
     A, V, rho, g = _hermitian_golden()
     cs = fm.Coeffs("R8")
@@ -227,9 +229,10 @@ def test_hermitian_action_d4096(fm):
     assert info == 0 and N == N_ref
     Wm, Wd = Wm.cpu().numpy(), Wd.cpu().numpy()
     cols = g["cols"]
+    bar = max(TOL_FP64, 2.0 * float(g["spread_full"]))
     for W in (Wm, Wd):
         for j, c in enumerate(cols):
-            assert relerr(W[:, c], g["W_full"][:, j]) <= TOL_FP64
+            assert relerr(W[:, c], g["W_full"][:, j]) <= bar
     assert relerr(Wm, Wd) <= TOL_FP64
     nv = np.linalg.norm(V, axis=0)
     assert np.max(np.abs(np.linalg.norm(Wm, axis=0) - nv) / nv) <= 1e-12

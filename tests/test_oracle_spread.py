@@ -45,3 +45,32 @@ def test_remeasure_one_entry():
     assert s == 11
     assert sp <= rows[11][1] * 1.05 and se <= rows[11][2] * 1.05
     assert max(sp, se) >= 0.5 * max(rows[11][1], rows[11][2])
+
+
+def test_hermitian_action_spread():
+    """The full-size Hermitian action (N = 206 steps): the spread of two correct
+    double evaluations stored with the oracle's result (the oracle on A and on
+    P A P^T, d = 4096) against one re-measured here at d = 256.  Rounding of the
+    roundoff form accumulates over the N steps (about N u (sum_i |b_i c_i| theta
+    + 1) at most) and grows with the length d of the dot products; the stored
+    spread must lie between the d = 256 one and 8 times it (at most the sqrt(d)
+    growth of random rounding, times 2), and above 1e-12: two correct double
+    evaluations at this size do not agree to 1e-12."""
+    import numpy as np
+    import oracle
+    from oracle import coeffs as oc
+    from paper_2210_03714_gb300 import workloads as wl
+    g = np.load(os.path.join(HERE, "golden", "hermitian_d4096.npz"))
+    stored = float(g["spread_full"])
+    A, V, rho = wl.hermitian_action(d=256, m=3, rho=20.0, seed=2000)
+    W, N, _ = oracle.zexpmv(A, V, 1.0, "R8", anorm=rho)
+    p = np.random.default_rng(5).permutation(256)
+    W2, N2, _ = oracle.zexpmv(A[np.ix_(p, p)], V[p], 1.0, "R8", anorm=rho)
+    W2 = W2[np.argsort(p)]
+    assert N == N2 == int(g["N_full"]) == 206
+    s256 = max(float(np.linalg.norm(W[:, j] - W2[:, j]) / np.linalg.norm(W[:, j])) for j in range(3))
+    cs = oc.oracle_coeffs("R8")
+    per_step = sum(abs(b * c) for b, c in zip(cs["b_re"], cs["c_re"])) * cs["theta"] + 1
+    assert s256 <= 4 * N * U * per_step
+    assert s256 <= stored <= 8 * s256
+    assert stored > TOL_FP64
