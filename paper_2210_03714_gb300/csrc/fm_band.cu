@@ -86,18 +86,6 @@ __device__ __forceinline__ double aent(const BArgs& a, int k, int o, int b) {
   return __ldg(a.dg + ((size_t)(o + 2) * a.n + k) * a.batch + b);
 }
 
-// (B v)_k = h sum_o A[k][k + o] v_{k + o}, v read at stride batch
-__device__ __forceinline__ double bmul(const BArgs& a, int k, int b, double h, const double* v) {
-  double s = 0.0;
-#pragma unroll
-  for (int o = -2; o <= 2; ++o) {
-    const int c = k + o;
-    if (c < 0 || c >= a.n) continue;
-    s = fma(__dmul_rn(h, aent(a, k, o, b)), v[(size_t)c * a.batch + b], s);
-  }
-  return s;
-}
-
 __global__ void band_prep(BArgs a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.batch) return;
@@ -174,6 +162,16 @@ __global__ void band_prep(BArgs a) {
   if (a.nsteps) a.nsteps[b] = (int)N;
 }
 
+// row r of h A as its five diagonals (zero outside the matrix)
+__device__ __forceinline__ void load_row(const BArgs& a, int r, int b, double h, double* c) {
+#pragma unroll
+  for (int o = -2; o <= 2; ++o) c[o + 2] = (r < a.n) ? __dmul_rn(h, aent(a, r, o, b)) : 0.0;
+}
+
+// The N steps for KN nonzero nodes; one thread per system.  Sliding windows
+// keep v_{k-2..k+4}, the rows k..k+2 of h A and (B v)_{k-2..k+2} in registers
+// (B v of row k + 2 is formed at row k, so B^2 v of row k has its five
+// neighbours), and every factor is loaded one row ahead on the read-only path.
 template <int KN>
 __global__ void __launch_bounds__(kStepThreads) band_steps(BArgs a) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,62 +194,128 @@ __global__ void __launch_bounds__(kStepThreads) band_steps(BArgs a) {
   for (int q = 0; q < N; ++q) {
     const double* __restrict__ src = q == 0 ? a.V : (((N - q) & 1) == 0 ? a.W : a.sv);
     double* __restrict__ dst = (((N - 1 - q) & 1) == 0) ? a.W : a.sv;
-    double z1[KN], z2[KN];  // z_{k-1}, z_{k-2}
+    // windows: vw[i] = v_{k-2+i} (i = 0..6), c0/c1/c2 = rows k, k+1, k+2 of h A,
+    // bw[i] = (B v)_{k-2+i} (i = 0..4)
+    double vw[7], c0[5], c1[5], c2[5], bw[5];
 #pragma unroll
-    for (int j = 0; j < KN; ++j) z1[j] = z2[j] = 0.0;
-    // B v held for rows k-2 .. k+2 when B^2 v is needed
-    double bv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (a.need_b2)
-      for (int r = 0; r <= 2 && r < n; ++r) bv[2 + r] = bmul(a, r, b, h, src);
+    for (int i = 0; i < 7; ++i) {
+      const int r = i - 2;
+      vw[i] = (r >= 0 && r < n) ? src[(size_t)r * S + b] : 0.0;
+    }
+    bw[0] = bw[1] = bw[2] = bw[3] = bw[4] = 0.0;
+    if (a.need_bv) {
+      load_row(a, 0, b, h, c0);
+      load_row(a, 1, b, h, c1);
+      load_row(a, 2, b, h, c2);
+      // (B v)_0 and (B v)_1
+      double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+      for (int o = 0; o < 5; ++o) {
+        s0 = fma(c0[o], vw[o], s0);      // v_{0 + o - 2}
+        s1 = fma(c1[o], vw[o + 1], s1);  // v_{1 + o - 2}
+      }
+      bw[2] = s0;
+      bw[3] = n > 1 ? s1 : 0.0;
+    }
+    double z1[KN], z2[KN], l1n[KN], l2n[KN];
+#pragma unroll
+    for (int j = 0; j < KN; ++j) {
+      z1[j] = z2[j] = 0.0;
+      l1n[j] = l2n[j] = 0.0;  // row 0 has no multipliers
+    }
     for (int k = 0; k < n; ++k) {
       const size_t at = (size_t)k * S + b;
-      const double v0 = src[at];
-      double bk = 0.0;
-      if (a.need_b2) bk = bv[2];
-      else if (a.need_bv) bk = bmul(a, k, b, h, src);
-      double base = a.a0p * v0;
-      if (a.need_bv) base = fma(a.d1, bk, base);
-      if (a.need_b2) {
+      double l1c[KN], l2c[KN];
+#pragma unroll
+      for (int j = 0; j < KN; ++j) {
+        l1c[j] = l1n[j];
+        l2c[j] = l2n[j];
+      }
+      if (k + 1 < n) {
+#pragma unroll
+        for (int j = 0; j < KN; ++j) {
+          l1n[j] = __ldg(L1 + j * plane + at + S);
+          l2n[j] = __ldg(L2 + j * plane + at + S);
+        }
+      }
+      double bk = 0.0, b2k = 0.0;
+      if (a.need_bv) {
+        // (B v)_{k+2} from row k + 2 and v_{k..k+4}
         double s2 = 0.0;
 #pragma unroll
-        for (int o = -2; o <= 2; ++o) {
-          const int c = k + o;
-          if (c < 0 || c >= n) continue;
-          s2 = fma(__dmul_rn(h, aent(a, k, o, b)), bv[2 + o], s2);
+        for (int o = 0; o < 5; ++o) s2 = fma(c2[o], vw[o + 2], s2);
+        bw[4] = k + 2 < n ? s2 : 0.0;
+        bk = bw[2];
+        if (a.need_b2) {
+#pragma unroll
+          for (int o = 0; o < 5; ++o) b2k = fma(c0[o], bw[o], b2k);
         }
-        base = fma(a.d2, s2, base);
       }
+      const double v0 = vw[2];
+      double base = a.a0p * v0;
+      if (a.need_bv) base = fma(a.d1, bk, base);
+      if (a.need_b2) base = fma(a.d2, b2k, base);
       const double rhs = a.roundoff ? bk : v0;
 #pragma unroll
       for (int j = 0; j < KN; ++j) {
-        const size_t aj = j * plane + at;
-        double zk = rhs;
-        if (k >= 1) zk = fma(-__ldg(L1 + aj), z1[j], zk);
-        if (k >= 2) zk = fma(-__ldg(L2 + aj), z2[j], zk);
-        zs[aj] = zk;
+        const double zk = fma(-l2c[j], z2[j], fma(-l1c[j], z1[j], rhs));
+        zs[j * plane + at] = zk;
         z2[j] = z1[j];
         z1[j] = zk;
       }
       dst[at] = base;
-      if (a.need_b2) {
+      // slide the windows one row
 #pragma unroll
-        for (int r = 0; r < 4; ++r) bv[r] = bv[r + 1];
-        bv[4] = k + 3 < n ? bmul(a, k + 3, b, h, src) : 0.0;
+      for (int i = 0; i < 6; ++i) vw[i] = vw[i + 1];
+      vw[6] = k + 5 < n ? src[(size_t)(k + 5) * S + b] : 0.0;
+      if (a.need_bv) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) bw[i] = bw[i + 1];
+#pragma unroll
+        for (int o = 0; o < 5; ++o) {
+          c0[o] = c1[o];
+          c1[o] = c2[o];
+        }
+        load_row(a, k + 3, b, h, c2);
       }
     }
-    // backward sweep and the combination
-    double y1[KN], y2[KN];  // y_{k+1}, y_{k+2}
+    // backward sweep and the combination; row k - 1 loaded ahead
+    double y1[KN], y2[KN], zn[KN], in[KN], g1n[KN], g2n[KN];
+    {
+      const size_t at = (size_t)(n - 1) * S + b;
 #pragma unroll
-    for (int j = 0; j < KN; ++j) y1[j] = y2[j] = 0.0;
+      for (int j = 0; j < KN; ++j) {
+        y1[j] = y2[j] = 0.0;
+        zn[j] = zs[j * plane + at];
+        in[j] = __ldg(IB + j * plane + at);
+        g1n[j] = __ldg(G1 + j * plane + at);
+        g2n[j] = __ldg(G2 + j * plane + at);
+      }
+    }
     for (int k = n - 1; k >= 0; --k) {
       const size_t at = (size_t)k * S + b;
+      double zc[KN], ic[KN], g1c[KN], g2c[KN];
+#pragma unroll
+      for (int j = 0; j < KN; ++j) {
+        zc[j] = zn[j];
+        ic[j] = in[j];
+        g1c[j] = g1n[j];
+        g2c[j] = g2n[j];
+      }
+      if (k > 0) {
+        const size_t an = at - S;
+#pragma unroll
+        for (int j = 0; j < KN; ++j) {
+          zn[j] = zs[j * plane + an];
+          in[j] = __ldg(IB + j * plane + an);
+          g1n[j] = __ldg(G1 + j * plane + an);
+          g2n[j] = __ldg(G2 + j * plane + an);
+        }
+      }
       double acc = dst[at];
 #pragma unroll
       for (int j = 0; j < KN; ++j) {
-        const size_t aj = j * plane + at;
-        double yk = zs[aj] * __ldg(IB + aj);
-        yk = fma(-__ldg(G1 + aj), y1[j], yk);
-        yk = fma(-__ldg(G2 + aj), y2[j], yk);
+        const double yk = fma(-g2c[j], y2[j], fma(-g1c[j], y1[j], zc[j] * ic[j]));
         y2[j] = y1[j];
         y1[j] = yk;
         acc = fma(cw[j], yk, acc);
