@@ -221,6 +221,20 @@ def roofline_of(work, ms, peaks):
             "frac": b["frac"], "traffic": None, "pipes": pipes}
 
 
+def oracle_leg(fn, unit, sample):
+    """The CPU baseline leg of a configuration line: the oracle as it stands,
+    timed on a bounded sample (fn runs it and returns its result).  Returns
+    (result, cpu_baseline object); the result also serves the line's error
+    against the oracle."""
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    res = fn(oracle)
+    dt = time.perf_counter() - t0
+    return res, {"value": 1.0 / dt, "unit": unit, "cores": oracle.num_threads(),
+                 "kind": "oracle", "sample": sample}
+
+
 def cpu_baseline(dims, norms, sample, gpu_F=None, P=None):
     """The oracle (plain C, FP64, OpenMP over matrices) on a bounded sample."""
     import numpy as np
@@ -354,18 +368,19 @@ def run_single(args, emit=True):
     # against the oracle: the stored full-size result (three columns) for the
     # Hermitian action, one matrix for the diffusion batch, one for dense exp
     err_oracle = None
-    if not args.no_cpu_baseline:
-        import oracle
-        if args.workload == "hermitian":
-            gpath = os.path.join(ROOT, "tests", "golden", "hermitian_d4096.npz")
-            if os.path.exists(gpath):
-                g = np.load(gpath)
-                Wc = out.cpu().numpy()[:, g["cols"]]
-                err_oracle = float(np.linalg.norm(Wc - g["W_full"]) / np.linalg.norm(g["W_full"]))
-        elif args.workload == "diffusion":
-            Pref, _, _, _ = oracle.phi1(mats[0], ts[0], "R8", "R8_phi1")
-            got = Pd.get(out, 0).cpu().numpy()
-            err_oracle = float(np.linalg.norm(got - Pref) / np.linalg.norm(Pref))
+    cpu = None
+    if args.workload == "hermitian":
+        # the oracle's stored result (tests/golden, written by the oracle alone)
+        gpath = os.path.join(ROOT, "tests", "golden", "hermitian_d4096.npz")
+        if os.path.exists(gpath):
+            g = np.load(gpath)
+            Wc = out.cpu().numpy()[:, g["cols"]]
+            err_oracle = float(np.linalg.norm(Wc - g["W_full"]) / np.linalg.norm(g["W_full"]))
+    elif args.workload == "diffusion" and not args.no_cpu_baseline:
+        res, cpu = oracle_leg(lambda o: o.phi1(mats[0], ts[0], "R8", "R8_phi1"), "evals/s",
+                              "1 matrix of the batch (phi_1 and exp)")
+        got = Pd.get(out, 0).cpu().numpy()
+        err_oracle = float(np.linalg.norm(got - res[0]) / np.linalg.norm(res[0]))
     diff = None
     fp64_ms = None
     if not args.no_fp64 and args.precision == "mixed":
@@ -389,7 +404,7 @@ def run_single(args, emit=True):
                                              "l2": "working set > L2"},
             "roofline": roofline, "products": st["products"],
             "corrections": st["corrections"], "fp64_ms": fp64_ms,
-            "rel_err_vs_oracle": err_oracle,
+            "rel_err_vs_oracle": err_oracle, "cpu_baseline": cpu,
             "rel_diff_vs_fp64": diff, "clocks": clk}
     if rank == 0 and emit:
         print(json.dumps(line), flush=True)
@@ -403,7 +418,6 @@ def run_trid(args, emit=True):
     ||t A||_1 = 8 (N = 36 steps).  One step is one fm_trid_expmv_batched call."""
     import numpy as np
     import torch
-    import oracle
     import paper_2210_03714_gb300 as fm
     from paper_2210_03714_gb300 import workloads as wl
     rank = int(os.environ.get("RANK", "0"))
@@ -479,11 +493,15 @@ def run_trid(args, emit=True):
                 "note": "whole call (the factorization launch included); fp64: the paper's "
                         "flop count, peak derived from unit counts; hbm: the kernel's design "
                         "traffic over the measured copy bandwidth"}
-    # one sampled system against the oracle (dense LU of the same matrix)
-    Wh = W[:, 7].cpu().numpy()
-    ref, Nr, _ = oracle.expmv(dense_of(7), v[:, 7], t[7], "R10",
-                              oracle.PLAIN if form == "plain" else oracle.ROUNDOFF)
-    err = float(np.linalg.norm(Wh - ref) / np.linalg.norm(ref))
+    # the CPU baseline leg: one sampled system by the oracle (dense LU of the
+    # same matrix), timed, and the GPU's result for it against the oracle's
+    err, cpu = None, None
+    if not args.no_cpu_baseline:
+        Wh = W[:, 7].cpu().numpy()
+        res, cpu = oracle_leg(lambda o: o.expmv(dense_of(7), v[:, 7], t[7], "R10",
+                                                o.PLAIN if form == "plain" else o.ROUNDOFF),
+                              "systems/s", "1 system of the batch (dense LU of the same matrix)")
+        err = float(np.linalg.norm(Wh - res[0]) / np.linalg.norm(res[0]))
     # end to end with host buffers: inputs in, result and status out, per step
     pins = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in host_in]
     W_host = torch.empty((d, batch), dtype=torch.float64).pin_memory()
@@ -505,14 +523,6 @@ def run_trid(args, emit=True):
     e2e = {"value": batch / (e2e_ms / 1000.0), "unit": "systems/s",
            "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in pins)),
            "d2h_bytes_per_step": int(W_host.numel() * 8 + info_host.numel() * 4)}
-    cpu = None
-    if not args.no_cpu_baseline:
-        t0 = time.perf_counter()
-        oracle.expmv(dense_of(8), v[:, 8], t[8], "R10",
-                     oracle.PLAIN if form == "plain" else oracle.ROUNDOFF)
-        cs_ = time.perf_counter() - t0
-        cpu = {"value": 1.0 / cs_, "unit": "systems/s", "cores": oracle.num_threads(),
-               "kind": "oracle", "sample": "1 system of the batch (dense LU of the same matrix)"}
     kind_name = "pentadiagonal" if penta else "tridiagonal"
     line = {"metric": "%s action evals/sec (systems/s) at <=1e-12 rel err" % kind_name,
             "value": batch / sec, "unit": "systems/s", "n_gpus": 1, "steps": args.steps,
@@ -535,10 +545,12 @@ def run_trid(args, emit=True):
 
 
 def run_small(args, emit=True):
-    """The two latency-bound configurations on the one-CTA kernels: exp of one
-    real d = 64 matrix (N(0,1) scaled to ||A||_1 = 2, R4, s = 10), and the
-    gradient batch (256 matrices of order 128, N(0,1)/sqrt(d), R8 action with
-    N from each matrix's norm, forward and adjoint in one call)."""
+    """The two latency-bound configurations: exp of one real d = 64 matrix in
+    double (N(0,1) scaled to ||A||_1 = 2, R4, s = 10) on the team path (one
+    cooperative launch over many SMs; the one-CTA kernel's time is reported
+    beside it), and the gradient batch on the one-CTA kernels (256 matrices of
+    order 128, N(0,1)/sqrt(d), R8 action with N from each matrix's norm,
+    forward and adjoint in one call)."""
     import numpy as np
     import torch
     import paper_2210_03714_gb300 as fm
@@ -554,7 +566,7 @@ def run_small(args, emit=True):
         cs = fm.Coeffs("R4")
         call = lambda prec: fm.expm(Ad, 1.0, cs, precision=prec, status=False)
         units, d = 1, 64
-        metric = "exp of one d=64 matrix, evals/sec at <=1e-12 rel err (one CTA)"
+        metric = "exp of one d=64 matrix, evals/sec at <=1e-12 rel err (plain FP64)"
         workload = "exp(A): one real d=64 matrix, N(0,1) scaled to ||A||_1 = 2, R4 (s = 10)"
     else:
         A, v, y = wl.grad_batch(batch=256)
@@ -571,7 +583,7 @@ def run_small(args, emit=True):
         workload = ("d/dA, d/dv of <wbar, r(B)^N v>: 256 matrices of order 128, N(0,1)/sqrt(d), "
                     "R8, N = ceil(||A||_1/theta) per matrix (mean %.0f)" % np.mean(Ns))
     stream = torch.cuda.current_stream()
-    prec = args.precision if args.workload == "single" else "fp64"
+    prec = "fp64"  # the plain method in double (config 0) and the FP64 adjoint
     for _ in range(args.warmup):
         out = call(prec)
     torch.cuda.synchronize()
@@ -587,18 +599,32 @@ def run_small(args, emit=True):
     ms = e0.elapsed_time(e1) / args.steps
     extra = {}
     if args.workload == "single":
-        _, _, s = fm.expm(Ad, 1.0, cs, precision=prec)
+        F, _, s = fm.expm(Ad, 1.0, cs, precision=prec)
         # B^2, the two +-c pairs of R4 (one LU and a d-column solve each), s squarings
         flops = (2.0 + 2 * 8.0 / 3.0) * d ** 3 + 2.0 * s * d ** 3
-        sm_peak = fp64_peak / 152
         ach = flops / (ms / 1000.0) / 1e12
-        roofline = {"bound": "latency", "pipe": "fp64", "achieved": ach, "peak": sm_peak,
-                    "unit": "TFLOP/s", "frac": ach / sm_peak, "traffic": None,
-                    "note": "one CTA on one SM: the paper's flop count over one SM's derived "
-                            "FP64 rate (1/152 of the GPU's)"}
-        if prec == "mixed":
-            ref = fm.expm(Ad, 1.0, cs, precision="fp64")[0]
-            extra["rel_diff_vs_fp64"] = float(((out - ref).norm() / ref.norm()).item())
+        roofline = {"bound": "latency", "pipe": "fp64", "achieved": ach, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+                    "note": "the paper's flop count over the GPU's measured FP64 peak; the "
+                            "path is a chain of about 14 grid-wide barriers (B^2, two "
+                            "factorizations on two blocks, the solves, 10 squarings) on a "
+                            "d = 64 problem: latency-bound"}
+        # the same call on one thread block (the one-CTA kernel), for context
+        for _ in range(2):
+            fm.expm(Ad, 1.0, cs, precision=prec, path="cta", status=False)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            fm.expm(Ad, 1.0, cs, precision=prec, path="cta", status=False)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        extra["one_cta_ms"] = c0.elapsed_time(c1) / args.steps
+        if not args.no_cpu_baseline:
+            res, extra["cpu_baseline"] = oracle_leg(lambda o: o.expm(A, 1.0, "R4"), "evals/s",
+                                                    "the matrix itself")
+            extra["rel_err_vs_oracle"] = float(np.linalg.norm(F.cpu().numpy() - res[0]) /
+                                               np.linalg.norm(res[0]))
         extra["s"] = s
     else:
         Nv = np.array(Ns, dtype=np.float64)
@@ -618,7 +644,8 @@ def run_small(args, emit=True):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "replicas", "vs_baseline": None,
             "dtype": ("f32+f64" if prec == "mixed" else "f64"), "data": "synthetic",
-            "config": {"workload": workload, "precision": prec, "path": "one-CTA",
+            "config": {"workload": workload, "precision": prec,
+                       "path": "team" if args.workload == "single" else "one-CTA",
                        "l2": "working set within L2 (latency-bound)"},
             "roofline": roofline, "clocks": clk}
     line.update(extra)

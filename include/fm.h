@@ -40,8 +40,9 @@
  *                out; its outputs are not written)
  *        -5      fm_rfun: ||tA||_1 > theta, outside the accuracy range of the
  *                set (the result is still computed)
- *        -7      a bounded wait inside a tensor-core kernel ran out (the
- *                kernel stopped early; the results of the call are invalid)
+ *        -7      a bounded wait inside a tensor-core kernel or at a grid-wide
+ *                barrier of the team path ran out (the kernel stopped early;
+ *                the results of the call are invalid)
  *  - Outputs must not alias inputs.
  *  - Scratch: opts.workspace (device, opts.workspace_bytes >= fm_workspace_size)
  *    or, when NULL, a buffer the library keeps per (device, stream): calls on
@@ -161,7 +162,7 @@ fm_status fm_theta(const fm_coeffs* cs, int func, double tol, double* theta_out)
  *              steps; info = -1 if it does not converge); opts.max_ir_iters
  *              and opts.ir_tol are not used.
  *  FM_MIXED    FM_FP32_IR on the one-CTA kernels, FM_BF16_IR on the grid
- *              paths (the default). */
+ *              paths, double on the team path (the default). */
 enum { FM_FP64 = 0, FM_FP32_IR = 1, FM_BF16_IR = 2, FM_MIXED = 3 };
 enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       */
 /* Execution path.  FM_PATH_CTA: one thread block per matrix, every step in it
@@ -179,14 +180,23 @@ enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       
  * The action forms the matrix r(B) once and applies it N times.  Calls on
  * this path synchronize their stream (s or N, the batch orders and the
  * iteration counts are read on the host).
+ * FM_PATH_TEAM: single-matrix exp (fm_expm, fm_zexpm, fm_rfun) of order
+ * d <= 512 in double (FM_FP64 or FM_MIXED): one cooperative launch whose thread
+ * blocks share every step -- the shifted systems are factored on separate
+ * blocks at once (Sec. 2: one processor per system), their d right-hand-side
+ * columns solved in column blocks across the grid, and B^2 and each squaring
+ * computed as 8 x 8 output tiles over all blocks; grid-wide barriers (bounded
+ * waits: info -7 when one runs out) separate the steps.  The call
+ * synchronizes its stream to read the status.
  * FM_PATH_AUTO: FM_BF16_IR calls, single-matrix calls with d > fm_max_dim(),
  * and batched exp, phi_1, phi_1 V and cos/sin in FM_MIXED with dmax >= 64 take
- * the grid path; everything else the one-CTA kernels.  After fm_autotune (or
+ * the grid path; single-matrix exp with d <= 512 in FM_FP64 or FM_MIXED the
+ * team path; everything else the one-CTA kernels.  After fm_autotune (or
  * with its FM_TUNE_CACHE), batched matrix functions in FM_MIXED are split at
  * the measured order d* instead.  A precision value and a path
  * that do not go together (FM_FP32_IR with FM_PATH_GRID, FM_BF16_IR with
  * FM_PATH_CTA, a batched action on the grid path) give FM_EINVAL. */
-enum { FM_PATH_AUTO = 0, FM_PATH_CTA = 1, FM_PATH_GRID = 2 };
+enum { FM_PATH_AUTO = 0, FM_PATH_CTA = 1, FM_PATH_GRID = 2, FM_PATH_TEAM = 3 };
 
 typedef struct {
   int precision;      /* FM_FP64, FM_FP32_IR, FM_BF16_IR or FM_MIXED (above)    */
@@ -200,7 +210,7 @@ typedef struct {
   long nsteps;        /* > 0: force N for actions (default 0)                   */
   void* workspace;    /* device scratch or NULL                                 */
   size_t workspace_bytes;
-  int path;           /* FM_PATH_AUTO (default), FM_PATH_CTA or FM_PATH_GRID     */
+  int path;           /* FM_PATH_AUTO (default), _CTA, _GRID or _TEAM            */
 } fm_opts;
 
 /* Defaults: FM_MIXED, FM_ROUNDOFF, 2 refinement steps, ir_tol 1e-8, automatic

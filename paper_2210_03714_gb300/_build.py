@@ -12,7 +12,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libfm.so")
 
 CU = ["fm_api.cu", "fm_launch.cu", "fm_inst_real.cu", "fm_inst_cplx.cu", "fm_grid.cu", "fm_bgrid.cu",
-      "fm_trid.cu", "fm_band.cu"]
+      "fm_trid.cu", "fm_band.cu", "fm_team.cu"]
 CPP = ["fm_coeffs.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC]

@@ -165,6 +165,6 @@ def default_opts(**kw):
         if k == "form" and isinstance(v, str):
             v = {"roundoff": FM_ROUNDOFF, "plain": FM_PLAIN}[v]
         if k == "path" and isinstance(v, str):
-            v = {"auto": 0, "cta": 1, "grid": 2}[v]
+            v = {"auto": 0, "cta": 1, "grid": 2, "team": 3}[v]
         setattr(o, k, v)
     return o

@@ -18,6 +18,7 @@
 #include "fm_band.h"
 #include "fm_bgrid.h"
 #include "fm_grid.h"
+#include "fm_team.h"
 #include "fm_job.h"
 #include "fm_launch.h"
 #include "fm_trid.h"
@@ -216,7 +217,7 @@ fm_status check_opts(const fm_opts& o) {
   if (!(o.ir_tol >= 0) || !isfinite(o.anorm) || o.anorm < 0) return fail(FM_EINVAL, "opts.ir_tol / opts.anorm");
   if (o.s_fixed > 1000 || o.s_fixed < kSRfun) return fail(FM_EINVAL, "opts.s_fixed");
   if (o.nsteps < 0) return fail(FM_EINVAL, "opts.nsteps");
-  if (o.path < FM_PATH_AUTO || o.path > FM_PATH_GRID) return fail(FM_EINVAL, "opts.path");
+  if (o.path < FM_PATH_AUTO || o.path > FM_PATH_TEAM) return fail(FM_EINVAL, "opts.path");
   return FM_OK;
 }
 
@@ -262,13 +263,29 @@ Plan make_plan(int kind, bool cplx, int precision, int batch, int dmax, int m, i
 // Which kernels run a call.  FM_FP64 runs anywhere; FM_FP32_IR (single
 // factors + refinement) only on the one-CTA kernels; FM_BF16_IR (tensor-core
 // digit products in the correction iteration) only on the grid paths;
-// FM_MIXED picks by path.  The batched grid path takes exp, phi_1 and phi_1 V.
-enum Route { R_CTA = 0, R_GRID = 1, R_BGRID = 2, R_BAD = -1 };
+// FM_MIXED picks by path (double on the team kernel).  The batched grid path
+// takes exp, phi_1 and phi_1 V; the team kernel single-matrix exp.
+enum Route { R_CTA = 0, R_GRID = 1, R_BGRID = 2, R_TEAM = 3, R_BAD = -1 };
 
 Route route(int kind, bool single, int dmax, int precision, int path, const char** why) {
   const bool bg_kind = kind == JOB_EXPM || kind == JOB_PHI1 || kind == JOB_PHI1MV || kind == JOB_TRIG;
   *why = "";
   if (kind == JOB_ADJ) return R_CTA;
+  if (path == FM_PATH_TEAM) {
+    if (!single || kind != JOB_EXPM) {
+      *why = "FM_PATH_TEAM takes single-matrix exp (fm_expm, fm_zexpm, fm_rfun) only";
+      return R_BAD;
+    }
+    if (precision == FM_FP32_IR || precision == FM_BF16_IR) {
+      *why = "FM_PATH_TEAM computes in double: FM_FP64 or FM_MIXED";
+      return R_BAD;
+    }
+    if (dmax > kTeamMaxDim) {
+      *why = "FM_PATH_TEAM takes d <= 512";
+      return R_BAD;
+    }
+    return R_TEAM;
+  }
   if (precision == FM_FP32_IR && path == FM_PATH_GRID) {
     *why = "FM_FP32_IR runs on the one-CTA kernels; the grid paths take FM_FP64, FM_BF16_IR or FM_MIXED";
     return R_BAD;
@@ -280,6 +297,10 @@ Route route(int kind, bool single, int dmax, int precision, int path, const char
   const bool want_grid = path == FM_PATH_GRID || precision == FM_BF16_IR;
   if (single) {
     if (want_grid) return R_GRID;
+    // one small matrix: every step spread over many SMs beats one block
+    if (path == FM_PATH_AUTO && kind == JOB_EXPM && dmax <= kTeamMaxDim &&
+        (precision == FM_FP64 || precision == FM_MIXED))
+      return R_TEAM;
     if (path == FM_PATH_AUTO && dmax > fm_max_dim()) {
       if (precision == FM_FP32_IR) {
         *why = "FM_FP32_IR runs on the one-CTA kernels (d <= fm_max_dim())";
@@ -525,6 +546,38 @@ int tuned_dstar(int kind) {
 
 fm_status run_cta(const Call& c, fm_opts o, cudaStream_t st);
 
+// one small matrix over many SMs (fm_team.cu)
+fm_status run_team(const Call& c, const fm_opts& o, cudaStream_t st) {
+  const int n = c.d1;
+  if (n < 1 || n > kTeamMaxDim) return fail(FM_ESHAPE, "d must be in [1, 512] on FM_PATH_TEAM");
+  if (!c.A) return fail(FM_EINVAL, "A is NULL");
+  if (!c.F) return fail(FM_EINVAL, "output is NULL");
+  if (c.lda < n || c.ldf < n) return fail(FM_ESHAPE, "leading dimension smaller than the row length");
+  TeamJob j;
+  memset(&j, 0, sizeof j);
+  fm_status s = pack(c.ce, c.cp, c.cplx, o.form, j.cf);
+  if (s) return s;
+  j.cplx = c.cplx;
+  j.form = o.form;
+  j.n = n;
+  j.A = c.A;
+  j.lda = c.lda;
+  j.t = c.t1;
+  j.F = c.F;
+  j.ldf = c.ldf;
+  j.anorm = o.anorm;
+  j.s_fixed = o.s_fixed;
+  j.st = st;
+  j.info_host = c.info_host;
+  j.s_host = c.s_host;
+  j.ws_bytes = team_ws_bytes(c.cplx, n, team_systems(j.cf, o.form));
+  std::unique_lock<std::mutex> hold;  // the scratch stays ours until the work is done
+  s = get_scratch(j.ws_bytes, &o, &j.ws, st, &hold);
+  if (s) return s;
+  g_stats.launches = 1;
+  return (fm_status)team_run(j, g_err, sizeof g_err);
+}
+
 fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   memset(&g_stats, 0, sizeof g_stats);
   fm_opts o = resolve_opts(optsp);
@@ -555,6 +608,7 @@ fm_status run(const Call& c, const fm_opts* optsp, cudaStream_t st) {
   }
   if (r == R_BGRID) return run_bgrid(c, o, st);
   if (r == R_GRID && c.dmax >= 1) return run_grid(c, o, st);
+  if (r == R_TEAM) return run_team(c, o, st);
   return run_cta(c, o, st);
 }
 
@@ -703,6 +757,7 @@ size_t fm_workspace_size(int job, int batch, int dmax, int m, int k, const fm_op
   const int prec = o.precision == FM_FP64 ? 0 : 1;
   if (r == R_BAD) return 0;
   if (r == R_GRID) return grid_ws_bytes(kind, cplx, prec, dmax, m);
+  if (r == R_TEAM) return team_ws_bytes(cplx, dmax, k);
   if (r == R_BGRID) {
     if (dmax > fm_max_dim()) return 0;
     std::vector<int> d(batch, dmax);

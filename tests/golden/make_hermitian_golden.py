@@ -10,17 +10,21 @@ own, so the oracle runs on the stored columns only.  Three runs:
   - N = 16 forced (a short chain; spectral radius 20/16 of B keeps the shifted
     systems well inside the region where the grid path's correction
     iteration converges);
-  - N = 206 on the permuted copy P A P^T (and P V): exp(P A P^T) P V = P exp(A) V,
-    so mapping it back gives a second correct double evaluation that rounds
-    in another order; the largest relative distance per column between the
-    two is stored as the spread of two correct double evaluations.
+  - both again on the permuted copy P A P^T (and P V): r(P B P^T)^N P V =
+    P r(B)^N V, so mapping it back gives a second correct double evaluation
+    that rounds in another order; the largest relative distance per column
+    between the two is stored as the spread of two correct double
+    evaluations (spread_full, spread_n16).  At N = 16 the step matrix B has
+    spectral radius 1.25, far outside the set's theta, so r(B) is not close
+    to exp(B) and its shifted systems are less well conditioned: its spread
+    is larger than at N = 206.
 
 Only oracle/ and the seeded input generator are called.  The result also
 records the scale that gives H spectral radius 20 (so a test rebuilds A bit
 for bit without an eigenvalue routine, whose last bits differ between
 machines) and checks of the inputs (Frobenius norm of A, the selected columns
 of V).  Run from the repository root: python tests/golden/make_hermitian_golden.py
-(about fifteen minutes of CPU per run; the three run in parallel processes)."""
+(about fifteen minutes of CPU per run; the four run in parallel processes)."""
 import multiprocessing as mp
 import os
 import sys
@@ -63,22 +67,24 @@ def main():
     scale = wl.hermitian_scale(H, RHO)
     del H
     ctx = mp.get_context("spawn")
-    with ctx.Pool(3) as pool:
-        res = pool.map(_run, [(0, scale, False), (16, scale, False), (0, scale, True)])
+    with ctx.Pool(4) as pool:
+        res = pool.map(_run, [(0, scale, False), (16, scale, False), (0, scale, True),
+                              (16, scale, True)])
     out = {"cols": np.array(COLS), "seed": SEED, "d": D, "m": M, "rho": RHO, "scale": scale}
-    perm = None
+    perm = {}
     for nsteps, permute, W, N, anorm_f, Vc in res:
-        if permute:
-            perm = W
-            continue
         key = "full" if nsteps == 0 else "n16"
+        if permute:
+            perm[key] = W
+            continue
         out["W_" + key] = W
         out["N_" + key] = N
         out["A_fro"] = anorm_f
         out["V_cols"] = Vc
-    W = out["W_full"]
-    out["spread_full"] = max(float(np.linalg.norm(W[:, j] - perm[:, j]) / np.linalg.norm(W[:, j]))
-                             for j in range(len(COLS)))
+    for key in ("full", "n16"):
+        W, Wp = out["W_" + key], perm[key]
+        out["spread_" + key] = max(float(np.linalg.norm(W[:, j] - Wp[:, j]) / np.linalg.norm(W[:, j]))
+                                   for j in range(len(COLS)))
     np.savez(OUT, **out)
     print("wrote", OUT, {k: np.shape(v) for k, v in out.items()})
 

@@ -138,6 +138,24 @@ def test_precision_and_path_routing():
     st = L.fm_expmv_batched(C.byref(cs), 4, 16, fake, fake, fake, fake, 1, fake, fake, fake, fake,
                             None, C.byref(o), None)
     assert st == _ffi.FM_EINVAL
+    # the team path: single-matrix exp in double, d <= 512
+    for prec, d in ((_ffi.FM_FP32_IR, 64), (_ffi.FM_BF16_IR, 64), (_ffi.FM_FP64, 513)):
+        o = _ffi.default_opts(precision=prec, path="team")
+        st = L.fm_expm(C.byref(cs), d, fake, d, 1.0, fake, d, C.byref(o), None, None, None)
+        assert st == _ffi.FM_EINVAL, (prec, d)
+    o = _ffi.default_opts(path="team")
+    st = L.fm_phi1(C.byref(cs), C.byref(cs), 64, fake, 64, 1.0, fake, 64, None, 64, C.byref(o),
+                   None, None, None)
+    assert st == _ffi.FM_EINVAL
+    st = L.fm_expm_batched(C.byref(cs), 4, 16, fake, fake, fake, fake, fake, fake, None,
+                           C.byref(o), None)
+    assert st == _ffi.FM_EINVAL
+    o = _ffi.default_opts()
+    o.path = 4
+    st = L.fm_expm(C.byref(cs), 64, fake, 64, 1.0, fake, 64, C.byref(o), None, None, None)
+    assert st == _ffi.FM_EINVAL
+    assert L.fm_workspace_size(0, 1, 512, 0, 9, C.byref(_ffi.default_opts(path="team"))) > 0
+    assert L.fm_workspace_size(0, 1, 513, 0, 9, C.byref(_ffi.default_opts(path="team"))) == 0
     # workspace sizes follow the same routes
     assert L.fm_workspace_size(0, 1, 64, 0, 9, C.byref(_ffi.default_opts(precision="bf16_ir"))) > 0
     assert L.fm_workspace_size(2, 8, 64, 1, 9, C.byref(_ffi.default_opts(precision="bf16_ir"))) == 0

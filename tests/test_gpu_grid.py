@@ -197,13 +197,18 @@ def test_hermitian_action_d4096_oracle_n16(fm, prec):
     """The Hermitian action at full size (d = 4096, V 4096 x 256, the K-split
     tile products and the 4096 x 256 block) with N = 16 steps forced against
     the oracle's result on three columns (the action treats each column on its
-    own), per result at 1e-12."""
+    own), per column.  At N = 16 the step matrix has spectral radius 1.25, far
+    outside the set's theta: r(B) is then not exp(B), and the shifted systems
+    are less well conditioned, so two correct double evaluations (the oracle
+    on A and on P A P^T) differ by the stored spread; the bar is twice that
+    spread."""
     A, V, rho, g = _hermitian_golden()
     W, info, N = fm.expmv(T(A), T(V), 1.0, "R8", precision=prec, nsteps=16)
     assert info == 0 and N == int(g["N_n16"]) == 16
     W = W.cpu().numpy()[:, g["cols"]]
+    bar = max(TOL_FP64, 2.0 * float(g["spread_n16"]))
     for j in range(len(g["cols"])):
-        assert relerr(W[:, j], g["W_n16"][:, j]) <= TOL_FP64
+        assert relerr(W[:, j], g["W_n16"][:, j]) <= bar
 
 
 def test_hermitian_action_d4096(fm):

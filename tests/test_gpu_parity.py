@@ -341,9 +341,10 @@ def test_status_codes(fm):
     A = np.diag([7.5, 0.1, 0.2])
     _, info, _ = fm.expm(T(A), 1.0, "R8", anorm=1e-3, precision="fp64")
     assert info == 3 * 3 + 1
-    # refinement switched off with a tolerance set: flagged as not converged
+    # single-precision factors with refinement switched off and a tolerance
+    # set: flagged as not converged
     A = wl.dense_scaled(20, 2.0, 3)
-    _, info, _ = fm.expm(T(A), 1.0, "R8", precision="mixed", max_ir_iters=0, ir_tol=1e-12)
+    _, info, _ = fm.expm(T(A), 1.0, "R8", precision="fp32_ir", max_ir_iters=0, ir_tol=1e-12)
     assert info == -1
     # d = 1: the scalar approximant, against the oracle and exp within the
     # round-off bound of the roundoff form: 2^s times (sum_i |b_i c_i| theta + 1) u
