@@ -762,7 +762,7 @@ def other_configs(args):
     out = {}
     keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config",
             "roofline", "rel_err_vs_oracle", "rel_diff_vs_fp64", "rel_err_vs_oracle_sample",
-            "e2e", "cpu_baseline", "clocks", "s", "status_nonzero")
+            "e2e", "cpu_baseline", "clocks", "s", "status_nonzero", "one_cta_ms")
     plan = (("single_d64_R4", "single", run_small, dict(steps=10, warmup=3)),
             ("gradient_256x128", "adjoint", run_small, dict(steps=3, warmup=1)),
             ("hermitian_action_d4096", "hermitian", run_single, dict(steps=2, warmup=1)),

@@ -187,7 +187,7 @@ enum { FM_ROUNDOFF = 0, FM_PLAIN = 1 }; /* Eq. ParallRoundOff or Eq. rat1       
  * columns solved in column blocks across the grid, and B^2 and each squaring
  * computed as 8 x 8 output tiles over all blocks; grid-wide barriers (bounded
  * waits: info -7 when one runs out) separate the steps.  The call
- * synchronizes its stream to read the status.
+ * synchronizes its stream only to read a status that was asked for.
  * FM_PATH_AUTO: FM_BF16_IR calls, single-matrix calls with d > fm_max_dim(),
  * and batched exp, phi_1, phi_1 V and cos/sin in FM_MIXED with dmax >= 64 take
  * the grid path; single-matrix exp with d <= 512 in FM_FP64 or FM_MIXED the

@@ -438,19 +438,35 @@ class ExpmvFn(torch.autograd.Function):
     """w = exp(tA) v for a batch of equal-order real matrices, with the
     hand-written adjoint kernel as backward.  A: (batch, d, d) float64 CUDA,
     v: (batch, d); nsteps: step counts, fixed (not differentiated); None
-    takes N = max(1, ceil(||tA||_1 / theta)) per matrix from the library.  A
-    nonzero status of any matrix raises FmError."""
+    takes N = max(1, ceil(||tA||_1 / theta)) per matrix from the library.
+    precision: "fp64" runs the forward map in the adjoint kernel (double);
+    "fp32_ir" runs it as the batched action with single-precision factors and
+    iterative refinement (one-CTA kernels), accurate to double; the backward is
+    the double adjoint in both cases, with the forward's N.  A nonzero status
+    of any matrix raises FmError."""
 
     @staticmethod
-    def forward(ctx, A, v, nsteps=None, t=1.0, coeffs="R8"):
+    def forward(ctx, A, v, nsteps=None, t=1.0, coeffs="R8", precision="fp64"):
         b, d, _ = A.shape
         P = Packed(dims=[d] * b, flat=A.reshape(-1).contiguous())
-        if nsteps is None:  # N as the action chooses it, computed on the device
-            nsteps, info = select_batched(P, t, coeffs, "expmv_adj")
-            _raise_info(info, "ExpmvFn step count")
         vf = v.reshape(-1).contiguous()
-        zero = torch.zeros_like(vf)
-        W, _, _, info = expmv_adjoint_batched(P, vf, zero, nsteps, t, coeffs)
+        if precision == "fp64":
+            if nsteps is None:  # N as the action chooses it, computed on the device
+                nsteps, info = select_batched(P, t, coeffs, "expmv_adj")
+                _raise_info(info, "ExpmvFn step count")
+            zero = torch.zeros_like(vf)
+            W, _, _, info = expmv_adjoint_batched(P, vf, zero, nsteps, t, coeffs)
+        elif precision == "fp32_ir":
+            kw = {}
+            if nsteps is not None:
+                ns = [int(x) for x in torch.as_tensor(nsteps).reshape(-1).tolist()]
+                if len(set(ns)) != 1:
+                    raise ValueError("precision='fp32_ir' takes one step count for the batch")
+                kw["nsteps"] = ns[0]
+            W, info, N = expmv_batched(P, vf, 1, t, coeffs, precision="fp32_ir", path="cta", **kw)
+            nsteps = N.to(torch.int64)
+        else:
+            raise ValueError("precision must be 'fp64' or 'fp32_ir'")
         _raise_info(info, "ExpmvFn forward")
         ctx.save_for_backward(A, v)
         ctx.nsteps, ctx.t, ctx.coeffs = nsteps, t, coeffs
@@ -465,4 +481,4 @@ class ExpmvFn(torch.autograd.Function):
                                                     gw.reshape(-1).contiguous(), ctx.nsteps, ctx.t,
                                                     ctx.coeffs)
         _raise_info(info, "ExpmvFn backward")
-        return Abar.view(b, d, d), vbar.view(b, d), None, None, None
+        return Abar.view(b, d, d), vbar.view(b, d), None, None, None, None

@@ -198,39 +198,14 @@ __global__ void b_add_identity(const BMat* mats, const int* mask, const T* in, d
   }
 }
 
-// Row digit planes of rows [RB y, RB y + RB) of X_b (d x d) and their exponents
-// ex[eo + r].  Only real rows and the 8-value groups holding real columns are
-// written; the rest of the planes stays zero from the reset at the start of
-// the call.
+// The row digit planes of rows [r0, r0 + nr) of X_b (Xb: its first element,
+// d x d) with the rows' exponents s_e (shared memory, set by the caller).
+// Only real rows and the 8-value groups holding real columns are written; the
+// rest of the planes stays zero from the reset at the start of the call.
 template <class T>
-__global__ void b_split_rows(const BMat* mats, const int* mask, const T* X, unsigned char* px,
-                             int* ex) {
-  __shared__ int s_e[RB];
-  if (!mask[blockIdx.x]) return;
-  const BMat M = mats[blockIdx.x];
+__device__ __forceinline__ void row_planes(const BMat& M, const T* Xb, int r0, int nr,
+                                           const int* s_e, unsigned char* px) {
   const int n = M.d, kc = M.kc;
-  const int r0 = blockIdx.y * RB;
-  if (r0 >= n) return;
-  const int nr = min(RB, n - r0);
-  const T* Xb = X + M.off;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int rr = w; rr < nr; rr += nw) {
-    const int r = r0 + rr;
-    unsigned long long mx = 0;  // largest |re|, |im| as bits: integer operations only
-    for (int k = lane; k < n; k += 32) {
-      const unsigned long long b = abs_bits<T>(Xb[(size_t)r * n + k]);
-      mx = b > mx ? b : mx;
-    }
-    for (int o = 16; o; o >>= 1) {
-      const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = b > mx ? b : mx;
-    }
-    if (lane == 0) {
-      s_e[rr] = oz::exp_above_bits(mx);
-      ex[M.eo + r] = s_e[rr];
-    }
-  }
-  __syncthreads();
   unsigned char* pb = px + M.px;
   const size_t pxs = (size_t)M.mtn * kc * GXST;
   const int g8 = (n + 7) / 8;  // 8-value groups holding real columns
@@ -263,6 +238,40 @@ __global__ void b_split_rows(const BMat* mats, const int* mask, const T* X, unsi
       for (int p = 0; p < oz::S; ++p) *(uint4*)(pb + pxs + blk + p * GXB + off) = *(const uint4*)di[p];
     }
   }
+}
+
+// Row digit planes of rows [RB y, RB y + RB) of X_b (d x d) and their exponents
+// ex[eo + r] (one warp per row for the row's largest entry).
+template <class T>
+__global__ void b_split_rows(const BMat* mats, const int* mask, const T* X, unsigned char* px,
+                             int* ex) {
+  __shared__ int s_e[RB];
+  if (!mask[blockIdx.x]) return;
+  const BMat M = mats[blockIdx.x];
+  const int n = M.d;
+  const int r0 = blockIdx.y * RB;
+  if (r0 >= n) return;
+  const int nr = min(RB, n - r0);
+  const T* Xb = X + M.off;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int rr = w; rr < nr; rr += nw) {
+    const int r = r0 + rr;
+    unsigned long long mx = 0;  // largest |re|, |im| as bits: integer operations only
+    for (int k = lane; k < n; k += 32) {
+      const unsigned long long b = abs_bits<T>(Xb[(size_t)r * n + k]);
+      mx = b > mx ? b : mx;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) {
+      s_e[rr] = oz::exp_above_bits(mx);
+      ex[M.eo + r] = s_e[rr];
+    }
+  }
+  __syncthreads();
+  row_planes<T>(M, Xb, r0, nr, s_e, px);
 }
 
 // Column digit planes of columns [CB y, CB y + CB) of Y_b (N-major) and their
@@ -338,68 +347,59 @@ __global__ void b_split_cols(const BMat* mats, const int* mask, const T* Y, unsi
   }
 }
 
-// rows [RB y, RB y + RB) of out_b = alpha P_b + b1 Z1_b + b2 Z2_b + g I, P_b
-// from the exact sums; emax[b] (bits, zeroed by the caller, nullable) =
-// largest |re|, |im| of out_b
+// rows [RB y, RB y + RB) of out_b = alpha P_b + b1 Z1_b + b2 Z2_b + g I, one
+// warp per row; P_b is the product, each entry its exact sum rounded once to
+// double by the tile kernel (the matrices' packed layout).  emax[b] (bits,
+// zeroed by the caller, nullable) = largest |re|, |im| of out_b.  px, ex
+// (nullable): also the row digit planes of out_b and their exponents, for a
+// product that takes out_b as its left operand next (no separate row split).
 template <class T>
-__global__ void b_epilogue(const BMat* mats, const int* mask, const long long* acc, const int* ex,
-                           const int* fy, Epi e, T* out, unsigned long long* emax, double* flops) {
+__global__ void b_epilogue(const BMat* mats, const int* mask, const T* P, Epi e, T* out,
+                           unsigned long long* emax, unsigned char* px, int* ex) {
+  __shared__ int s_e[RB];
   if (!mask[blockIdx.x]) return;
   const BMat M = mats[blockIdx.x];
-  const int n = M.d, parts = El<T>::parts;
+  const int n = M.d;
   const int r0 = blockIdx.y * RB;
   if (r0 >= n) return;
   const int nr = min(RB, n - r0);
-  if (flops && blockIdx.y == 0 && threadIdx.x == 0)
-    atomicAdd(flops, (parts == 2 ? 8.0 : 2.0) * n * (double)n * n);
-  const int Mp = M.mtn * oz::TM, Np = M.ntn * oz::TN;
-  const long long* ab = acc + M.acc * 2;
-  const T* Z1 = (const T*)e.Z1;
-  const T* Z2 = (const T*)e.Z2;
+  const T* Pb = P + M.off;
+  const T* Z1 = e.Z1 ? (const T*)e.Z1 + M.off : nullptr;
+  const T* Z2 = e.Z2 ? (const T*)e.Z2 + M.off : nullptr;
+  T* Ob = out + M.off;
   const bool scale = e.ar != 1.0 || e.ai != 0;
-  unsigned long long mx = 0;
-  const int cnt = nr * n;
-#pragma unroll 2
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-    const int i = r0 + k / n, j = k % n;
-    const size_t el = (size_t)i * n + j;
-    const int e2 = ex[M.eo + i] + fy[M.fo + j] - 64;
-    const longlong2 a0 = *(const longlong2*)(ab + ((size_t)i * Np + j) * 2);
-    T v;
-    if (e.fx) {
-      const T z1 = Z1 ? Z1[M.off + el] : El<T>::make(0.0, 0.0);
-      const T z2 = Z2 ? Z2[M.off + el] : El<T>::make(0.0, 0.0);
-      const double re = epi_part(e, a0.x, a0.y, e2, Z1, El<T>::re(z1), Z2, El<T>::re(z2), i == j, e.gr);
-      double im = 0;
-      if (parts == 2) {
-        const longlong2 a1 = *(const longlong2*)(ab + ((size_t)Mp * Np + (size_t)i * Np + j) * 2);
-        im = epi_part(e, a1.x, a1.y, e2, Z1, El<T>::im(z1), Z2, El<T>::im(z2), i == j, e.gi);
-      }
-      v = El<T>::make(re, im);
-    } else {
-      const double pr = oz::combine_scaled(a0.x, a0.y, e2);
-      double pi = 0;
-      if (parts == 2) {
-        const longlong2 a1 = *(const longlong2*)(ab + ((size_t)Mp * Np + (size_t)i * Np + j) * 2);
-        pi = oz::combine_scaled(a1.x, a1.y, e2);
-      }
-      v = El<T>::make(pr, pi);
+  const bool diag = e.gr != 0 || e.gi != 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long bm = 0;
+  for (int rr = w; rr < nr; rr += nw) {
+    const int r = r0 + rr;
+    const size_t ro = (size_t)r * n;
+    unsigned long long mx = 0;
+#pragma unroll 4
+    for (int c = lane; c < n; c += 32) {
+      T v = Pb[ro + c];
       if (scale) v = cmul<T>(e.ar, e.ai, v);
-      if (Z1) v = axpy1<T>(v, e.b1r, e.b1i, Z1[M.off + el]);
-      if (Z2) v = axpy1<T>(v, e.b2r, e.b2i, Z2[M.off + el]);
-      if (i == j && (e.gr != 0 || e.gi != 0)) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
+      if (Z1) v = axpy1<T>(v, e.b1r, e.b1i, Z1[ro + c]);
+      if (Z2) v = axpy1<T>(v, e.b2r, e.b2i, Z2[ro + c]);
+      if (diag && r == c) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
+      Ob[ro + c] = v;
+      const unsigned long long ab = abs_bits<T>(v);
+      mx = ab > mx ? ab : mx;
     }
-    out[M.off + el] = v;
-    const unsigned long long bb = abs_bits<T>(v);
-    mx = bb > mx ? bb : mx;
-  }
-  if (emax) {
     for (int o = 16; o; o >>= 1) {
       const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
       mx = v > mx ? v : mx;
     }
-    if ((threadIdx.x & 31) == 0 && mx) atomicMax(emax + blockIdx.x, mx);
+    if (px && lane == 0) {
+      s_e[rr] = oz::exp_above_bits(mx);
+      ex[M.eo + r] = s_e[rr];
+    }
+    bm = mx > bm ? mx : bm;
   }
+  if (emax && lane == 0 && bm) atomicMax(emax + blockIdx.x, bm);
+  if (!px) return;
+  __syncthreads();  // the block's rows of out_b and their exponents are in place
+  row_planes<T>(M, Ob, r0, nr, s_e, px);
 }
 
 // One correction step's decision per matrix (the single-matrix rule):

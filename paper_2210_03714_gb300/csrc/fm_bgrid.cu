@@ -25,7 +25,6 @@ struct Geo {
   std::vector<int4> items;
   long long elems = 0;       // sum of d^2
   long long pxb = 0, pyb = 0;  // plane bytes (all sets)
-  long long accp = 0;        // accumulator pairs
   long long rows = 0, cols = 0;
 };
 
@@ -45,13 +44,11 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
     M.voff = voff ? voff[b] : 0;
     M.px = g.pxb;
     M.py = g.pyb;
-    M.acc = g.accp;
     M.eo = (int)g.rows;
     M.fo = (int)g.cols;
     g.elems += (long long)n * n;
     g.pxb += (long long)parts * M.mtn * M.kc * grid::GXST;
     g.pyb += (long long)(cplx ? 3 : 1) * M.ntn * M.kc * grid::GYST;
-    g.accp += (long long)parts * M.mtn * oz::TM * M.ntn * oz::TN;
     g.rows += (long long)M.mtn * oz::TM;
     g.cols += (long long)M.ntn * oz::TN;
     for (int p = 0; p < parts; ++p)
@@ -67,7 +64,7 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 
 struct Lay {
   size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, B2, C, Y, E, F, F1,
-      G, pxC, pxG, py, acc, exC, exG, fy, total;
+      G, pxC, pxG, py, P, exC, exG, fy, total;
 };
 
 Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
@@ -100,7 +97,7 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.pxC = take((size_t)g.pxb);
   L.pxG = take((size_t)g.pxb);
   L.py = take((size_t)g.pyb);
-  L.acc = take((size_t)g.accp * 16);
+  L.P = take((size_t)g.elems * elt);
   L.exC = take((size_t)g.rows * 4);
   L.exG = take((size_t)g.rows * 4);
   L.fy = take((size_t)g.cols * 4);
@@ -144,7 +141,7 @@ class BRunner {
   T *B_ = nullptr, *B2_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
     *F1_ = nullptr, *G_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
-  long long* acc_ = nullptr;
+  T* P_ = nullptr;  // the products, each entry rounded once from its exact sum
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
   long long products_ = 0;
   int sms_ = 1;
@@ -174,8 +171,6 @@ class BRunner {
     return h;
   }
 
-  // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
-  // row planes of X into px (else reuse those already there)
   // Y = (I - C)^-1 C by residual correction from Y = C, for every live matrix:
   // E = C Y + C - Y, then Y = Y E + Y + E (the product at the digit levels
   // its accuracy needs), until the largest residual entry times d is below
@@ -215,19 +210,22 @@ class BRunner {
       e2.Z2 = E_;
       e2.b2r = 1.0;
       // first correction: Y = C, whose row planes are already in pxC
-      if (it == 0) prod(Y_, pxC_, exC_, false, E_, e2, Y_, mask_u_, nullptr, lmax);
-      else prod(Y_, pxG_, exG_, true, E_, e2, Y_, mask_u_, nullptr, lmax);
+      // (later corrections: the row planes of Y from the previous update's epilogue)
+      if (it == 0) prod(Y_, pxC_, exC_, false, E_, e2, Y_, mask_u_, nullptr, lmax, pxG_, exG_);
+      else prod(Y_, pxG_, exG_, false, E_, e2, Y_, mask_u_, nullptr, lmax, pxG_, exG_);
       api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
       if (h.active == 0) break;
     }
   }
 
+  // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
+  // row planes of X into px (else they are there already); px_next, ex_next:
+  // the epilogue also writes the row planes of out there (out is the left
+  // operand of the next product)
   void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp,
-            const grid::Epi& e_in, T* out, const int* mask, unsigned long long* emax,
-            int lmax = 8) {
+            const grid::Epi& e, T* out, const int* mask, unsigned long long* emax,
+            int lmax = 8, unsigned char* px_next = nullptr, int* ex_next = nullptr) {
     if (err_ != cudaSuccess) return;
-    grid::Epi e = e_in;
-    grid::fixed_form(e);
     const int batch = j_.batch;
     const int parts = grid::El<T>::parts;
     if (split_x) {
@@ -249,12 +247,15 @@ class BRunner {
     }
     a.ksplit = 1;
     a.lmax = lmax;
-    a.acc = acc_;
+    a.acc = nullptr;
     a.err = &ctr_->err;
     a.items = items_;
     a.mats = mats_;
     a.mask = mask;
-    a.store = 1;
+    a.store = 2;  // each exact sum rounded once to double into P_
+    a.pout = (double*)P_;
+    a.ex = ex;
+    a.fy = fy_;
     a.flops = &ctr_->flops;
     a.dflops = &ctr_->dflops;
     a.nitems = (int)g_.items.size();
@@ -264,7 +265,7 @@ class BRunner {
     timer_.stop(st_);
     check("tensor-core products");
     if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
-    grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy_, e, out, emax, nullptr);
+    grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, P_, e, out, emax, px_next, ex_next);
     check("product epilogue");
     ++products_;
   }
@@ -312,7 +313,7 @@ int BRunner<T>::run() {
   pxC_ = (unsigned char*)(base_ + L_.pxC);
   pxG_ = (unsigned char*)(base_ + L_.pxG);
   py_ = (unsigned char*)(base_ + L_.py);
-  acc_ = (long long*)(base_ + L_.acc);
+  P_ = (T*)(base_ + L_.P);
   exC_ = (int*)(base_ + L_.exC);
   exG_ = (int*)(base_ + L_.exG);
   fy_ = (int*)(base_ + L_.fy);
@@ -450,12 +451,12 @@ int BRunner<T>::run() {
       e1.ar = 2.0;
       e1.Z1 = F1_;
       e1.b1r = 2.0;
-      prod(E_, pxG_, exG_, true, F1_, e1, F1_, mask_s_, nullptr);
+      prod(E_, pxG_, exG_, q == 0, F1_, e1, F1_, mask_s_, nullptr);
       grid::Epi e;
       e.ar = 2.0;
       e.Z1 = E_;
       e.b1r = 4.0;
-      prod(E_, pxG_, exG_, false, E_, e, E_, mask_s_, nullptr);
+      prod(E_, pxG_, exG_, false, E_, e, E_, mask_s_, nullptr, 8, pxG_, exG_);
       continue;
     }
     if (phi) {
@@ -466,13 +467,14 @@ int BRunner<T>::run() {
       e1.b1r = 1.0;
       e1.Z2 = E_;
       e1.b2r = 0.5;
-      prod(E_, pxG_, exG_, true, F1_, e1, F1_, mask_s_, nullptr);
+      prod(E_, pxG_, exG_, q == 0, F1_, e1, F1_, mask_s_, nullptr);
     }
     // E <- 2E + E E (the row planes of E are already there for phi_1)
     grid::Epi e;
     e.Z1 = E_;
     e.b1r = 2.0;
-    prod(E_, pxG_, exG_, !phi, E_, e, E_, mask_s_, nullptr);
+    // (after the first squaring the row planes of E come from the last epilogue)
+    prod(E_, pxG_, exG_, q == 0 && !phi, E_, e, E_, mask_s_, nullptr, 8, pxG_, exG_);
   }
   if (j.kind == JOB_EXPM) {
     grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.F, 1);

@@ -21,6 +21,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "../../include/fm.h"
 #include "cta_la.cuh"
 #include "fm_kernels.cuh"
@@ -344,22 +346,41 @@ int team_launch(const TeamJob& j, char* msg, size_t len) {
   a.piv = (int*)(base + L.piv);
   a.ctl = (TeamCtl*)(base + L.ctl);
   const size_t smem = team_smem(n, sizeof(T));
-  int dev = 0, sms = 1, per_sm = 0, coop = 0;
+  // per device, once: the kernel's shared-memory limit raised to the largest
+  // order's need, and one block per SM checked to fit (so any grid up to the
+  // SM count is co-resident)
+  static std::mutex mu;
+  static int ready[64] = {}, sms_of[64] = {};
+  int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(team_expm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, team_expm<T>, NT, smem);
-  if (e != cudaSuccess) {
-    snprintf(msg, len, "team path setup: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    snprintf(msg, len, "team path setup: %s", e != cudaSuccess ? cudaGetErrorString(e) : "device id");
     return FM_ECUDA;
   }
-  if (!coop || per_sm < 1) {
-    snprintf(msg, len, "team path: the device cannot run a cooperative launch of this size");
-    return FM_ECUDA;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[dev]) {
+      const size_t smax = team_smem(kTeamMaxDim, sizeof(T));
+      int sms = 1, per_sm = 0, coop = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(team_expm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, team_expm<T>, NT, smax);
+      if (e != cudaSuccess) {
+        snprintf(msg, len, "team path setup: %s", cudaGetErrorString(e));
+        return FM_ECUDA;
+      }
+      if (!coop || per_sm < 1) {
+        snprintf(msg, len, "team path: the device cannot run a cooperative launch of this size");
+        return FM_ECUDA;
+      }
+      sms_of[dev] = sms;
+      ready[dev] = 1;
+    }
   }
+  const int sms = sms_of[dev];
   // blocks: enough for the product tiles and the solve items, at most one per SM
   const int nt = (n + TT8 - 1) / TT8;
   int G = sms;
@@ -378,6 +399,7 @@ int team_launch(const TeamJob& j, char* msg, size_t len) {
     snprintf(msg, len, "team path launch: %s", cudaGetErrorString(e));
     return FM_ECUDA;
   }
+  if (!j.info_host && !j.s_host) return FM_OK;  // no status wanted: stays asynchronous
   TeamCtl h;
   e = cudaMemcpyAsync(&h, a.ctl, sizeof h, cudaMemcpyDeviceToHost, j.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(j.st);

@@ -322,6 +322,59 @@ def test_autograd_function_fd(fm):
     assert abs(fd - an) <= 2e-7 * max(1.0, abs(an))
 
 
+def test_autograd_function_fd_d128(fm):
+    """The same central-difference check on the gradient workload's own order
+    (d = 128, N from the norm, two matrices), in two random directions."""
+    import torch
+    A, v, y = wl.grad_batch(batch=2, d=128, seed=4200)
+    Ns = [oracle.select_nsteps(np.abs(a).sum(0).max(), oracle.CS("R8").theta) for a in A]
+    At = T(A).requires_grad_(True)
+    vt = T(v).requires_grad_(True)
+    yt = T(y)
+    L = ((fm.ExpmvFn.apply(At, vt, Ns) - yt) ** 2).sum()
+    L.backward()
+    h = 1e-5
+    for seed in (7, 8):
+        g = np.random.default_rng(seed)
+        dA = torch.tensor(g.standard_normal(A.shape), device="cuda")
+        dv = torch.tensor(g.standard_normal(v.shape), device="cuda")
+        with torch.no_grad():
+            Lp = ((fm.ExpmvFn.apply(At + h * dA, vt + h * dv, Ns) - yt) ** 2).sum()
+            Lm = ((fm.ExpmvFn.apply(At - h * dA, vt - h * dv, Ns) - yt) ** 2).sum()
+        fd = float((Lp - Lm) / (2 * h))
+        an = float((At.grad * dA).sum() + (vt.grad * dv).sum())
+        assert abs(fd - an) <= 2e-7 * max(1.0, abs(an)), (seed, fd, an)
+
+
+def test_autograd_fp32_forward(fm):
+    """The gradient workload with the forward action in single-precision
+    factors plus refinement: the forward result against the oracle at 1e-12,
+    the gradients (the double adjoint with the forward's N) equal to those of
+    the double forward, and against the oracle's at 1e-8."""
+    import torch
+    A, v, y = wl.grad_batch(batch=4, d=128, seed=4300)
+    Ns = [oracle.select_nsteps(np.abs(a).sum(0).max(), oracle.CS("R8").theta) for a in A]
+    grads = []
+    for prec in ("fp32_ir", "fp64"):
+        At = T(A).requires_grad_(True)
+        vt = T(v).requires_grad_(True)
+        w = fm.ExpmvFn.apply(At, vt, None, 1.0, "R8", prec)
+        for b in range(len(A)):
+            W_ref, N_ref, _ = oracle.expmv(A[b], v[b], 1.0, "R8")
+            assert N_ref == Ns[b]
+            assert relerr(w[b].detach().cpu().numpy(), W_ref) <= TOL_FP64
+        ((w - T(y)) ** 2).sum().backward()
+        grads.append((At.grad.cpu().numpy(), vt.grad.cpu().numpy()))
+    for g1, g2 in zip(grads[0], grads[1]):
+        assert relerr(g1, g2) <= 1e-10
+    for b in range(len(A)):
+        W_ref, _, _ = oracle.expmv(A[b], v[b], 1.0, "R8")
+        wbar = 2 * (W_ref - y[b])
+        Ab_ref, vb_ref, _ = oracle.expmv_adjoint(A[b], v[b], wbar, Ns[b], 1.0, "R8")
+        assert relerr(grads[0][0][b], Ab_ref) <= 1e-8
+        assert relerr(grads[0][1][b], vb_ref) <= 1e-8
+
+
 # ---------------------------------------------------------------------------
 # status codes and degenerate cases
 # ---------------------------------------------------------------------------

@@ -3,7 +3,8 @@ over many thread blocks of one cooperative launch (the shifted systems of
 Eq. ParallRoundOff factored on separate blocks at once, Sec. 2; the solves'
 right-hand-side columns, B^2 and the squarings split over the grid).  Double
 arithmetic throughout, so the bar is the 1e-12 of every double-accurate path,
-against the oracle, with the same s."""
+against the oracle, with the same s; for a set or form whose weights cancel it
+is twice the measured spread of two correct double evaluations."""
 import numpy as np
 import pytest
 
@@ -30,6 +31,20 @@ def T(x):
     return torch.tensor(x, dtype=dt, device="cuda")
 
 
+def spread_bar(A, cs, form, F_ref):
+    """max(1e-12, twice the measured spread of two correct double evaluations):
+    the oracle on P A P^T mapped back against the oracle on A.  Sets whose
+    weights cancel (Sec. 4.3: sum |b_i c_i| of R10* is 1.3e6) and the plain form
+    of Eq. rat1 amplify rounding by that much, so two correct evaluations differ
+    by about 1e-10 there; for R4, R8 and the Pade set in the roundoff form the
+    spread is far below 1e-12."""
+    d = A.shape[0]
+    p = np.random.default_rng(5).permutation(d)
+    F2, _, _ = oracle.expm(A[np.ix_(p, p)], 1.0, cs, form)
+    q = np.argsort(p)
+    return max(TOL_FP64, 2.0 * relerr(F2[np.ix_(q, q)], F_ref))
+
+
 # orders: one element, below one 8 x 8 tile, ragged tiles, the d = 64 problem,
 # several column blocks per system, the largest order of the path
 @pytest.mark.parametrize("d", [1, 5, 16, 37, 64, 130, 256, 512])
@@ -40,7 +55,8 @@ def test_team_expm_vs_oracle(fm, d, name):
     F_ref, s_ref, _ = oracle.expm(A, 1.0, cs)
     F, info, s = fm.expm(T(A), 1.0, fm.Coeffs(cs), precision="fp64", path="team")
     assert info == 0 and s == s_ref
-    assert relerr(F.cpu().numpy(), F_ref) <= TOL_FP64
+    bar = spread_bar(A, cs, oracle.ROUNDOFF, F_ref) if name == "R10star" else TOL_FP64
+    assert relerr(F.cpu().numpy(), F_ref) <= bar
 
 
 def test_team_single_d64_is_the_default_route(fm):
@@ -60,7 +76,10 @@ def test_team_single_d64_is_the_default_route(fm):
 def test_team_forms_against_one_cta(fm, form):
     """Both forms of Eq. ParallRoundOff / Eq. rat1 against the oracle and
     against the one-CTA kernel in double (same systems, same element-wise
-    steps: only the association of the dot products differs)."""
+    steps: only the association of the dot products differs).  The roundoff
+    form at 1e-12; the plain form within twice the measured spread of two
+    correct double evaluations (about 1.2e-10 here: Sec. 4.3, the rounding of
+    each (I - c_i B)^-1 is multiplied by |b_i|, sum |b_i| = 5.8e3 for R8)."""
     cs = oracle_set("R8")
     A = wl.dense_scaled(96, 6.0, 77)
     ofm = oracle.ROUNDOFF if form == "roundoff" else oracle.PLAIN
@@ -68,8 +87,9 @@ def test_team_forms_against_one_cta(fm, form):
     F1, i1, s1 = fm.expm(T(A), 1.0, fm.Coeffs(cs), precision="fp64", path="team", form=form)
     F2, i2, s2 = fm.expm(T(A), 1.0, fm.Coeffs(cs), precision="fp64", path="cta", form=form)
     assert i1 == i2 == 0 and s1 == s2 == s_ref
-    assert relerr(F1.cpu().numpy(), F_ref) <= TOL_FP64
-    assert relerr(F1.cpu().numpy(), F2.cpu().numpy()) <= TOL_FP64
+    bar = TOL_FP64 if form == "roundoff" else spread_bar(A, cs, ofm, F_ref)
+    assert relerr(F1.cpu().numpy(), F_ref) <= bar
+    assert relerr(F1.cpu().numpy(), F2.cpu().numpy()) <= bar
 
 
 @pytest.mark.parametrize("d", [24, 200])

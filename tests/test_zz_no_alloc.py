@@ -3,14 +3,16 @@
 Its scratch is a fixed array inside the library image, shared by every call.
 These checks call it through the C ABI twice in a row (different orders and
 precisions, so the second call runs over whatever the first left in the
-array) and compare each result with fm_expm on the same input, within the
-parity tolerance of the other GPU tests.  The file is collected last so that a
+array) and compare each result with fm_expm on the same input and with the
+oracle, within the parity tolerance of the other GPU tests.  The file is collected last so that a
 failure here does not stop the rest of a -x run.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
+
+import oracle
 
 from _common import TOL_FP64, need_gpu
 
@@ -35,7 +37,9 @@ def test_noalloc_matches_expm_twice():
     assert L.fm_coeffs_builtin(3, C.byref(cs)) == 0  # R8
     cases = [(128, "mixed", 8.0, 1), (37, "fp64", 2.5, 2), (96, "mixed", 0.7, 3)]
     for d, prec, nrm, seed in cases:
-        A = torch.tensor(wl.dense_scaled(d, nrm, seed, scale_sqrt=True), device="cuda")
+        An = wl.dense_scaled(d, nrm, seed, scale_sqrt=True)
+        F_or, s_or, _ = oracle.expm(An, 1.0, "R8")
+        A = torch.tensor(An, device="cuda")
         o = _ffi.default_opts(precision=prec)
         F_ref = torch.empty_like(A)
         st, info_ref, s_ref = _call(L, L.fm_expm, cs, A, F_ref, o, torch)
@@ -44,8 +48,11 @@ def test_noalloc_matches_expm_twice():
             F = torch.full_like(A, float("nan"))
             st, info, s = _call(L, L.fm_expm_noalloc, cs, A, F, o, torch)
             assert st == 0, L.fm_last_error()
-            assert info == 0 and s == s_ref
+            assert info == 0 and s == s_ref == s_or
             err = float((F - F_ref).norm() / F_ref.norm())
+            assert err <= TOL_FP64, (d, prec, err)
+            Fh = F.cpu().numpy()
+            err = float(np.linalg.norm(Fh - F_or) / np.linalg.norm(F_or))
             assert err <= TOL_FP64, (d, prec, err)
 
 
