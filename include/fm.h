@@ -462,8 +462,10 @@ size_t fm_band_workspace_size(int batch, int d, int p, int k);
  * array inside the library image; opts.workspace is ignored.
  *   - d <= FM_NOALLOC_MAX_DIM and the scratch the call needs must fit in
  *     FM_NOALLOC_SCRATCH_BYTES, else FM_ESHAPE with a message.
- *   - opts.path = FM_PATH_GRID and opts.precision = FM_BF16_IR are rejected
- *     (FM_EINVAL): there is no grid form without scratch.
+ *   - opts.path = FM_PATH_GRID or FM_PATH_TEAM and opts.precision =
+ *     FM_BF16_IR are rejected (FM_EINVAL): those paths need their own scratch.
+ *     (fm_expm itself takes the team path for d <= 512 by default; the
+ *     results agree to the double-accurate bar.)
  *   - Every call uses the same array: calls that overlap on the GPU (several
  *     streams or host threads) race and give wrong results; serialize them.
  *   - CUDA loads the library's device code, the array included, on a device

@@ -347,14 +347,111 @@ __global__ void b_split_cols(const BMat* mats, const int* mask, const T* Y, unsi
   }
 }
 
+// An epilogue's weights with their cases decided on the host, so that the
+// element loop runs only the arithmetic each term needs (a test of a double
+// weight inside the loop costs an FP64 instruction per element):
+//   am      0: alpha = 1, 1: real alpha, 2: complex alpha
+//   m1, m2  0: no term, 1: + Z, 2: - Z, 3: + b Z (b real), 4: + b Z (b complex)
+//   gd      1: + g on the diagonal
+struct EpiModes {
+  const void* Z1;
+  const void* Z2;
+  double ar, ai, b1r, b1i, b2r, b2i, gr, gi;
+  int am, m1, m2, gd;
+};
+
+inline EpiModes epi_modes(const Epi& e) {
+  EpiModes m;
+  m.Z1 = e.Z1;
+  m.Z2 = e.Z2;
+  m.ar = e.ar;
+  m.ai = e.ai;
+  m.b1r = e.b1r;
+  m.b1i = e.b1i;
+  m.b2r = e.b2r;
+  m.b2i = e.b2i;
+  m.gr = e.gr;
+  m.gi = e.gi;
+  m.am = (e.ar == 1.0 && e.ai == 0) ? 0 : (e.ai == 0 ? 1 : 2);
+  auto mode = [](const void* z, double br, double bi) {
+    if (!z) return 0;
+    if (bi == 0 && br == 1.0) return 1;
+    if (bi == 0 && br == -1.0) return 2;
+    return bi == 0 ? 3 : 4;
+  };
+  m.m1 = mode(e.Z1, e.b1r, e.b1i);
+  m.m2 = mode(e.Z2, e.b2r, e.b2i);
+  m.gd = (e.gr != 0 || e.gi != 0) ? 1 : 0;
+  return m;
+}
+
+// one weighted term, its case a compile-time constant (1: + Z, 2: - Z, 3: + b Z
+// with b real, 4: + b Z with b complex)
+template <class T, int M>
+__device__ __forceinline__ T epi_term(T v, double br, double bi, T z) {
+  if constexpr (M == 1) return Tr<T>::add(v, z);
+  else if constexpr (M == 2) return Tr<T>::sub(v, z);
+  else if constexpr (M == 3) return Tr<T>::add(v, Tr<T>::rscale(z, br));
+  else return Tr<T>::add(v, cmul<T>(br, bi, z));
+}
+
+template <class T>
+__device__ __forceinline__ T epi_term_rt(T v, int mode, double br, double bi, T z) {
+  if (mode == 1) return Tr<T>::add(v, z);
+  if (mode == 2) return Tr<T>::sub(v, z);
+  if (mode == 3) return Tr<T>::add(v, Tr<T>::rscale(z, br));
+  return Tr<T>::add(v, cmul<T>(br, bi, z));
+}
+
+// the entries c = lane, lane + 32, ... of one row: P from the exact sums
+// (a0: the row's (hi, lo) pairs, part 1 at pst pairs further), the weights'
+// cases as template constants (AM < 0, M1 < 0: the cases read at run time,
+// with the diagonal term).  Returns the largest |re|, |im| (bits).  Cases
+// decided inside the loop would be compiled to predicated instructions of
+// every case, each taking an FP64 issue slot per entry.
+template <class T, int AM, int M1, int M2>
+__device__ __forceinline__ unsigned long long epi_row(const EpiModes& e, const long long* a0,
+                                                      size_t pst, int er, const int* fyb,
+                                                      const T* z1, const T* z2, T* o, int n,
+                                                      int r, int lane) {
+  unsigned long long mx = 0;
+#pragma unroll 2
+  for (int c = lane; c < n; c += 32) {
+    const int e2 = er + fyb[c];
+    const longlong2 p0 = *(const longlong2*)(a0 + (size_t)c * 2);
+    double pi = 0;
+    if (El<T>::parts == 2) {
+      const longlong2 p1 = *(const longlong2*)(a0 + (pst + c) * 2);
+      pi = oz::combine_scaled(p1.x, p1.y, e2);
+    }
+    T v = El<T>::make(oz::combine_scaled(p0.x, p0.y, e2), pi);
+    if constexpr (AM >= 0 && M1 >= 0) {
+      if constexpr (AM == 1) v = Tr<T>::rscale(v, e.ar);
+      if constexpr (AM == 2) v = cmul<T>(e.ar, e.ai, v);
+      if constexpr (M1 > 0) v = epi_term<T, M1>(v, e.b1r, e.b1i, z1[c]);
+      if constexpr (M2 > 0) v = epi_term<T, M2>(v, e.b2r, e.b2i, z2[c]);
+    } else {
+      if (e.am == 1) v = Tr<T>::rscale(v, e.ar);
+      else if (e.am == 2) v = cmul<T>(e.ar, e.ai, v);
+      if (e.m1) v = epi_term_rt<T>(v, e.m1, e.b1r, e.b1i, z1[c]);
+      if (e.m2) v = epi_term_rt<T>(v, e.m2, e.b2r, e.b2i, z2[c]);
+      if (e.gd && r == c) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
+    }
+    o[c] = v;
+    const unsigned long long b = abs_bits<T>(v);
+    mx = b > mx ? b : mx;
+  }
+  return mx;
+}
+
 // rows [RB y, RB y + RB) of out_b = alpha P_b + b1 Z1_b + b2 Z2_b + g I, one
-// warp per row; P_b is the product, each entry its exact sum rounded once to
-// double by the tile kernel (the matrices' packed layout).  emax[b] (bits,
+// warp per row; P_b from the exact sums (rounded once).  emax[b] (bits,
 // zeroed by the caller, nullable) = largest |re|, |im| of out_b.  px, ex
 // (nullable): also the row digit planes of out_b and their exponents, for a
 // product that takes out_b as its left operand next (no separate row split).
 template <class T>
-__global__ void b_epilogue(const BMat* mats, const int* mask, const T* P, Epi e, T* out,
+__global__ void b_epilogue(const BMat* mats, const int* mask, const long long* acc,
+                           const int* exs, const int* fy, EpiModes e, T* out,
                            unsigned long long* emax, unsigned char* px, int* ex) {
   __shared__ int s_e[RB];
   if (!mask[blockIdx.x]) return;
@@ -363,31 +460,41 @@ __global__ void b_epilogue(const BMat* mats, const int* mask, const T* P, Epi e,
   const int r0 = blockIdx.y * RB;
   if (r0 >= n) return;
   const int nr = min(RB, n - r0);
-  const T* Pb = P + M.off;
-  const T* Z1 = e.Z1 ? (const T*)e.Z1 + M.off : nullptr;
-  const T* Z2 = e.Z2 ? (const T*)e.Z2 + M.off : nullptr;
+  const int Mp = M.mtn * oz::TM, Np = M.ntn * oz::TN;
+  const size_t pst = (size_t)Mp * Np;
+  const long long* ab = acc + M.acc * 2;
+  const T* Z1 = e.m1 ? (const T*)e.Z1 + M.off : nullptr;
+  const T* Z2 = e.m2 ? (const T*)e.Z2 + M.off : nullptr;
+  const int* fyb = fy + M.fo;
   T* Ob = out + M.off;
-  const bool scale = e.ar != 1.0 || e.ai != 0;
-  const bool diag = e.gr != 0 || e.gi != 0;
+  // the weight combinations of this path's products
+  const int key = e.gd ? -1 : e.am * 100 + e.m1 * 10 + e.m2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   unsigned long long bm = 0;
   for (int rr = w; rr < nr; rr += nw) {
     const int r = r0 + rr;
     const size_t ro = (size_t)r * n;
-    unsigned long long mx = 0;
-#pragma unroll 4
-    for (int c = lane; c < n; c += 32) {
-      T v = Pb[ro + c];
-      if (scale) v = cmul<T>(e.ar, e.ai, v);
-      if (Z1) v = axpy1<T>(v, e.b1r, e.b1i, Z1[ro + c]);
-      if (Z2) v = axpy1<T>(v, e.b2r, e.b2i, Z2[ro + c]);
-      if (diag && r == c) v = Tr<T>::add(v, El<T>::make(e.gr, e.gi));
-      Ob[ro + c] = v;
-      const unsigned long long ab = abs_bits<T>(v);
-      mx = ab > mx ? ab : mx;
+    const int er = exs[M.eo + r] - 64;
+    const long long* a0 = ab + (size_t)r * Np * 2;
+    const T* z1 = Z1 ? Z1 + ro : nullptr;
+    const T* z2 = Z2 ? Z2 + ro : nullptr;
+    T* o = Ob + ro;
+    unsigned long long mx;
+#define FM_EPI_ROW(AM, M1, M2) epi_row<T, AM, M1, M2>(e, a0, pst, er, fyb, z1, z2, o, n, r, lane)
+    switch (key) {
+      case 0: mx = FM_EPI_ROW(0, 0, 0); break;      // B^2
+      case 12: mx = FM_EPI_ROW(0, 1, 2); break;     // residual C Y + C - Y
+      case 11: mx = FM_EPI_ROW(0, 1, 1); break;     // correction Y + E + E Y
+      case 13: mx = FM_EPI_ROW(0, 1, 3); break;     // F + G B + (sum a) B
+      case 14: mx = FM_EPI_ROW(0, 1, 4); break;     // the same, complex sum
+      case 30: mx = FM_EPI_ROW(0, 3, 0); break;     // squaring 2E + E E
+      case 113: mx = FM_EPI_ROW(1, 1, 3); break;    // phi_1 doubling
+      case 130: mx = FM_EPI_ROW(1, 3, 0); break;    // cos / sin doublings
+      default: mx = FM_EPI_ROW(-1, -1, -1); break;
     }
-    for (int o = 16; o; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+#undef FM_EPI_ROW
+    for (int o2 = 16; o2; o2 >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o2);
       mx = v > mx ? v : mx;
     }
     if (px && lane == 0) {

@@ -1404,8 +1404,8 @@ const char* fm_version(void) { return "fm 0.1 (sm_103a)"; }
 // in FM_NOALLOC_SCRATCH_BYTES (2 MiB); larger problems are rejected with
 // FM_ESHAPE.  All calls share the one array: calls that overlap on the GPU (two
 // streams, or two host threads) race on it and give wrong results; serialize
-// them.  It runs the one-CTA kernel only: opts.path = FM_PATH_GRID and
-// opts.precision = FM_BF16_IR are rejected with FM_EINVAL.  It is not for host
+// them.  It runs the one-CTA kernel only: opts.path = FM_PATH_GRID or
+// FM_PATH_TEAM and opts.precision = FM_BF16_IR are rejected with FM_EINVAL.  It is not for host
 // functions enqueued on a stream (cudaLaunchHostFunc): CUDA forbids every CUDA
 // call there, and this entry point launches kernels.
 // ---------------------------------------------------------------------------
@@ -1448,7 +1448,7 @@ extern "C" fm_status fm_expm_noalloc(const fm_coeffs* cs, int d, const double* A
   fm_opts o = resolve_opts(optsp);
   fm_status s = check_opts(o);
   if (s) return s;
-  if (o.path == FM_PATH_GRID || o.precision == FM_BF16_IR)
+  if (o.path == FM_PATH_GRID || o.path == FM_PATH_TEAM || o.precision == FM_BF16_IR)
     return fail(FM_EINVAL, "fm_expm_noalloc runs on the one-CTA kernel: opts.path must be "
                            "FM_PATH_AUTO or FM_PATH_CTA, opts.precision not FM_BF16_IR");
   o.precision = o.precision == FM_FP64 ? 0 : 1;

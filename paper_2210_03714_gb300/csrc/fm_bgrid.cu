@@ -24,6 +24,7 @@ struct Geo {
   std::vector<grid::BMat> mats;
   std::vector<int4> items;
   long long elems = 0;       // sum of d^2
+  long long accp = 0;        // accumulator pairs
   long long pxb = 0, pyb = 0;  // plane bytes (all sets)
   long long rows = 0, cols = 0;
 };
@@ -44,11 +45,13 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
     M.voff = voff ? voff[b] : 0;
     M.px = g.pxb;
     M.py = g.pyb;
+    M.acc = g.accp;
     M.eo = (int)g.rows;
     M.fo = (int)g.cols;
     g.elems += (long long)n * n;
     g.pxb += (long long)parts * M.mtn * M.kc * grid::GXST;
     g.pyb += (long long)(cplx ? 3 : 1) * M.ntn * M.kc * grid::GYST;
+    g.accp += (long long)parts * M.mtn * oz::TM * M.ntn * oz::TN;
     g.rows += (long long)M.mtn * oz::TM;
     g.cols += (long long)M.ntn * oz::TN;
     for (int p = 0; p < parts; ++p)
@@ -64,7 +67,7 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 
 struct Lay {
   size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, B2, C, Y, E, F, F1,
-      G, pxC, pxG, py, P, exC, exG, fy, total;
+      G, pxC, pxG, py, acc, exC, exG, fy, total;
 };
 
 Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
@@ -97,7 +100,7 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.pxC = take((size_t)g.pxb);
   L.pxG = take((size_t)g.pxb);
   L.py = take((size_t)g.pyb);
-  L.P = take((size_t)g.elems * elt);
+  L.acc = take((size_t)g.accp * 16);
   L.exC = take((size_t)g.rows * 4);
   L.exG = take((size_t)g.rows * 4);
   L.fy = take((size_t)g.cols * 4);
@@ -141,7 +144,7 @@ class BRunner {
   T *B_ = nullptr, *B2_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
     *F1_ = nullptr, *G_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
-  T* P_ = nullptr;  // the products, each entry rounded once from its exact sum
+  long long* acc_ = nullptr;  // exact sums of the products, (hi, lo) per entry
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
   long long products_ = 0;
   int sms_ = 1;
@@ -172,9 +175,13 @@ class BRunner {
   }
 
   // Y = (I - C)^-1 C by residual correction from Y = C, for every live matrix:
-  // E = C Y + C - Y, then Y = Y E + Y + E (the product at the digit levels
+  // E = C Y + C - Y, then Y = E Y + Y + E (the product at the digit levels
   // its accuracy needs), until the largest residual entry times d is below
-  // 2^-30 (then one more correction)
+  // 2^-30 (then one more correction).  Every iterate is a function of C, so
+  // E (I + Y) = (I + Y) E up to rounding and the update converges as the
+  // Newton-Schulz step does; in this order both products of a step take Y
+  // as the right operand (one column split per step) and E as the left one
+  // gets its row planes from its own epilogue.
   void correct(int dmax, int nb) {
     const int batch = j_.batch;
     api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
@@ -186,14 +193,14 @@ class BRunner {
       e1.b1r = 1.0;
       e1.Z2 = Y_;
       e1.b2r = -1.0;
-      prod(C_, pxC_, exC_, it == 0, Y_, e1, E_, mask_e_, emax_);
+      prod(C_, pxC_, exC_, it == 0, Y_, e1, E_, mask_e_, emax_, 8, pxG_, exG_);
       grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, it, j_.max_iters, mask_e_,
                                          mask_u_, j_.info_dev, &ctr_->active, &ctr_->corrections,
                                          &ctr_->emax);
       check("correction flags");
       const Ctr h = read_ctr();
       if (err_ != cudaSuccess) break;
-      // Y E needs an absolute accuracy of about u max|Y| only, and its error is
+      // E Y needs an absolute accuracy of about u max|Y| only, and its error is
       // about 2^(14 - 8 Lmax) 8 sqrt(d) max|Y| max|E|: keep the digit-pair
       // levels that bound requires
       double em;
@@ -209,10 +216,8 @@ class BRunner {
       e2.b1r = 1.0;
       e2.Z2 = E_;
       e2.b2r = 1.0;
-      // first correction: Y = C, whose row planes are already in pxC
-      // (later corrections: the row planes of Y from the previous update's epilogue)
-      if (it == 0) prod(Y_, pxC_, exC_, false, E_, e2, Y_, mask_u_, nullptr, lmax, pxG_, exG_);
-      else prod(Y_, pxG_, exG_, false, E_, e2, Y_, mask_u_, nullptr, lmax, pxG_, exG_);
+      // rows of E from the residual's epilogue, columns of Y from its product
+      prod(E_, pxG_, exG_, false, Y_, e2, Y_, mask_u_, nullptr, lmax, nullptr, nullptr, false);
       api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
       if (h.active == 0) break;
     }
@@ -221,10 +226,12 @@ class BRunner {
   // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
   // row planes of X into px (else they are there already); px_next, ex_next:
   // the epilogue also writes the row planes of out there (out is the left
-  // operand of the next product)
+  // operand of the next product); split_y = false: the column planes of Y
+  // are those of the last product (same Y, a subset of its matrices)
   void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp,
             const grid::Epi& e, T* out, const int* mask, unsigned long long* emax,
-            int lmax = 8, unsigned char* px_next = nullptr, int* ex_next = nullptr) {
+            int lmax = 8, unsigned char* px_next = nullptr, int* ex_next = nullptr,
+            bool split_y = true) {
     if (err_ != cudaSuccess) return;
     const int batch = j_.batch;
     const int parts = grid::El<T>::parts;
@@ -232,8 +239,10 @@ class BRunner {
       grid::b_split_rows<T><<<gR_, NT, 0, st_>>>(mats_, mask, X, px, ex);
       check("row digit planes");
     }
-    grid::b_split_cols<T><<<gC_, NT, 0, st_>>>(mats_, mask, Yp, py_, fy_);
-    check("column digit planes");
+    if (split_y) {
+      grid::b_split_cols<T><<<gC_, NT, 0, st_>>>(mats_, mask, Yp, py_, fy_);
+      check("column digit planes");
+    }
     grid::OzTiles a;
     memset(&a, 0, sizeof a);
     a.px = px;
@@ -247,15 +256,12 @@ class BRunner {
     }
     a.ksplit = 1;
     a.lmax = lmax;
-    a.acc = nullptr;
+    a.acc = acc_;
     a.err = &ctr_->err;
     a.items = items_;
     a.mats = mats_;
     a.mask = mask;
-    a.store = 2;  // each exact sum rounded once to double into P_
-    a.pout = (double*)P_;
-    a.ex = ex;
-    a.fy = fy_;
+    a.store = 1;
     a.flops = &ctr_->flops;
     a.dflops = &ctr_->dflops;
     a.nitems = (int)g_.items.size();
@@ -265,7 +271,8 @@ class BRunner {
     timer_.stop(st_);
     check("tensor-core products");
     if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
-    grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, P_, e, out, emax, px_next, ex_next);
+    grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy_, grid::epi_modes(e), out,
+                                             emax, px_next, ex_next);
     check("product epilogue");
     ++products_;
   }
@@ -313,7 +320,7 @@ int BRunner<T>::run() {
   pxC_ = (unsigned char*)(base_ + L_.pxC);
   pxG_ = (unsigned char*)(base_ + L_.pxG);
   py_ = (unsigned char*)(base_ + L_.py);
-  P_ = (T*)(base_ + L_.P);
+  acc_ = (long long*)(base_ + L_.acc);
   exC_ = (int*)(base_ + L_.exC);
   exG_ = (int*)(base_ + L_.exG);
   fy_ = (int*)(base_ + L_.fy);

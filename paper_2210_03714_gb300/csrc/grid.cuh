@@ -573,6 +573,7 @@ struct BMat {
   long long off;        // element offset in the packed work matrices (leading dimension d)
   long long uoff;       // element offset of the caller's matrix (A in, F out)
   long long px, py;     // byte offsets of its X and Y digit planes
+  long long acc;        // offset, in (hi, lo) pairs, of its accumulators
   int eo, fo;           // offsets of its rows (mtn*128) and columns (ntn*64) in the
                         // exponent and maximum arrays
   long long voff;       // element offset of its block of vectors V / W (d x m), actions
@@ -598,14 +599,7 @@ struct OzTiles {
   const int4* items;
   const BMat* mats;
   const int* mask;
-  int store;       // 1: plain stores into acc (one item per tile), 0: atomic adds,
-                   // 2 (batch mode): each exact sum rounded once to double into
-                   // pout (the matrices' packed layout, leading dimension d;
-                   // complex: the part's component), with the planes' exponents
-                   // ex (rows) and fy (columns)
-  double* pout;
-  const int* ex;
-  const int* fy;
+  int store;       // 1: plain stores into acc (one item per tile), 0: atomic adds
   double* flops;             // batch mode: product flops (2d^3, complex 8d^3) added, nullable
   double* dflops;            // batch mode: digit-pair flops (pairs kept x product flops), nullable
   int nitems;                // work items: batch mode, the table's length; else parts x tiles x ksplit
@@ -642,7 +636,7 @@ __device__ __forceinline__ TileGeo tile_geo(const OzTiles& a, int idx) {
     G.py = a.py + M.py;
     G.pxs = (size_t)G.mtn * G.kc * GXST;
     G.pys = (size_t)G.ntn * G.kc * GYST;
-    G.acc = nullptr;  // batch mode: the sums go to pout (store 2)
+    G.acc = a.acc + M.acc * 2;
     G.dm = M.d;
   } else {
     int item = idx;
@@ -850,24 +844,6 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
         if (lane == 0) tc::mbar_arrive(&accr);
       }
       if (!ok || s_err) break;
-      if (a.store == 2) {
-        // round each sum to double: P = (hi 2^24 + lo) 2^(ex_i + fy_j - 64)
-        const BMat& M = a.mats[G.b];
-        const int n = M.d;
-        const int row = G.mt * oz::TM + 32 * (warp & 3) + lane;
-        const int col0 = G.nt * oz::TN + colh;
-        if (row < n) {
-          const int er = a.ex[M.eo + row] - 64;
-          const int* fyc = a.fy + M.fo + col0;
-          const size_t el = (size_t)M.off + (size_t)row * n + col0;
-          const int cs = a.nparts;  // element stride in doubles (complex: 2)
-          double* dst = a.pout + el * cs + G.part;
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j < n) dst[(size_t)j * cs] = oz::combine_scaled(ahi[j], alo[j], er + fyc[j]);
-        }
-        continue;
-      }
       const int Mp = G.mtn * oz::TM, Np = G.ntn * oz::TN;
       const int row = G.mt * oz::TM + 32 * (warp & 3) + lane;
       unsigned long long* dst =

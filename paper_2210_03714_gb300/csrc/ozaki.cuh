@@ -28,6 +28,7 @@
 // while one thread issues tcgen05.mma into eight 128 x 64 accumulators.
 #pragma once
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include "cta_la.cuh"
 #include "tc.cuh"
@@ -125,13 +126,48 @@ __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out) {
   }
 }
 
+// count of leading zero bits and a bit pattern as a double, on both sides
+__host__ __device__ __forceinline__ int clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+__host__ __device__ __forceinline__ double bits_double(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
+
+// m 2^e (1 <= m <= 2^53, already rounded) as a double, sign neg, assembled
+// from its bits
+__host__ __device__ __forceinline__ double assemble_m(unsigned long long m, int e, bool neg) {
+  const int nbm = 64 - clz64(m);
+  const int ef = e + nbm - 1 + 1023;  // biased exponent of the result
+  const unsigned long long sgn = neg ? 0x8000000000000000ULL : 0ULL;
+  const unsigned long long mant = nbm <= 53 ? (m << (53 - nbm)) : (m >> (nbm - 53));
+  if (ef >= 1 && ef <= 2046)
+    return bits_double(((unsigned long long)ef << 52) | (mant & 0xFFFFFFFFFFFFFULL) | sgn);
+  // outside the normal range, with integer operations only (no FP64 unit):
+  // overflow to infinity; below 2^-1022 the 53-bit mantissa is shifted into
+  // the subnormal field (truncated: such values are far below any result here)
+  if (ef > 2046) return bits_double(sgn | 0x7FF0000000000000ULL);
+  const int sh = 1 - ef;
+  return bits_double(sgn | (sh < 64 ? (mant >> sh) : 0ULL));
+}
+
 // round-to-nearest double of v 2^e2, v an exact 128-bit integer
-__device__ __forceinline__ double round_i128(__int128 v, int e2) {
+__host__ __device__ __forceinline__ double round_i128(__int128 v, int e2) {
   if (v == 0) return 0.0;
   const bool neg = v < 0;
   unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
   const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
-  const int nb = ah ? 128 - __clzll(ah) : 64 - __clzll(al);  // bit length
+  const int nb = ah ? 128 - clz64(ah) : 64 - clz64(al);  // bit length
   unsigned long long m;
   int e = e2;
   if (nb <= 53) {
@@ -144,24 +180,51 @@ __device__ __forceinline__ double round_i128(__int128 v, int e2) {
     if (rem > half || (rem == half && (m & 1))) m += 1;
     e += sh;
   }
-  // assemble the double directly: m 2^e with m <= 2^53
-  const int nbm = 64 - __clzll((long long)m);
-  const int ef = e + nbm - 1 + 1023;  // biased exponent of the result
-  if (ef >= 1 && ef <= 2046) {
-    const unsigned long long mant = nbm <= 53 ? (m << (53 - nbm)) : (m >> (nbm - 53));
-    const unsigned long long bits = ((unsigned long long)ef << 52) |
-                                    (mant & 0xFFFFFFFFFFFFFULL) |
-                                    (neg ? 0x8000000000000000ULL : 0ULL);
-    return __longlong_as_double((long long)bits);
+  return assemble_m(m, e, neg);
+}
+
+// t 2^e rounded to nearest (ties to even), t nonzero and below 2^63, sticky:
+// nonzero bits below t's lowest bit were dropped (never on a tie then)
+__host__ __device__ __forceinline__ double round_u64(unsigned long long t, bool sticky, int e,
+                                                     bool neg) {
+  const int nb = 64 - clz64(t);
+  unsigned long long m = t;
+  if (nb > 53) {
+    const int sh = nb - 53;
+    const unsigned long long half = 1ULL << (sh - 1);
+    const unsigned long long rem = t & ((1ULL << sh) - 1);
+    m = t >> sh;
+    if (rem > half || (rem == half && (sticky || (m & 1)))) m += 1;
+    e += sh;
   }
-  // outside the normal range, with integer operations only (no FP64 unit):
-  // overflow to infinity; below 2^-1022 the 53-bit mantissa is shifted into
-  // the subnormal field (truncated: such values are far below any result here)
-  const unsigned long long sgn = neg ? 0x8000000000000000ULL : 0ULL;
-  if (ef > 2046) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ULL));
-  const unsigned long long mant = nbm <= 53 ? (m << (53 - nbm)) : (m >> (nbm - 53));
-  const int sh = 1 - ef;
-  return __longlong_as_double((long long)(sgn | (sh < 64 ? (mant >> sh) : 0ULL)));
+  return assemble_m(m, e, neg);
+}
+
+// The same rounding of (hi 2^24 + lo) 2^e2 as round_i128, for the two exact
+// sums of the tile products (|hi|, |lo| < 2^62), with 64-bit operations only:
+// hi 2^24 + lo = s 2^24 + l, s = hi + floor(lo / 2^24), 0 <= l < 2^24; when
+// |s| < 2^39 the value is a 63-bit integer, else its top 63 bits are kept and
+// the rest of l folded into a sticky bit (the rounding position is then at
+// bit 10 or above, so no tie is lost).
+__host__ __device__ __forceinline__ double round_hl(long long hi, long long lo, int e2) {
+  const long long s1 = hi + (lo >> 24);  // arithmetic shift: floor
+  unsigned long long l0 = (unsigned long long)lo & 0xFFFFFFULL;
+  const bool neg = s1 < 0;
+  unsigned long long m1 = (unsigned long long)s1;
+  if (neg) {  // |value| = (-s1) 2^24 - l0
+    m1 = 0ULL - m1;
+    if (l0) {
+      m1 -= 1;
+      l0 = (1ULL << 24) - l0;
+    }
+  }
+  if (m1 < (1ULL << 39)) {  // |value| = m1 2^24 + l0 < 2^63
+    const unsigned long long t = (m1 << 24) | l0;
+    return t ? round_u64(t, false, e2, neg) : 0.0;
+  }
+  const int k = (64 - clz64(m1)) - 39;  // 1 .. 23: keep the top 63 bits
+  const unsigned long long t = (m1 << (24 - k)) | (l0 >> k);
+  return round_u64(t, (l0 & ((1ULL << k) - 1)) != 0, e2 + k, neg);
 }
 
 // s 2^k z as an exact multiple of 2^e (z double, s = +-1): false when z is not
@@ -191,8 +254,9 @@ __device__ __forceinline__ bool to_fixed(double z, int k, bool neg, int e, __int
 }
 
 // round-to-nearest double of (hi 2^24 + lo) 2^e2, hi and lo exact integers
-__device__ __forceinline__ double combine_scaled(long long hi, long long lo, int e2) {
-  return round_i128(((__int128)hi << 24) + (__int128)lo, e2);
+// (|hi|, |lo| < 2^62)
+__host__ __device__ __forceinline__ double combine_scaled(long long hi, long long lo, int e2) {
+  return round_hl(hi, lo, e2);
 }
 
 
