@@ -45,10 +45,12 @@ def load_peaks():
         return {}
 
 
-# DRAM bytes (read + write) per launch of the persistent kernel on the full
-# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
-# None until captured for the current kernel.
-TRAFFIC = {"mixed": None, "fp64": None, "grid": None}
+# DRAM bytes (read + write) of the dominant kernel on the full workload, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); None until
+# captured for the current kernel.  "grid": the 21 tile launches of one step,
+# captured on the 1024-matrix batch (17.38 GB) and scaled by the entries of
+# the 4096-matrix batch (sum of d^2, x3.92), profiles/oz_tiles_dram_batch1024.md.
+TRAFFIC = {"mixed": None, "fp64": None, "grid": 68.15e9}
 
 
 class Clocks:
@@ -963,6 +965,7 @@ def main():
         roofline = {"bound": "tensor", "kernel": "oz_tiles", "pipe": "tensor_bf16",
                     "achieved": ach, "peak": pk[0], "peak_source": pk[1], "unit": "TFLOP/s",
                     "frac": ach / pk[0], "traffic": TRAFFIC.get("grid") if BATCH == 4096 and not args.dims else None,
+                    "traffic_unit": "bytes per step (the tile launches of one call)",
                     "flops_per_step": alg, "flops_count": "(8/3 k + 2 s) d^3 per matrix, k = 8, "
                                                           "over the matrices on the grid path",
                     "kernel_ms_per_step": st["tile_ms"], "step_achieved": step_ach,
