@@ -412,7 +412,8 @@ constexpr uint32_t GXST = oz::S * GXB;           // 28672
 constexpr uint32_t GYST = oz::S * GYB;           // 14336
 constexpr uint32_t GST = GXST + GYST;            // 43008
 constexpr uint32_t GSMEM = GNST * GST;           // 172032
-constexpr int GTHREADS = NT + 32;                // 8 readout warps + 1 producer / MMA warp
+constexpr int GRW = 16;                          // readout warps: 4 per TMEM lane quarter
+constexpr int GTHREADS = GRW * 32 + 32;          // readout warps + 1 producer / MMA warp
 
 __device__ __forceinline__ uint32_t plane_off16(int r, int k) {
   return (uint32_t)(((r >> 3) * (GKC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
@@ -560,12 +561,12 @@ __global__ void split_cols(int K, int N, const T* Y, int ldy, const unsigned lon
 // accumulators adjacent in TMEM, so one MMA of N = 64 (8 - p) (split at 256)
 // covers them: 10 MMAs per K step.
 //
-// Warps 0-7 read the accumulators after each group (warp w: TMEM lanes
-// 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31 of every accumulator) into
-// two exact 64-bit sums per output; warp 8 lane 0 keeps a ring of 4 stages
+// Warps 0-15 read the accumulators after each group (warp w: TMEM lanes
+// 32 (w % 4) .. + 31, columns 16 (w / 4) .. + 15 of every accumulator) into
+// two exact 64-bit sums per output; warp 16 lane 0 keeps a ring of 4 stages
 // filled by bulk copies and issues the MMAs.  mbarriers: full[s] (copies
 // landed), empty[s] (the stage's MMAs finished), accf (a group's MMAs
-// finished), accr (the 8 readout warps released the accumulators).
+// finished), accr (the 16 readout warps released the accumulators).
 // One matrix of a batch on the tensor-core product path: its geometry and
 // where its data sits in the batch-wide buffers.
 struct BMat {
@@ -670,9 +671,9 @@ __device__ __forceinline__ TileGeo tile_geo(const OzTiles& a, int idx) {
 }
 
 // Persistent: CTA i takes work items i, i + gridDim.x, ... (largest first when
-// the host sorts them).  Warp 8 lane 0 walks the items' K chunks with two
+// the host sorts them).  Warp 16 lane 0 walks the items' K chunks with two
 // cursors, one issuing bulk copies up to GNST chunks ahead (across item
-// boundaries) and one issuing the MMAs; warps 0-7 read the accumulators after
+// boundaries) and one issuing the MMAs; warps 0-15 read the accumulators after
 // every group and write an item's sums after its last group.
 static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
   extern __shared__ unsigned char dsm[];
@@ -691,7 +692,7 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
       tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(&accf, 1);
-    tc::mbar_init(&accr, NT / 32);
+    tc::mbar_init(&accr, GRW);
     tc::mbar_fence_init();
     s_err = 0;
   }
@@ -701,7 +702,7 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
   tc::fence_after();
   const uint32_t tmem = tslot;
 
-  if (warp == NT / 32) {
+  if (warp == GRW) {
     // ---- producer and MMA issuer (one thread) ----
     if (lane == 0) {
       int err = 0;
@@ -796,7 +797,7 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
     }
   } else {
     // ---- readout warps ----
-    const int colh = 32 * (warp >> 2);
+    const int colh = 16 * (warp >> 2);  // 16 of the tile's 64 columns per warp
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     bool ok = true;
     long long g = 0;  // groups read
@@ -809,9 +810,9 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
         atomicAdd(a.flops, f);
         if (a.dflops) atomicAdd(a.dflops, f * (Lm - 1) * Lm / 2);
       }
-      long long ahi[32], alo[32];
+      long long ahi[16], alo[16];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) ahi[j] = alo[j] = 0;
+      for (int j = 0; j < 16; ++j) ahi[j] = alo[j] = 0;
       const int ng = (G.c1 - G.c0 + GSTEPS - 1) / GSTEPS;
       for (int gg = 0; gg < ng; ++gg, ++g) {
         if (!tc::mbar_wait(&accf, (uint32_t)(g & 1), oz::WAIT)) {
@@ -826,17 +827,14 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
           // FP32 -> int32 conversion (the 64-bit one runs on the FP64 unit)
           const int L = q + 2;
           const float sc = __int_as_float((127 + 8 * L) << 23);  // 2^(8L)
+          uint32_t r[16];
+          tc::tmem_ld16(tmem + lane_base + q * oz::TN + colh, r);
+          tc::tmem_ld_wait();
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t r[16];
-            tc::tmem_ld16(tmem + lane_base + q * oz::TN + colh + 16 * h, r);
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const long long k = __float2int_rz(__uint_as_float(r[j]) * sc);
-              if (q < 4) ahi[16 * h + j] += k << (40 - 8 * L);   // 2^-40 units
-              else alo[16 * h + j] += k << (64 - 8 * L);         // 2^-64 units
-            }
+          for (int j = 0; j < 16; ++j) {
+            const long long k = __float2int_rz(__uint_as_float(r[j]) * sc);
+            if (q < 4) ahi[j] += k << (40 - 8 * L);   // 2^-40 units
+            else alo[j] += k << (64 - 8 * L);         // 2^-64 units
           }
         }
         tc::fence_before();
@@ -853,12 +851,12 @@ static __global__ void __launch_bounds__(GTHREADS, 1) oz_tiles(OzTiles a) {
         const int col0 = G.nt * oz::TN + colh;
         if (row < G.dm) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
+          for (int j = 0; j < 16; ++j)
             if (col0 + j < G.dm) *(ulonglong2*)(dst + 2 * j) = make_ulonglong2(ahi[j], alo[j]);
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < 16; ++j) {
           if (ahi[j]) atomicAdd(dst + 2 * j, (unsigned long long)ahi[j]);
           if (alo[j]) atomicAdd(dst + 2 * j + 1, (unsigned long long)alo[j]);
         }

@@ -87,23 +87,17 @@ __device__ __forceinline__ uint32_t plane_off(int r, int k) {
   return (uint32_t)(((r >> 3) * (KC / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// q = round(|x| 2^(56 - e)) for |x| < 2^e (so q <= 2^56), 0 for a zero or
-// subnormal x, from the bits of x; selects only, no branch on the value
-__host__ __device__ __forceinline__ long long digit_q(long long bits, int e) {
-  const int E = (int)((bits >> 52) & 0x7FF);
-  const long long mant = E ? ((bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL) : 0LL;
-  const int sh = E - 1019 - e;  // |x| 2^(56 - e) = mant 2^sh
-  const int ls = sh > 0 ? sh : 0;
-  const int rs = sh < 0 ? (sh > -63 ? -sh : 63) : 0;
-  const long long rnd = rs ? (1LL << (rs - 1)) : 0LL;
-  const long long q = ((mant << ls) + rnd) >> rs;
-  return sh > -63 ? q : 0LL;
-}
-
 // The 7 digits of x * 2^-e (|x| < 2^e), as BF16 values d_p 2^(-8p).
 __device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out) {
   const long long bits = __double_as_longlong(x);
-  const long long q = digit_q(bits, e);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long q = 0;
+  if (E != 0) {  // zero or subnormal: all digits 0
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+    const int sh = E - 1019 - e;  // q = round(|x| 2^(56 - e))
+    if (sh >= 0) q = mant << sh;
+    else if (sh > -63) q = (mant + (1LL << (-sh - 1))) >> (-sh);
+  }
   const bool neg = bits < 0;
   // signed digits from the bytes of q (lowest first): a byte plus the carry
   // of 128 or more becomes byte - 256 and carries one into the next byte;
@@ -189,34 +183,48 @@ __host__ __device__ __forceinline__ double round_i128(__int128 v, int e2) {
   return assemble_m(m, e, neg);
 }
 
+// t 2^e rounded to nearest (ties to even), t nonzero and below 2^63, sticky:
+// nonzero bits below t's lowest bit were dropped (never on a tie then)
+__host__ __device__ __forceinline__ double round_u64(unsigned long long t, bool sticky, int e,
+                                                     bool neg) {
+  const int nb = 64 - clz64(t);
+  unsigned long long m = t;
+  if (nb > 53) {
+    const int sh = nb - 53;
+    const unsigned long long half = 1ULL << (sh - 1);
+    const unsigned long long rem = t & ((1ULL << sh) - 1);
+    m = t >> sh;
+    if (rem > half || (rem == half && (sticky || (m & 1)))) m += 1;
+    e += sh;
+  }
+  return assemble_m(m, e, neg);
+}
+
 // The same rounding of (hi 2^24 + lo) 2^e2 as round_i128, for the two exact
-// sums of the tile products (|hi|, |lo| < 2^62), with 64-bit operations and
-// no data-dependent branch (the lanes of a warp do not diverge on the value):
-// hi 2^24 + lo = s 2^24 + l, s = hi + floor(lo / 2^24), 0 <= l < 2^24;
-// |value| = m 2^24 + l'.  When m < 2^39 that is a 63-bit integer; else its top
-// 63 bits are kept and the rest of l' becomes a sticky bit (the rounding
-// position is then at bit 10 or above, so no tie is lost).
+// sums of the tile products (|hi|, |lo| < 2^62), with 64-bit operations only:
+// hi 2^24 + lo = s 2^24 + l, s = hi + floor(lo / 2^24), 0 <= l < 2^24; when
+// |s| < 2^39 the value is a 63-bit integer, else its top 63 bits are kept and
+// the rest of l folded into a sticky bit (the rounding position is then at
+// bit 10 or above, so no tie is lost).
 __host__ __device__ __forceinline__ double round_hl(long long hi, long long lo, int e2) {
   const long long s1 = hi + (lo >> 24);  // arithmetic shift: floor
-  const unsigned long long lr = (unsigned long long)lo & 0xFFFFFFULL;
+  unsigned long long l0 = (unsigned long long)lo & 0xFFFFFFULL;
   const bool neg = s1 < 0;
-  const unsigned long long ms = neg ? 0ULL - (unsigned long long)s1 : (unsigned long long)s1;
-  const bool borrow = neg && lr != 0;  // (-s) 2^24 - l = (-s - 1) 2^24 + (2^24 - l)
-  const unsigned long long m1 = ms - (borrow ? 1ULL : 0ULL);
-  const unsigned long long l0 = borrow ? (1ULL << 24) - lr : lr;
-  const int bl = 64 - clz64(m1);
-  const int k = bl > 39 ? bl - 39 : 0;  // 0 .. 23
+  unsigned long long m1 = (unsigned long long)s1;
+  if (neg) {  // |value| = (-s1) 2^24 - l0
+    m1 = 0ULL - m1;
+    if (l0) {
+      m1 -= 1;
+      l0 = (1ULL << 24) - l0;
+    }
+  }
+  if (m1 < (1ULL << 39)) {  // |value| = m1 2^24 + l0 < 2^63
+    const unsigned long long t = (m1 << 24) | l0;
+    return t ? round_u64(t, false, e2, neg) : 0.0;
+  }
+  const int k = (64 - clz64(m1)) - 39;  // 1 .. 23: keep the top 63 bits
   const unsigned long long t = (m1 << (24 - k)) | (l0 >> k);
-  const bool sticky = (l0 & ((1ULL << k) - 1)) != 0;
-  // t 2^(e2 + k) rounded to 53 bits, ties to even
-  const int nb = 64 - clz64(t);
-  const int sh = nb > 53 ? nb - 53 : 0;  // 0 .. 10
-  const unsigned long long rem = t & ((1ULL << sh) - 1);
-  const unsigned long long half = (1ULL << sh) >> 1;
-  unsigned long long m = t >> sh;
-  m += (sh > 0 && (rem > half || (rem == half && (sticky || (m & 1))))) ? 1ULL : 0ULL;
-  const double r = assemble_m(m, e2 + k + sh, neg);
-  return t ? r : 0.0;
+  return round_u64(t, (l0 & ((1ULL << k) - 1)) != 0, e2 + k, neg);
 }
 
 // s 2^k z as an exact multiple of 2^e (z double, s = +-1): false when z is not
