@@ -190,7 +190,7 @@ FM_HD size_t fm_align(size_t x) { return (x + 255) & ~(size_t)255; }
 struct WsLayout {
   size_t B, C, Y, F, Phi, T1, T2, B2, LU, RL, piv, D;  // matrix-function part
   size_t Cs, LUs, pivs, Ds, Wc, Wn, U, U2, RHS;    // action part
-  size_t Wst, Yst, Lam, Yt;                        // adjoint part
+  size_t Wst, Yst, LamY, UB;                       // adjoint part
   size_t gx, gy, ex, fy;                           // digit planes (tensor-core products)
   size_t total;
 };
@@ -237,8 +237,10 @@ FM_HD WsLayout ws_layout(int kind, int n, int m, int k, size_t elt, size_t lelt,
     if (kind == JOB_ADJ) {
       L.Wst = take((size_t)(nmax + 1) * n * elt);
       L.Yst = take((size_t)nmax * k * n * elt);
-      L.Lam = take((size_t)n * (k + 1) * elt);
-      L.Yt = take((size_t)n * (k + 1) * elt);
+      // the reverse sweep's c_i lambda_iq (n x kN) and ubar_q (n x N), for the
+      // two products that form Bbar after the sweep
+      L.LamY = take((size_t)n * k * nmax * elt);
+      L.UB = take((size_t)n * nmax * elt);
     }
   }
   if (tc) {

@@ -592,6 +592,55 @@ __device__ __forceinline__ void cta_gemv(int n, const double* M, const double* x
   __syncthreads();
 }
 
+// k stacked products y_i = s_i M_i x (M_i n x n row-major, M_i at M + i n n,
+// y_i at y + i n), one warp per row of the k n stacked rows; a block with
+// s_i = 0 gives y_i = 0 without reading M_i.  y must not alias x.
+__device__ __forceinline__ void cta_gemv_stack(int n, int k, const double* M, const double* x,
+                                               const double* s, double* y) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int r = w; r < k * n; r += NT / 32) {
+    const double si = s[r / n];
+    double acc = 0.0;
+    if (si != 0.0)
+      for (int c = lane; c < n; c += 32) acc = fma(M[(size_t)r * n + c], x[c], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[r] = si * acc;
+  }
+  __syncthreads();
+}
+
+// k stacked transposed products y_i = s_i M_i^T x, one output (i, c) per
+// thread and pass, four outputs per thread in one sweep over the rows (four
+// independent sums); a block with s_i = 0 gives y_i = 0.
+__device__ __forceinline__ void cta_gemv_t_stack(int n, int k, const double* M, const double* x,
+                                                 const double* s, double* y) {
+  const int tot = k * n;
+  for (int o0 = threadIdx.x; o0 < tot; o0 += 4 * NT) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const double* col[4];
+    bool on[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int o = o0 + u * NT;
+      const int i = o < tot ? o / n : 0, c = o < tot ? o % n : 0;
+      on[u] = o < tot && s[i] != 0.0;
+      col[u] = M + (size_t)i * n * n + c;
+    }
+    for (int r = 0; r < n; ++r) {
+      const double xr = x[r];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (on[u]) acc[u] = fma(col[u][(size_t)r * n], xr, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int o = o0 + u * NT;
+      if (o < tot) y[o] = s[o / n] * acc[u];
+    }
+  }
+  __syncthreads();
+}
+
 // y = s M^T x (+ y when accumulate), one thread per column; y must not alias x
 __device__ __forceinline__ void cta_gemv_t(int n, const double* M, const double* x, double s,
                                            double* y, bool accumulate) {
@@ -629,11 +678,10 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
   T* ub = (T*)(ws + L.U2);
   T* wb = (T*)(ws + L.Wc);
   T* wbp = (T*)(ws + L.Wn);
-  T* y = (T*)(ws + L.RHS);
+  T* y = (T*)(ws + L.LUs);    // the reverse products' k n outputs (the factors
+                              // are not used once the inverses are formed)
   T* Wst = (T*)(ws + L.Wst);
   T* Yst = (T*)(ws + L.Yst);
-  T* Lam = (T*)(ws + L.Lam);  // n x (k+1): columns c_i lambda_i, then ubar
-  T* Yt = (T*)(ws + L.Yt);    // (k+1) x n: rows Y_i^T, then w^T
   const T* A = (const T*)J.A + off;
   int info = 0;
   if (N <= 0 || N > J.nsteps_max) info = -3;
@@ -663,66 +711,67 @@ __device__ __noinline__ void run_adjoint(const FmJob& J, const FmCoef& cf, int b
                      n, Inv, n, (T*)smem);
   }
   if (info == 0) {
-    // forward sweep, storing w_q and Y_iq
+    // per-node scales: c_i for the forward products, b_i for the reverse ones
+    // (0 for a zero node, whose inverse is not formed)
+    double* sc = (double*)smem;  // 2 k doubles
+    for (int i = tid; i < k; i += NT) {
+      sc[i] = cf.c_re[i];
+      sc[k + i] = cf.c_re[i] != 0.0 ? cf.b_re[0][i] : 0.0;
+    }
+    // forward sweep, storing w_q and Y_iq: u = B w, every Y_iq = c_i M_i^-1 u
+    // in one stacked product, w_q = a0 w + sum_i b_i Y_iq (ascending i)
     for (int r = tid; r < n; r += NT) Wst[r] = ((const T*)J.V)[vo + r];
     __syncthreads();
+    const T* Inv = (const T*)(ws + L.Cs);
     for (long long q = 1; q <= N; ++q) {
       const T* wp = Wst + (size_t)(q - 1) * n;
       T* wq = Wst + (size_t)q * n;
+      T* yq = Yst + (size_t)(q - 1) * k * n;
       cta_gemv(n, B, wp, 1.0, u);
-      for (int r = tid; r < n; r += NT) wq[r] = TT::rscale(wp[r], cf.a0[0]);
-      __syncthreads();
-      for (int i = 0; i < k; ++i) {
-        T* yi = Yst + ((size_t)(q - 1) * k + i) * n;
-        if (cf.c_re[i] == 0.0) {
-          for (int r = tid; r < n; r += NT) yi[r] = 0.0;
-          __syncthreads();
-          continue;
-        }
-        cta_gemv(n, (const T*)(ws + L.Cs) + (size_t)i * n * n, u, cf.c_re[i], yi);
-        for (int r = tid; r < n; r += NT) wq[r] = TT::add(wq[r], TT::rscale(yi[r], cf.b_re[0][i]));
-        __syncthreads();
+      cta_gemv_stack(n, k, Inv, u, sc, yq);
+      for (int r = tid; r < n; r += NT) {
+        T v = TT::rscale(wp[r], cf.a0[0]);
+        for (int i = 0; i < k; ++i)
+          if (cf.c_re[i] != 0.0) v = TT::add(v, TT::rscale(yq[(size_t)i * n + r], cf.b_re[0][i]));
+        wq[r] = v;
       }
+      __syncthreads();
     }
     for (int r = tid; r < n; r += NT) {
       ((T*)J.W)[vo + r] = Wst[(size_t)N * n + r];
       wb[r] = J.wbar[vo + r];
     }
     __syncthreads();
-    // reverse sweep
+    // reverse sweep: lambda_i = b_i M_i^-T wbar (one stacked product),
+    // ubar = sum_i c_i lambda_i, wbar_{q-1} = a0 wbar + B^T ubar; the terms
+    // of Bbar = sum_q (sum_i c_i lambda_iq Y_iq^T + ubar_q w_{q-1}^T) are kept
+    // (c_i lambda_iq as column (q-1) k + i of LamY, ubar_q as column q-1 of UB)
+    // and summed by two products after the sweep
+    T* LamY = (T*)(ws + L.LamY);
+    T* UB = (T*)(ws + L.UB);
+    const size_t ldl = (size_t)k * N;
     for (long long q = N; q >= 1; --q) {
-      const T* wp = Wst + (size_t)(q - 1) * n;
+      cta_gemv_t_stack(n, k, Inv, wb, sc + k, y);
       for (int r = tid; r < n; r += NT) {
-        wbp[r] = TT::rscale(wb[r], cf.a0[0]);
-        ub[r] = 0.0;
-      }
-      __syncthreads();
-      int kk = 0;
-      for (int i = 0; i < k; ++i) {
-        const double c = cf.c_re[i];
-        if (c == 0.0) continue;
-        const T* yi = Yst + ((size_t)(q - 1) * k + i) * n;
-        cta_gemv_t(n, (const T*)(ws + L.Cs) + (size_t)i * n * n, wb, cf.b_re[0][i], y, false);
-        for (int r = tid; r < n; r += NT) {
-          ub[r] = TT::add(ub[r], TT::rscale(y[r], c));
-          Lam[(size_t)r * (k + 1) + kk] = TT::rscale(y[r], c);
-          Yt[(size_t)kk * n + r] = yi[r];
+        T ubr = 0.0;
+        for (int i = 0; i < k; ++i) {
+          const double c = cf.c_re[i];
+          const T l = c != 0.0 ? TT::rscale(y[(size_t)i * n + r], c) : 0.0;
+          LamY[(size_t)r * ldl + (size_t)(q - 1) * k + i] = l;
+          ubr = TT::add(ubr, l);
         }
-        __syncthreads();
-        ++kk;
-      }
-      for (int r = tid; r < n; r += NT) {
-        Lam[(size_t)r * (k + 1) + kk] = ub[r];
-        Yt[(size_t)kk * n + r] = wp[r];
+        ub[r] = ubr;
+        UB[(size_t)r * N + (q - 1)] = ubr;
+        wbp[r] = TT::rscale(wb[r], cf.a0[0]);
       }
       __syncthreads();
-      // Bbar += [c_i lambda_i, ubar] [Y_i^T; w^T]
-      cta_gemm<T>(n, n, kk + 1, 1.0, Lam, k + 1, Yt, n, 1.0, Cb, n, (T*)(smem + 256));
-      // wbar_{q-1} += B^T ubar
       cta_gemv_t(n, B, ub, 1.0, wbp, true);
       for (int r = tid; r < n; r += NT) wb[r] = wbp[r];
       __syncthreads();
     }
+    // Bbar = LamY Yst + UB Wst (rows 0..N-1 of Wst are w_0 .. w_{N-1})
+    cta_gemm<T>(n, n, (int)(k * N), 1.0, LamY, (int)ldl, Yst, n, 0.0, Cb, n, (T*)(smem + 256));
+    cta_gemm<T>(n, n, (int)N, 1.0, UB, (int)N, Wst, n, 1.0, Cb, n, (T*)(smem + 256));
     for (int e = tid; e < n * n; e += NT) J.Abar[off + e] = TT::rscale(Cb[e], h);
     for (int r = tid; r < n; r += NT) J.vbar[vo + r] = wb[r];
   }
