@@ -54,18 +54,19 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
   T* Bb = B + M.off;
   const double tb = t[blockIdx.x];
   int bad = !isfinite(tb);
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const T a = Ab[e];
-    bad |= !Tr<T>::finite(a);
-    Bb[e] = Tr<T>::rscale(a, tb);
-  }
-  bad = __syncthreads_or(bad);
+  // eta = ||fl(t A)||_1 from A itself: column sums of |fl(t a)|, rows
+  // ascending (the order of the one-CTA kernels), with the finiteness check
   double cmax = 0;
   for (int c = tid; c < n; c += blockDim.x) {
     double sc = 0;
-    for (int r = 0; r < n; ++r) sc += Tr<T>::mag(Bb[(size_t)r * n + c]);
+    for (int r = 0; r < n; ++r) {
+      const T a = Ab[(size_t)r * n + c];
+      bad |= !Tr<T>::finite(a);
+      sc += Tr<T>::mag(Tr<T>::rscale(a, tb));
+    }
     cmax = (sc > cmax || isnan(sc)) ? sc : cmax;
   }
+  bad = __syncthreads_or(bad);
   cmax = block_max(cmax, red);
   const double eta = anorm > 0 ? anorm * fabs(tb) : cmax;
   int s = s_fixed;
@@ -75,10 +76,11 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
     s = 0;
     while (eta > ldexp(theta, s) && s < 1023) ++s;
   }
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const T v = Bb[e];
-    Bb[e] = El<T>::make(ldexp(El<T>::re(v), -s), ldexp(El<T>::im(v), -s));
-  }
+  // B = fl(t A) 2^-s, written once (the power of two is exact, so the product
+  // is the same correctly rounded value as ldexp gives)
+  const double p2 = ldexp(1.0, -s);
+  for (int e = tid; e < n * n; e += blockDim.x)
+    Bb[e] = Tr<T>::rscale(Tr<T>::rscale(Ab[e], tb), p2);
   if (tid == 0) {
     if (s_out) s_out[blockIdx.x] = s;
     info[blockIdx.x] = bad ? -2 : ((s_fixed == kSRfun && !(eta <= theta)) ? -5 : 0);
@@ -452,9 +454,13 @@ __device__ __forceinline__ unsigned long long epi_row(const EpiModes& e, const l
 template <class T>
 __global__ void b_epilogue(const BMat* mats, const int* mask, const long long* acc,
                            const int* exs, const int* fy, EpiModes e, T* out,
-                           unsigned long long* emax, unsigned char* px, int* ex) {
+                           unsigned long long* emax, unsigned char* px, int* ex,
+                           const int* sneed = nullptr, int qneed = 0) {
   __shared__ int s_e[RB];
   if (!mask[blockIdx.x]) return;
+  // sneed (nullable): the planes only for matrices with sneed[b] > qneed (a
+  // squaring that is not the matrix's last)
+  if (sneed && sneed[blockIdx.x] <= qneed) px = nullptr;
   const BMat M = mats[blockIdx.x];
   const int n = M.d;
   const int r0 = blockIdx.y * RB;

@@ -231,7 +231,7 @@ class BRunner {
   void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp,
             const grid::Epi& e, T* out, const int* mask, unsigned long long* emax,
             int lmax = 8, unsigned char* px_next = nullptr, int* ex_next = nullptr,
-            bool split_y = true) {
+            bool split_y = true, int q_next = -1) {
     if (err_ != cudaSuccess) return;
     const int batch = j_.batch;
     const int parts = grid::El<T>::parts;
@@ -271,8 +271,10 @@ class BRunner {
     timer_.stop(st_);
     check("tensor-core products");
     if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
+    // q_next >= 0: a squaring; its row planes serve only matrices with s > q_next
     grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy_, grid::epi_modes(e), out,
-                                             emax, px_next, ex_next);
+                                             emax, px_next, ex_next,
+                                             q_next >= 0 ? s_ : nullptr, q_next);
     check("product epilogue");
     ++products_;
   }
@@ -463,7 +465,7 @@ int BRunner<T>::run() {
       e.ar = 2.0;
       e.Z1 = E_;
       e.b1r = 4.0;
-      prod(E_, pxG_, exG_, false, E_, e, E_, mask_s_, nullptr, 8, pxG_, exG_);
+      prod(E_, pxG_, exG_, false, E_, e, E_, mask_s_, nullptr, 8, pxG_, exG_, true, q + 1);
       continue;
     }
     if (phi) {
@@ -481,7 +483,7 @@ int BRunner<T>::run() {
     e.Z1 = E_;
     e.b1r = 2.0;
     // (after the first squaring the row planes of E come from the last epilogue)
-    prod(E_, pxG_, exG_, q == 0 && !phi, E_, e, E_, mask_s_, nullptr, 8, pxG_, exG_);
+    prod(E_, pxG_, exG_, q == 0 && !phi, E_, e, E_, mask_s_, nullptr, 8, pxG_, exG_, true, q + 1);
   }
   if (j.kind == JOB_EXPM) {
     grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, E_, 1.0, (T*)j.F, 1);
