@@ -130,6 +130,27 @@ __global__ void b_build_shift2(const BMat* mats, const int* mask, const T* B, do
   }
 }
 
+// The first correction step of a system C = u B^2 (u real: a fused +-c pair,
+// u = c^2) from powers of B shared by every such system.  From Y = C the
+// residual C Y + C - Y is u^2 B^4 and the update E Y + Y + E is
+// u^3 B^6 + u B^2 + u^2 B^4 (the same iterate, in the update's order of
+// additions).  Y for every live matrix; C = u B^2 only where cont[b] (the
+// matrices that go on correcting).
+template <class T>
+__global__ void b_pair_first(const BMat* mats, const int* mask, const int* cont, double u,
+                             double u2, double u3, const T* B2, const T* B4, const T* B6, T* C,
+                             T* Y) {
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+  const bool wc = cont[blockIdx.x] != 0;
+#pragma unroll 4
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const T c = Tr<T>::rscale(B2[M.off + e], u);
+    const T p = Tr<T>::rscale(B6[M.off + e], u3);
+    Y[M.off + e] = Tr<T>::add(Tr<T>::add(p, c), Tr<T>::rscale(B4[M.off + e], u2));
+    if (wc) C[M.off + e] = c;
+  }
+}
+
 // F = base I
 template <class T>
 __global__ void b_init_f(const BMat* mats, const int* mask, double base, T* F) {
@@ -564,6 +585,16 @@ __global__ void b_apply(const BMat* mats, const int* mask, const T* Psi, const T
     for (int q = 0; q < n; ++q) Tr<T>::mac(acc, Pb[(size_t)r * n + q], Vb[(size_t)q * m + c]);
     Wb[(size_t)r * m + c] = acc;
   }
+}
+
+// dst[b] = the bits of src[b] sc (live matrices; 0 for the others): the
+// largest entry of u^2 B^4 from that of B^4 (u real, sc = u^2)
+static __global__ void b_emax_scale(int batch, const int* alive, const unsigned long long* src,
+                                    double sc, unsigned long long* dst) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const double v = __longlong_as_double((long long)src[b]) * sc;
+  dst[b] = alive[b] ? (unsigned long long)__double_as_longlong(v) : 0ULL;
 }
 
 // info[b] = code for every live matrix

@@ -66,8 +66,8 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 }
 
 struct Lay {
-  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, prev, ctr, B, B2, C, Y, E, F, F1,
-      G, pxC, pxG, py, acc, exC, exG, fy, total;
+  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, emax4, prev, ctr, B, B2, B4, B6,
+      C, Y, E, F, F1, G, pxC, pxG, py, acc, exC, exG, fy, total;
 };
 
 Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
@@ -87,10 +87,13 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.mask_s = take((size_t)batch * 4);
   L.sbuf = take((size_t)batch * 4);
   L.emax = take((size_t)batch * 8);
+  L.emax4 = take((size_t)batch * 8);
   L.prev = take((size_t)batch * 8);
   L.ctr = take(64);
   L.B = take((size_t)g.elems * elt);
   L.B2 = take((size_t)g.elems * elt);
+  L.B4 = take((size_t)g.elems * elt);
+  L.B6 = take((size_t)g.elems * elt);
   L.C = take((size_t)g.elems * elt);
   L.Y = take((size_t)g.elems * elt);
   L.E = take((size_t)g.elems * elt);
@@ -138,10 +141,11 @@ class BRunner {
   int4* items_ = nullptr;
   int *alive_ = nullptr, *mask_e_ = nullptr, *mask_u_ = nullptr, *mask_s_ = nullptr, *s_ = nullptr;
   unsigned long long* emax_ = nullptr;
+  unsigned long long* emax4_ = nullptr;  // largest entry of B^4 per matrix (bits)
   double* prev_ = nullptr;
   dim3 gE_, gR_, gC_;  // grids: element slices, row slices, column slices
   Ctr* ctr_ = nullptr;
-  T *B_ = nullptr, *B2_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
+  T *B_ = nullptr, *B2_ = nullptr, *B4_ = nullptr, *B6_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
     *F1_ = nullptr, *G_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
   long long* acc_ = nullptr;  // exact sums of the products, (hi, lo) per entry
@@ -182,18 +186,21 @@ class BRunner {
   // Newton-Schulz step does; in this order both products of a step take Y
   // as the right operand (one column split per step) and E as the left one
   // gets its row planes from its own epilogue.
-  void correct(int dmax, int nb) {
+  // it0 = 1: the first step is done (first_shared) and mask_e holds the
+  // matrices that go on.
+  void correct(int dmax, int nb, int it0 = 0) {
     const int batch = j_.batch;
-    api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
-        "mask copy");
-    for (int it = 0; err_ == cudaSuccess; ++it) {
+    if (it0 == 0)
+      api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
+          "mask copy");
+    for (int it = it0; err_ == cudaSuccess; ++it) {
       api(cudaMemsetAsync(&ctr_->active, 0, 4, st_), "counter reset");
       grid::Epi e1;
       e1.Z1 = C_;
       e1.b1r = 1.0;
       e1.Z2 = Y_;
       e1.b2r = -1.0;
-      prod(C_, pxC_, exC_, it == 0, Y_, e1, E_, mask_e_, emax_, 8, pxG_, exG_);
+      prod(C_, pxC_, exC_, it == it0, Y_, e1, E_, mask_e_, emax_, 8, pxG_, exG_);
       grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, it, j_.max_iters, mask_e_,
                                          mask_u_, j_.info_dev, &ctr_->active, &ctr_->corrections,
                                          &ctr_->emax);
@@ -221,6 +228,31 @@ class BRunner {
       api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
       if (h.active == 0) break;
     }
+  }
+
+  // The first correction step of a system C = u B^2 (u real) from the shared
+  // powers B^4, B^6 (b_pair_first): the residual's largest entry is u^2 times
+  // that of B^4, the step's decisions are those of b_flags at step 0, and Y
+  // is the first iterate.  Returns the number of matrices that go on (their
+  // C is written; mask_e marks them).
+  int first_shared(const Sys& S, int nb) {
+    const int batch = j_.batch;
+    api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
+        "mask copy");
+    api(cudaMemsetAsync(&ctr_->active, 0, 4, st_), "counter reset");
+    const double u = S.u2r, u2 = u * u, u3 = u2 * u;
+    grid::b_emax_scale<<<nb, 256, 0, st_>>>(batch, alive_, emax4_, u2, emax_);
+    check("residual maximum");
+    grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, 0, j_.max_iters, mask_e_,
+                                       mask_u_, j_.info_dev, &ctr_->active, &ctr_->corrections,
+                                       &ctr_->emax);
+    check("correction flags");
+    const Ctr h = read_ctr();
+    grid::b_pair_first<T><<<gE_, NT, 0, st_>>>(mats_, alive_, mask_e_, u, u2, u3, B2_, B4_, B6_,
+                                               C_, Y_);
+    check("first correction");
+    api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
+    return err_ == cudaSuccess ? h.active : 0;
   }
 
   // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
@@ -309,10 +341,13 @@ int BRunner<T>::run() {
   mask_s_ = (int*)(base_ + L_.mask_s);
   s_ = j.s_dev ? j.s_dev : (int*)(base_ + L_.sbuf);
   emax_ = (unsigned long long*)(base_ + L_.emax);
+  emax4_ = (unsigned long long*)(base_ + L_.emax4);
   prev_ = (double*)(base_ + L_.prev);
   ctr_ = (Ctr*)(base_ + L_.ctr);
   B_ = (T*)(base_ + L_.B);
   B2_ = (T*)(base_ + L_.B2);
+  B4_ = (T*)(base_ + L_.B4);
+  B6_ = (T*)(base_ + L_.B6);
   C_ = (T*)(base_ + L_.C);
   Y_ = (T*)(base_ + L_.Y);
   E_ = (T*)(base_ + L_.E);
@@ -399,18 +434,35 @@ int BRunner<T>::run() {
       check("hybrid terms");
     }
 
+  // systems C = u B^2 with u real (the fused +-c pairs) take their first
+  // correction step from B^4 = B^2 B^2 and B^6 = B^4 B^2, formed once
+  auto shared_ok = [](const Sys& S) {
+    return S.quad && S.u1r == 0.0 && S.u1i == 0.0 && S.u2i == 0.0;
+  };
+  int nshared = 0;
+  for (int q = 0; q < nsys; ++q) nshared += shared_ok(sys[q]) ? 1 : 0;
+  if (nshared > 0) {
+    grid::Epi e;
+    prod(B2_, pxG_, exG_, true, B2_, e, B4_, alive_, emax4_, 8, pxG_, exG_);
+    prod(B4_, pxG_, exG_, false, B2_, e, B6_, alive_, nullptr, 8, nullptr, nullptr, false);
+  }
+
   // a3-a6: the shifted systems, ascending first term
   bool pair_seen = false;
   double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
   for (int qs = 0; qs < nsys && err_ == cudaSuccess; ++qs) {
     const Sys& S = sys[qs];
-    if (S.quad)  // C = u1 B + u2 B^2
-      grid::b_build_shift2<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.u1r, S.u1i, B2_, S.u2r,
-                                                   S.u2i, C_, Y_);
-    else
-      grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.cr, S.ci, C_, Y_);
-    check("shift");
-    correct(dmax, nb);  // Y = (I - C)^-1 C
+    if (nshared > 0 && shared_ok(S)) {
+      if (first_shared(S, nb) > 0) correct(dmax, nb, 1);  // Y = (I - C)^-1 C
+    } else {
+      if (S.quad)  // C = u1 B + u2 B^2
+        grid::b_build_shift2<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.u1r, S.u1i, B2_, S.u2r,
+                                                     S.u2i, C_, Y_);
+      else
+        grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.cr, S.ci, C_, Y_);
+      check("shift");
+      correct(dmax, nb);  // Y = (I - C)^-1 C
+    }
     if (err_ != cudaSuccess) break;
     for (int f = 0; f < nf; ++f) {
       T* Ff = f ? F1_ : F_;

@@ -32,7 +32,7 @@ size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 int rnd(int x, int q) { return (x + q - 1) / q * q; }
 
 struct Layout {
-  size_t B, C, Y, E, F0, F1, B2, G, Tm, colsum, misc, rmax, cmax, ex, fy, px, py, acc, total;
+  size_t B, C, Y, E, F0, F1, B2, B4, B6, G, Tm, colsum, misc, rmax, cmax, ex, fy, px, py, acc, total;
   size_t pxs, pys;
 };
 
@@ -58,6 +58,8 @@ Layout layout(int kind, bool cplx, int precision, int d, int m) {
   const bool two = kind == JOB_PHI1 || kind == JOB_PHI1MV || kind == JOB_TRIG;
   L.F1 = take(two ? nn : 0);
   L.B2 = take(nn);
+  L.B4 = take(nn);
+  L.B6 = take(nn);
   L.G = take((two ? 2 : 1) * nn);
   L.Tm = take(precision == 0 ? (size_t)d * w * elt : 0);
   L.colsum = take((size_t)d * 8);
@@ -92,6 +94,7 @@ struct Misc {
   int pad[2];
   double eta;
   unsigned long long emax;
+  unsigned long long emax4;  // largest entry of B^4 (bits)
 };
 
 template <class T>
@@ -111,7 +114,7 @@ class Runner {
   Layout L_;
   char* base_ = nullptr;
   T *B_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F0_ = nullptr, *F1_ = nullptr,
-    *B2_ = nullptr, *G_ = nullptr, *Tm_ = nullptr;
+    *B2_ = nullptr, *B4_ = nullptr, *B6_ = nullptr, *G_ = nullptr, *Tm_ = nullptr;
   double* colsum_ = nullptr;
   Misc* misc_ = nullptr;
   unsigned long long *rmax_ = nullptr, *cmax_ = nullptr;
@@ -298,6 +301,8 @@ int Runner<T>::run() {
   F0_ = (T*)(base_ + L_.F0);
   F1_ = two ? (T*)(base_ + L_.F1) : nullptr;
   B2_ = (T*)(base_ + L_.B2);
+  B4_ = (T*)(base_ + L_.B4);
+  B6_ = (T*)(base_ + L_.B6);
   G_ = (T*)(base_ + L_.G);
   Tm_ = tcp_ ? nullptr : (T*)(base_ + L_.Tm);
   colsum_ = (double*)(base_ + L_.colsum);
@@ -410,20 +415,61 @@ int Runner<T>::run() {
     check("initial combination");
   }
 
+  // systems C = u B^2 with u real (the fused +-c pairs) take their first
+  // correction step from B^4 = B^2 B^2 and B^6 = B^4 B^2, formed once
+  auto shared_ok = [](const Sys& S) {
+    return S.quad && S.u1r == 0.0 && S.u1i == 0.0 && S.u2i == 0.0;
+  };
+  int nshared = 0;
+  for (int q = 0; q < nsys; ++q) nshared += shared_ok(sys[q]) ? 1 : 0;
+  double em4 = 0.0;
+  if (nshared > 0) {
+    memset0(&misc_->emax4, 8, "maximum reset");
+    grid::Epi e4;
+    e4.maxabs = &misc_->emax4;
+    prod(n, n, n, B2_, n, true, B2_, n, e4, B4_, n);
+    grid::Epi e6;
+    prod(n, n, n, B4_, n, true, B2_, n, e6, B6_, n);
+    const Misc h4 = read_misc();
+    memcpy(&em4, &h4.emax4, sizeof em4);
+  }
+
   // a3-a5: every shifted system, ascending first term; a6: F_f += b_i Y_i
   const double stop = ldexp(1.0, -30) / (double)n;
   bool pair_seen = false;
   double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
   for (int qs = 0; qs < nsys && err_ == cudaSuccess; ++qs) {
     const Sys& S = sys[qs];
-    if (S.quad)  // C = u1 B + u2 B^2
-      grid::build_shift2<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, S.u1r, S.u1i, B2_, S.u2r,
-                                                              S.u2i, C_, Y_);
-    else
-      grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, S.cr, S.ci, C_, Y_);
-    check("shift");
     double prev = INFINITY;
-    for (int it = 0;; ++it) {
+    int it0 = 0;
+    bool done = false;
+    if (nshared > 0 && shared_ok(S)) {
+      // step 0 from the shared powers: the residual u^2 B^4, its largest entry
+      // u^2 max|B^4|, the same decisions as below
+      const double u = S.u2r, u2 = u * u, u3 = u2 * u;
+      const double em = em4 * u2;
+      grid::pair_first<T><<<blocks(nn), kThreads, 0, st_>>>(nn, u, u2, u3, B2_, B4_, B6_, C_, Y_);
+      check("first correction");
+      if (em == 0.0) {
+        done = true;
+      } else if (!(em < INFINITY) || g.max_iters <= 0) {
+        if (info == 0) info = -1;
+        done = true;
+      } else {
+        prev = em;
+        if (stats_ && stats_->corrections < 1) stats_->corrections = 1;
+        done = em <= stop;
+        it0 = 1;
+      }
+    } else {
+      if (S.quad)  // C = u1 B + u2 B^2
+        grid::build_shift2<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, S.u1r, S.u1i, B2_, S.u2r,
+                                                                S.u2i, C_, Y_);
+      else
+        grid::build_shift<T><<<blocks(nn), kThreads, 0, st_>>>(nn, B_, S.cr, S.ci, C_, Y_);
+      check("shift");
+    }
+    for (int it = it0; !done; ++it) {
       // E = C Y + C - Y  (= C - (I - C) Y), and its largest entry
       memset0(&misc_->emax, 8, "residual maximum reset");
       grid::Epi e1;

@@ -162,6 +162,22 @@ __global__ void build_shift2(size_t count, const T* B, double u1r, double u1i, c
   }
 }
 
+// The first correction step of a system C = u B^2 (u real) from powers of B
+// shared by every such system: from Y = C the residual is u^2 B^4 and the
+// update E Y + Y + E is u^3 B^6 + u B^2 + u^2 B^4 (in the update's order of
+// additions).  C = u B^2 and Y = that first iterate.
+template <class T>
+__global__ void pair_first(size_t count, double u, double u2, double u3, const T* B2, const T* B4,
+                           const T* B6, T* C, T* Y) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const T c = Tr<T>::rscale(B2[e], u);
+    const T p = Tr<T>::rscale(B6[e], u3);
+    C[e] = c;
+    Y[e] = Tr<T>::add(Tr<T>::add(p, c), Tr<T>::rscale(B4[e], u2));
+  }
+}
+
 // a fused +-c pair with Y = (I - c^2 B^2)^-1 - I: F += s Y and G += a Y
 // (G = a Y for the first pair), s = b+ + b-, a = (b+ - b-) c
 template <class T>
