@@ -50,7 +50,7 @@ def load_peaks():
 # captured for the current kernel.  "grid": the 21 tile launches of one step,
 # captured on the 1024-matrix batch (17.43 GB) and scaled by the entries of
 # the 4096-matrix batch (sum of d^2, x3.92), profiles/oz_tiles_dram_batch1024.md.
-TRAFFIC = {"mixed": None, "fp64": None, "grid": 68.36e9}
+TRAFFIC = {"mixed": None, "fp64": None, "grid": 45.2e9}
 
 
 class Clocks:

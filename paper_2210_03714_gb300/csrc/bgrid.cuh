@@ -54,15 +54,18 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
   T* Bb = B + M.off;
   const double tb = t[blockIdx.x];
   int bad = !isfinite(tb);
-  // eta = ||fl(t A)||_1 from A itself: column sums of |fl(t a)|, rows
-  // ascending (the order of the one-CTA kernels), with the finiteness check
+  // eta = ||fl(t A)||_1: column sums of |fl(t a)|, rows ascending (the order
+  // of the one-CTA kernels), with the finiteness check; fl(t A) goes to B
   double cmax = 0;
   for (int c = tid; c < n; c += blockDim.x) {
     double sc = 0;
+#pragma unroll 8
     for (int r = 0; r < n; ++r) {
       const T a = Ab[(size_t)r * n + c];
       bad |= !Tr<T>::finite(a);
-      sc += Tr<T>::mag(Tr<T>::rscale(a, tb));
+      const T v = Tr<T>::rscale(a, tb);
+      Bb[(size_t)r * n + c] = v;
+      sc += Tr<T>::mag(v);
     }
     cmax = (sc > cmax || isnan(sc)) ? sc : cmax;
   }
@@ -76,11 +79,13 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
     s = 0;
     while (eta > ldexp(theta, s) && s < 1023) ++s;
   }
-  // B = fl(t A) 2^-s, written once (the power of two is exact, so the product
-  // is the same correctly rounded value as ldexp gives)
-  const double p2 = ldexp(1.0, -s);
-  for (int e = tid; e < n * n; e += blockDim.x)
-    Bb[e] = Tr<T>::rscale(Tr<T>::rscale(Ab[e], tb), p2);
+  // B = fl(t A) 2^-s (the power of two is exact, so the product is the same
+  // correctly rounded value as ldexp gives); block_max's barriers order the
+  // column loop's stores before these loads
+  if (s > 0) {
+    const double p2 = ldexp(1.0, -s);
+    for (int e = tid; e < n * n; e += blockDim.x) Bb[e] = Tr<T>::rscale(Bb[e], p2);
+  }
   if (tid == 0) {
     if (s_out) s_out[blockIdx.x] = s;
     info[blockIdx.x] = bad ? -2 : ((s_fixed == kSRfun && !(eta <= theta)) ? -5 : 0);
@@ -148,6 +153,114 @@ __global__ void b_pair_first(const BMat* mats, const int* mask, const int* cont,
     const T p = Tr<T>::rscale(B6[M.off + e], u3);
     Y[M.off + e] = Tr<T>::add(Tr<T>::add(p, c), Tr<T>::rscale(B4[M.off + e], u2));
     if (wc) C[M.off + e] = c;
+  }
+}
+
+// Every system C_q = u_q B^2 (u_q real) of a call at once: the weights of
+// their first iterates (b_pair_first) in both functions.
+struct PairsFirst {
+  int nq;
+  double u[kMaxTerms], u2[kMaxTerms], u3[kMaxTerms];
+  double yr[2][kMaxTerms], yi[2][kMaxTerms], xr[2][kMaxTerms], xi[2][kMaxTerms];
+};
+
+// The step-0 decision of b_flags for every system q of P and every matrix,
+// from the largest entry of u_q^2 B^4 (the first residual): cont[q batch + b]
+// = 1 when system q of matrix b goes on correcting; active[q] counts them.
+// A non-finite residual sets info -1 (the matrix stops, as in b_flags).
+static __global__ void b_flags0_shared(int batch, const BMat* mats, const int* alive,
+                                       const unsigned long long* emax4, PairsFirst P,
+                                       int max_iters, int* cont, int* info, int* active,
+                                       int* corrections) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const double e4 = __longlong_as_double((long long)emax4[b]);
+  for (int q = 0; q < P.nq; ++q) {
+    int c = 0;
+    if (alive[b]) {
+      const double em = e4 * P.u2[q];
+      if (em == 0.0) {
+      } else if (!(em < INFINITY) || max_iters <= 0) {
+        if (info[b] == 0) info[b] = -1;
+      } else {
+        atomicMax(corrections, 1);
+        c = !(em * mats[b].d <= 9.313225746154785e-10 /* 2^-30 */);
+      }
+    }
+    cont[(size_t)q * batch + b] = c;
+    if (c) atomicAdd(active + q, 1);
+  }
+}
+
+// acc + (ar + i ai) z with fused multiply-adds (real: ar z + acc)
+template <class T> __device__ __forceinline__ T caxpy(T acc, double ar, double ai, T z);
+template <> __device__ __forceinline__ double caxpy<double>(double acc, double ar, double,
+                                                            double z) {
+  return fma(ar, z, acc);
+}
+template <> __device__ __forceinline__ zd caxpy<zd>(zd acc, double ar, double ai, zd z) {
+  return zd{fma(ar, z.x, fma(-ai, z.y, acc.x)), fma(ar, z.y, fma(ai, z.x, acc.y))};
+}
+
+// One pass for the systems of P that a matrix finishes at step 0 (cont = 0).
+// Their first iterates Y_q = u_q B^2 + u_q^2 B^4 + u_q^3 B^6 (b_pair_first)
+// enter F_f += sum_q y_qf Y_q and G_f = sum_q x_qf Y_q (b_pair_acc) as
+// polynomials in B^2: F_f += a1 B^2 + a2 B^4 + a3 B^6 with a_k = sum_q y_qf u_q^k
+// over the finished systems (likewise G_f with x_qf), formed once per matrix.
+// Each Y_q is never stored, and an entry costs three fused multiply-adds per
+// sum instead of nine operations per system (FP64 issue is the limit of
+// these passes on GB300).  init: F_f starts from base_f I (no hybrid terms)
+// instead of being read.  G_f is written for every live matrix (zero when no
+// system finished), so the systems that go on correcting add to it later.
+template <class T>
+__global__ void b_pairs_shared(const BMat* mats, const int* mask, const int* cont, int batch,
+                               PairsFirst P, int nf, int init, double base0, double base1,
+                               const T* B2, const T* B4, const T* B6, T* F, T* F1, T* G, T* G1) {
+  __shared__ double cf[2][2][3][2];  // [function][F, G][power of B^2][re, im]
+  FM_SLICE(M, (size_t)mats[blockIdx.x].d * mats[blockIdx.x].d)
+  if (threadIdx.x == 0) {
+    for (int f = 0; f < 2; ++f)
+      for (int w = 0; w < 2; ++w)
+        for (int k = 0; k < 3; ++k) cf[f][w][k][0] = cf[f][w][k][1] = 0.0;
+    for (int q = 0; q < P.nq; ++q) {
+      if (cont[(size_t)q * batch + blockIdx.x]) continue;
+      const double uk[3] = {P.u[q], P.u2[q], P.u3[q]};
+      for (int f = 0; f < nf; ++f)
+        for (int k = 0; k < 3; ++k) {
+          cf[f][0][k][0] += P.yr[f][q] * uk[k];
+          cf[f][0][k][1] += P.yi[f][q] * uk[k];
+          cf[f][1][k][0] += P.xr[f][q] * uk[k];
+          cf[f][1][k][1] += P.xi[f][q] * uk[k];
+        }
+    }
+  }
+  __syncthreads();
+  const int n = M.d;
+  const double c00 = cf[0][0][0][0], c01 = cf[0][0][1][0], c02 = cf[0][0][2][0];
+  const double g00 = cf[0][1][0][0], g01 = cf[0][1][1][0], g02 = cf[0][1][2][0];
+  const double c00i = cf[0][0][0][1], c01i = cf[0][0][1][1], c02i = cf[0][0][2][1];
+  const double g00i = cf[0][1][0][1], g01i = cf[0][1][1][1], g02i = cf[0][1][2][1];
+  for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const size_t i = M.off + e;
+    const T b2 = B2[i], b4 = B4[i], b6 = B6[i];
+    const bool dg = e / n == e % n;
+    T f0 = init ? El<T>::make(dg ? base0 : 0.0, 0.0) : F[i];
+    f0 = caxpy<T>(caxpy<T>(caxpy<T>(f0, c02, c02i, b6), c01, c01i, b4), c00, c00i, b2);
+    T g0 = cmul<T>(g02, g02i, b6);
+    g0 = caxpy<T>(caxpy<T>(g0, g01, g01i, b4), g00, g00i, b2);
+    F[i] = f0;
+    G[i] = g0;
+    if (nf == 2) {
+      T f1 = init ? El<T>::make(dg ? base1 : 0.0, 0.0) : F1[i];
+      f1 = caxpy<T>(caxpy<T>(caxpy<T>(f1, cf[1][0][2][0], cf[1][0][2][1], b6), cf[1][0][1][0],
+                             cf[1][0][1][1], b4),
+                    cf[1][0][0][0], cf[1][0][0][1], b2);
+      T g1 = cmul<T>(cf[1][1][2][0], cf[1][1][2][1], b6);
+      g1 = caxpy<T>(caxpy<T>(g1, cf[1][1][1][0], cf[1][1][1][1], b4), cf[1][1][0][0],
+                    cf[1][1][0][1], b2);
+      F1[i] = f1;
+      G1[i] = g1;
+    }
   }
 }
 
@@ -585,16 +698,6 @@ __global__ void b_apply(const BMat* mats, const int* mask, const T* Psi, const T
     for (int q = 0; q < n; ++q) Tr<T>::mac(acc, Pb[(size_t)r * n + q], Vb[(size_t)q * m + c]);
     Wb[(size_t)r * m + c] = acc;
   }
-}
-
-// dst[b] = the bits of src[b] sc (live matrices; 0 for the others): the
-// largest entry of u^2 B^4 from that of B^4 (u real, sc = u^2)
-static __global__ void b_emax_scale(int batch, const int* alive, const unsigned long long* src,
-                                    double sc, unsigned long long* dst) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= batch) return;
-  const double v = __longlong_as_double((long long)src[b]) * sc;
-  dst[b] = alive[b] ? (unsigned long long)__double_as_longlong(v) : 0ULL;
 }
 
 // info[b] = code for every live matrix

@@ -66,7 +66,8 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 }
 
 struct Lay {
-  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, emax4, prev, ctr, B, B2, B4, B6,
+  size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, emax4, prev, ctr, act, cont, B,
+      B2, B4, B6,
       C, Y, E, F, F1, G, pxC, pxG, py, acc, exC, exG, fy, total;
 };
 
@@ -90,6 +91,8 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.emax4 = take((size_t)batch * 8);
   L.prev = take((size_t)batch * 8);
   L.ctr = take(64);
+  L.act = take((size_t)kMaxTerms * 4);
+  L.cont = take((size_t)kMaxTerms * batch * 4);
   L.B = take((size_t)g.elems * elt);
   L.B2 = take((size_t)g.elems * elt);
   L.B4 = take((size_t)g.elems * elt);
@@ -145,6 +148,8 @@ class BRunner {
   double* prev_ = nullptr;
   dim3 gE_, gR_, gC_;  // grids: element slices, row slices, column slices
   Ctr* ctr_ = nullptr;
+  int* act_ = nullptr;   // per system C = u B^2: matrices that go on after step 0
+  int* cont_ = nullptr;  // per system and matrix: goes on after step 0
   T *B_ = nullptr, *B2_ = nullptr, *B4_ = nullptr, *B6_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
     *F1_ = nullptr, *G_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
@@ -186,8 +191,8 @@ class BRunner {
   // Newton-Schulz step does; in this order both products of a step take Y
   // as the right operand (one column split per step) and E as the left one
   // gets its row planes from its own epilogue.
-  // it0 = 1: the first step is done (first_shared) and mask_e holds the
-  // matrices that go on.
+  // it0 = 1: the first step is done (b_pairs_shared, b_pair_first) and
+  // mask_e holds the matrices that go on.
   void correct(int dmax, int nb, int it0 = 0) {
     const int batch = j_.batch;
     if (it0 == 0)
@@ -228,31 +233,6 @@ class BRunner {
       api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
       if (h.active == 0) break;
     }
-  }
-
-  // The first correction step of a system C = u B^2 (u real) from the shared
-  // powers B^4, B^6 (b_pair_first): the residual's largest entry is u^2 times
-  // that of B^4, the step's decisions are those of b_flags at step 0, and Y
-  // is the first iterate.  Returns the number of matrices that go on (their
-  // C is written; mask_e marks them).
-  int first_shared(const Sys& S, int nb) {
-    const int batch = j_.batch;
-    api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
-        "mask copy");
-    api(cudaMemsetAsync(&ctr_->active, 0, 4, st_), "counter reset");
-    const double u = S.u2r, u2 = u * u, u3 = u2 * u;
-    grid::b_emax_scale<<<nb, 256, 0, st_>>>(batch, alive_, emax4_, u2, emax_);
-    check("residual maximum");
-    grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, 0, j_.max_iters, mask_e_,
-                                       mask_u_, j_.info_dev, &ctr_->active, &ctr_->corrections,
-                                       &ctr_->emax);
-    check("correction flags");
-    const Ctr h = read_ctr();
-    grid::b_pair_first<T><<<gE_, NT, 0, st_>>>(mats_, alive_, mask_e_, u, u2, u3, B2_, B4_, B6_,
-                                               C_, Y_);
-    check("first correction");
-    api(cudaMemsetAsync(&ctr_->emax, 0, 8, st_), "counter reset");
-    return err_ == cudaSuccess ? h.active : 0;
   }
 
   // out = epilogue(X Y) for every matrix with mask[b]; split_x: compute the
@@ -344,6 +324,8 @@ int BRunner<T>::run() {
   emax4_ = (unsigned long long*)(base_ + L_.emax4);
   prev_ = (double*)(base_ + L_.prev);
   ctr_ = (Ctr*)(base_ + L_.ctr);
+  act_ = (int*)(base_ + L_.act);
+  cont_ = (int*)(base_ + L_.cont);
   B_ = (T*)(base_ + L_.B);
   B2_ = (T*)(base_ + L_.B2);
   B4_ = (T*)(base_ + L_.B4);
@@ -417,9 +399,45 @@ int BRunner<T>::run() {
     if (sys[q].quad)  // a quadratic system's g I (plain form) joins the multiple of I
       for (int f = 0; f < nf; ++f) base[f] += sys[q].gr[f];
   }
+  // systems C = u B^2 with u real (the fused +-c pairs) take their first
+  // correction step from B^4 = B^2 B^2 and B^6 = B^4 B^2, formed once: every
+  // such system's step-0 decision in one launch, and the systems a matrix
+  // finishes at step 0 go straight into F and G in one pass (b_pairs_shared)
+  auto shared_ok = [](const Sys& S) {
+    return S.quad && S.u1r == 0.0 && S.u1i == 0.0 && S.u2i == 0.0;
+  };
+  grid::PairsFirst pf;
+  memset(&pf, 0, sizeof pf);
+  int qidx[kMaxTerms];  // system -> its index in pf (-1: not a shared one)
+  for (int q = 0; q < nsys; ++q) {
+    qidx[q] = -1;
+    if (!shared_ok(sys[q])) continue;
+    const int i = pf.nq++;
+    qidx[q] = i;
+    const double u = sys[q].u2r;
+    pf.u[i] = u;
+    pf.u2[i] = u * u;
+    pf.u3[i] = u * u * u;
+    for (int f = 0; f < nf; ++f) {
+      pf.yr[f][i] = sys[q].yr[f];
+      pf.yi[f][i] = sys[q].yi[f];
+      pf.xr[f][i] = sys[q].xr[f];
+      pf.xi[f][i] = sys[q].xi[f];
+    }
+  }
+  bool hybrid = false;
+  for (int f = 0; f < nf; ++f) hybrid |= cf.d1[f] != 0 || cf.d2[f] != 0;
+  // a7 works in the deviation from the identity (E = F - I; Psi = F1 - I for
+  // phi_1; X = C - I and S itself for cos and sin): the combination starts
+  // from (base - 1) I for those, so it ends in the deviation (every later
+  // term is added to it) and no subtraction of I is needed
+  const double base_dev[2] = {base[0] - 1.0, phi ? base[1] - 1.0 : base[1]};
+  // F_f = base_f I is written by the shared systems' pass when there are
+  // such systems and no hybrid terms
+  const bool f_in_pairs = pf.nq > 0 && !hybrid;
   // a6 (first part): F_f = base_f I + d1 B + d2 B^2 for each function
-  for (int f = 0; f < nf; ++f) {
-    grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base[f], f ? F1_ : F_);
+  for (int f = 0; f < nf && !f_in_pairs; ++f) {
+    grid::b_init_f<T><<<gE_, NT, 0, st_>>>(mats_, alive_, base_dev[f], f ? F1_ : F_);
     check("initial combination");
   }
   const bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0) || any_quad;
@@ -434,35 +452,62 @@ int BRunner<T>::run() {
       check("hybrid terms");
     }
 
-  // systems C = u B^2 with u real (the fused +-c pairs) take their first
-  // correction step from B^4 = B^2 B^2 and B^6 = B^4 B^2, formed once
-  auto shared_ok = [](const Sys& S) {
-    return S.quad && S.u1r == 0.0 && S.u1i == 0.0 && S.u2i == 0.0;
-  };
-  int nshared = 0;
-  for (int q = 0; q < nsys; ++q) nshared += shared_ok(sys[q]) ? 1 : 0;
-  if (nshared > 0) {
+  bool pair_seen = false;
+  double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
+  int act_host[kMaxTerms] = {};
+  if (pf.nq > 0) {
     grid::Epi e;
     prod(B2_, pxG_, exG_, true, B2_, e, B4_, alive_, emax4_, 8, pxG_, exG_);
     prod(B4_, pxG_, exG_, false, B2_, e, B6_, alive_, nullptr, 8, nullptr, nullptr, false);
+    api(cudaMemsetAsync(act_, 0, (size_t)kMaxTerms * 4, st_), "counter reset");
+    grid::b_flags0_shared<<<nb, 256, 0, st_>>>(batch, mats_, alive_, emax4_, pf, j_.max_iters,
+                                               cont_, j_.info_dev, act_, &ctr_->corrections);
+    check("correction flags");
+    grid::b_pairs_shared<T><<<gE_, NT, 0, st_>>>(mats_, alive_, cont_, batch, pf, nf,
+                                                  f_in_pairs ? 1 : 0, base_dev[0], base_dev[1], B2_, B4_,
+                                                  B6_, F_, F1_, G_, G_ + (size_t)g_.elems);
+    check("pair combination");
+    api(cudaMemcpyAsync(act_host, act_, (size_t)kMaxTerms * 4, cudaMemcpyDeviceToHost, st_),
+        "reading counters");
+    api(cudaStreamSynchronize(st_), "stream synchronize");
+    pair_seen = true;
+    for (int i = 0; i < pf.nq; ++i)
+      for (int f = 0; f < nf; ++f) {
+        asum_r[f] += pf.xr[f][i];
+        asum_i[f] += pf.xi[f][i];
+      }
   }
 
   // a3-a6: the shifted systems, ascending first term
-  bool pair_seen = false;
-  double asum_r[2] = {0.0, 0.0}, asum_i[2] = {0.0, 0.0};
   for (int qs = 0; qs < nsys && err_ == cudaSuccess; ++qs) {
     const Sys& S = sys[qs];
-    if (nshared > 0 && shared_ok(S)) {
-      if (first_shared(S, nb) > 0) correct(dmax, nb, 1);  // Y = (I - C)^-1 C
-    } else {
-      if (S.quad)  // C = u1 B + u2 B^2
-        grid::b_build_shift2<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.u1r, S.u1i, B2_, S.u2r,
-                                                     S.u2i, C_, Y_);
-      else
-        grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.cr, S.ci, C_, Y_);
-      check("shift");
-      correct(dmax, nb);  // Y = (I - C)^-1 C
+    const int i = qidx[qs];
+    if (i >= 0) {
+      // a shared system: only the matrices that go on after step 0 are left
+      if (act_host[i] == 0) continue;
+      const int* cq = cont_ + (size_t)i * batch;
+      const double u = pf.u[i];
+      api(cudaMemcpyAsync(mask_e_, cq, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
+          "mask copy");
+      grid::b_pair_first<T><<<gE_, NT, 0, st_>>>(mats_, cq, cq, u, pf.u2[i], pf.u3[i], B2_, B4_,
+                                                 B6_, C_, Y_);
+      check("first correction");
+      correct(dmax, nb, 1);  // Y = (I - C)^-1 C
+      if (err_ != cudaSuccess) break;
+      for (int f = 0; f < nf; ++f) {
+        grid::b_pair_acc<T><<<gE_, NT, 0, st_>>>(mats_, cq, S.yr[f], S.yi[f], S.xr[f], S.xi[f],
+                                                  Y_, 0, f ? F1_ : F_, G_ + (size_t)f * g_.elems);
+        check("pair combination");
+      }
+      continue;
     }
+    if (S.quad)  // C = u1 B + u2 B^2
+      grid::b_build_shift2<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.u1r, S.u1i, B2_, S.u2r,
+                                                   S.u2i, C_, Y_);
+    else
+      grid::b_build_shift<T><<<gE_, NT, 0, st_>>>(mats_, alive_, B_, S.cr, S.ci, C_, Y_);
+    check("shift");
+    correct(dmax, nb);  // Y = (I - C)^-1 C
     if (err_ != cudaSuccess) break;
     for (int f = 0; f < nf; ++f) {
       T* Ff = f ? F1_ : F_;
@@ -495,14 +540,9 @@ int BRunner<T>::run() {
   }
   if (err_ != cudaSuccess) return FM_ECUDA;
 
-  // a7 in the deviation from the identity: E = F - I (and Psi = F1 - I; for
-  // cos and sin, X = C - I and S itself)
-  grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F_, -1.0, E_, 0);
-  check("deviation");
-  if (phi) {
-    grid::b_add_identity<T><<<gE_, NT, 0, st_>>>(mats_, alive_, F1_, -1.0, F1_, 0);
-    check("deviation");
-  }
+  // a7 in the deviation from the identity, which F (and F1 for phi_1) hold
+  // already: E takes F's buffer (F is not needed any more)
+  std::swap(E_, F_);
   for (int q = 0; q < s_max; ++q) {
     grid::b_square_mask<<<nb, 256, 0, st_>>>(batch, alive_, s_, q, mask_s_);
     check("squaring mask");
