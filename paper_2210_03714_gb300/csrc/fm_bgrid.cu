@@ -67,7 +67,7 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 
 struct Lay {
   size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, emax4, prev, ctr, act, cont, B,
-      B2, B4, B6,
+      B2, B4, B6, pyB, fyB,
       C, Y, E, F, F1, G, pxC, pxG, py, acc, exC, exG, fy, total;
 };
 
@@ -106,6 +106,8 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.pxC = take((size_t)g.pxb);
   L.pxG = take((size_t)g.pxb);
   L.py = take((size_t)g.pyb);
+  L.pyB = take((size_t)g.pyb);
+  L.fyB = take((size_t)g.cols * 4);
   L.acc = take((size_t)g.accp * 16);
   L.exC = take((size_t)g.rows * 4);
   L.exG = take((size_t)g.rows * 4);
@@ -153,6 +155,8 @@ class BRunner {
   T *B_ = nullptr, *B2_ = nullptr, *B4_ = nullptr, *B6_ = nullptr, *C_ = nullptr, *Y_ = nullptr, *E_ = nullptr, *F_ = nullptr,
     *F1_ = nullptr, *G_ = nullptr;
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
+  unsigned char* pyB_ = nullptr;  // column planes of B (B^2 and every G B)
+  int* fyB_ = nullptr;
   long long* acc_ = nullptr;  // exact sums of the products, (hi, lo) per entry
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
   long long products_ = 0;
@@ -243,8 +247,12 @@ class BRunner {
   void prod(const T* X, unsigned char* px, int* ex, bool split_x, const T* Yp,
             const grid::Epi& e, T* out, const int* mask, unsigned long long* emax,
             int lmax = 8, unsigned char* px_next = nullptr, int* ex_next = nullptr,
-            bool split_y = true, int q_next = -1) {
+            bool split_y = true, int q_next = -1, unsigned char* pyo = nullptr,
+            int* fyo = nullptr) {
     if (err_ != cudaSuccess) return;
+    // pyo, fyo (nullable): column planes of Y kept elsewhere than py_, fy_
+    unsigned char* py = pyo ? pyo : py_;
+    int* fy = fyo ? fyo : fy_;
     const int batch = j_.batch;
     const int parts = grid::El<T>::parts;
     if (split_x) {
@@ -252,13 +260,13 @@ class BRunner {
       check("row digit planes");
     }
     if (split_y) {
-      grid::b_split_cols<T><<<gC_, NT, 0, st_>>>(mats_, mask, Yp, py_, fy_);
+      grid::b_split_cols<T><<<gC_, NT, 0, st_>>>(mats_, mask, Yp, py, fy);
       check("column digit planes");
     }
     grid::OzTiles a;
     memset(&a, 0, sizeof a);
     a.px = px;
-    a.py = py_;
+    a.py = py;
     a.nparts = parts;
     a.nseg = parts;
     if (parts == 2) {
@@ -284,7 +292,7 @@ class BRunner {
     check("tensor-core products");
     if (emax) api(cudaMemsetAsync(emax, 0, (size_t)batch * 8, st_), "maximum reset");
     // q_next >= 0: a squaring; its row planes serve only matrices with s > q_next
-    grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy_, grid::epi_modes(e), out,
+    grid::b_epilogue<T><<<gR_, NT, 0, st_>>>(mats_, mask, acc_, ex, fy, grid::epi_modes(e), out,
                                              emax, px_next, ex_next,
                                              q_next >= 0 ? s_ : nullptr, q_next);
     check("product epilogue");
@@ -339,6 +347,8 @@ int BRunner<T>::run() {
   pxC_ = (unsigned char*)(base_ + L_.pxC);
   pxG_ = (unsigned char*)(base_ + L_.pxG);
   py_ = (unsigned char*)(base_ + L_.py);
+  pyB_ = (unsigned char*)(base_ + L_.pyB);
+  fyB_ = (int*)(base_ + L_.fyB);
   acc_ = (long long*)(base_ + L_.acc);
   exC_ = (int*)(base_ + L_.exC);
   exG_ = (int*)(base_ + L_.exG);
@@ -372,6 +382,7 @@ int BRunner<T>::run() {
   api(cudaMemsetAsync(pxC_, 0, (size_t)g_.pxb, st_), "plane reset");
   api(cudaMemsetAsync(pxG_, 0, (size_t)g_.pxb, st_), "plane reset");
   api(cudaMemsetAsync(py_, 0, (size_t)g_.pyb, st_), "plane reset");
+  api(cudaMemsetAsync(pyB_, 0, (size_t)g_.pyb, st_), "plane reset");
 
   // a1/a2
   grid::b_prologue<T><<<batch, NT, 0, st_>>>(mats_, (const T*)j.A, j.t_dev, B_, j.anorm, cf.theta,
@@ -443,7 +454,8 @@ int BRunner<T>::run() {
   const bool need_b2 = cf.d2[0] != 0 || (two && cf.d2[1] != 0) || any_quad;
   if (need_b2) {
     grid::Epi e;
-    prod(B_, pxG_, exG_, true, B_, e, B2_, alive_, nullptr);
+    prod(B_, pxG_, exG_, true, B_, e, B2_, alive_, nullptr, 8, nullptr, nullptr, true, -1, pyB_,
+         fyB_);
   }
   for (int f = 0; f < nf; ++f)
     if (cf.d1[f] != 0 || cf.d2[f] != 0) {
@@ -458,7 +470,24 @@ int BRunner<T>::run() {
   if (pf.nq > 0) {
     grid::Epi e;
     prod(B2_, pxG_, exG_, true, B2_, e, B4_, alive_, emax4_, 8, pxG_, exG_);
-    prod(B4_, pxG_, exG_, false, B2_, e, B6_, alive_, nullptr, 8, nullptr, nullptr, false);
+    // B^6 enters only as u^3 B^6 beside u B^2: it needs the absolute accuracy
+    // u max|B^2| 2^-53 / u^3, and the digit products' error at level cap L is
+    // about 2^(14 - 8L) 8 sqrt(d) max|B^4| max|B^2|.  With s from ||tA||_1,
+    // max|B^4| <= ||B||_1^4 <= theta^4, so L >= (70 + log2(sqrt(d) u^2 theta^4)) / 8
+    // suffices (the bound the correction update uses, at its a-priori value);
+    // with a caller's norm bound or a forced s, every level is kept.
+    int l6 = 8;
+    if (j_.anorm <= 0 && j_.s_fixed == -1) {
+      double u2max = 0;
+      for (int i = 0; i < pf.nq; ++i) u2max = pf.u2[i] > u2max ? pf.u2[i] : u2max;
+      const double th4 = cf.theta * cf.theta * cf.theta * cf.theta;
+      if (u2max > 0 && th4 > 0) {
+        const double need = 70.0 + 0.5 * log2((double)dmax) + log2(u2max * th4);
+        l6 = (int)ceil(need / 8.0);
+        l6 = l6 < 2 ? 2 : (l6 > 8 ? 8 : l6);
+      }
+    }
+    prod(B4_, pxG_, exG_, false, B2_, e, B6_, alive_, nullptr, l6, nullptr, nullptr, false);
     api(cudaMemsetAsync(act_, 0, (size_t)kMaxTerms * 4, st_), "counter reset");
     grid::b_flags0_shared<<<nb, 256, 0, st_>>>(batch, mats_, alive_, emax4_, pf, j_.max_iters,
                                                cont_, j_.info_dev, act_, &ctr_->corrections);
@@ -536,7 +565,10 @@ int BRunner<T>::run() {
     e.Z2 = B_;
     e.b2r = asum_r[f];
     e.b2i = asum_i[f];
-    prod(G_ + (size_t)f * g_.elems, pxG_, exG_, true, B_, e, Ff, alive_, nullptr);
+    // B's column planes from the B^2 product when it ran (else split here once)
+    const bool have_b = need_b2 || f > 0;
+    prod(G_ + (size_t)f * g_.elems, pxG_, exG_, true, B_, e, Ff, alive_, nullptr, 8, nullptr,
+         nullptr, !have_b, -1, pyB_, fyB_);
   }
   if (err_ != cudaSuccess) return FM_ECUDA;
 
