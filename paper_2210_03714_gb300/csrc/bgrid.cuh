@@ -63,7 +63,7 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
     for (int r = 0; r < n; ++r) {
       const T a = Ab[(size_t)r * n + c];
       bad |= !Tr<T>::finite(a);
-      const T v = Tr<T>::rscale(a, tb);
+      const T v = tb == 1.0 ? a : Tr<T>::rscale(a, tb);  // t = 1: fl(t a) = a
       Bb[(size_t)r * n + c] = v;
       sc += Tr<T>::mag(v);
     }
@@ -624,6 +624,7 @@ __global__ void b_epilogue(const BMat* mats, const int* mask, const long long* a
     switch (key) {
       case 0: mx = FM_EPI_ROW(0, 0, 0); break;      // B^2
       case 12: mx = FM_EPI_ROW(0, 1, 2); break;     // residual C Y + C - Y
+      case 112: mx = FM_EPI_ROW(1, 1, 2); break;    // residual u (B^2 Y) + C - Y
       case 11: mx = FM_EPI_ROW(0, 1, 1); break;     // correction Y + E + E Y
       case 13: mx = FM_EPI_ROW(0, 1, 3); break;     // F + G B + (sum a) B
       case 14: mx = FM_EPI_ROW(0, 1, 4); break;     // the same, complex sum

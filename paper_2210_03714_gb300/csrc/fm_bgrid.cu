@@ -67,7 +67,7 @@ Geo geometry(bool cplx, int batch, const int* d, const int64_t* off, const int64
 
 struct Lay {
   size_t mats, items, alive, mask_e, mask_u, mask_s, sbuf, emax, emax4, prev, ctr, act, cont, B,
-      B2, B4, B6, pyB, fyB,
+      B2, B4, B6, pyB, fyB, pxB2, exB2,
       C, Y, E, F, F1, G, pxC, pxG, py, acc, exC, exG, fy, total;
 };
 
@@ -108,6 +108,8 @@ Lay carve(const Geo& g, bool cplx, int batch, bool phi) {
   L.py = take((size_t)g.pyb);
   L.pyB = take((size_t)g.pyb);
   L.fyB = take((size_t)g.cols * 4);
+  L.pxB2 = take((size_t)g.pxb);
+  L.exB2 = take((size_t)g.rows * 4);
   L.acc = take((size_t)g.accp * 16);
   L.exC = take((size_t)g.rows * 4);
   L.exG = take((size_t)g.rows * 4);
@@ -157,6 +159,8 @@ class BRunner {
   unsigned char *pxC_ = nullptr, *pxG_ = nullptr, *py_ = nullptr;
   unsigned char* pyB_ = nullptr;  // column planes of B (B^2 and every G B)
   int* fyB_ = nullptr;
+  unsigned char* pxB2_ = nullptr;  // row planes of B^2 (B^4, and the residuals of C = u B^2)
+  int* exB2_ = nullptr;
   long long* acc_ = nullptr;  // exact sums of the products, (hi, lo) per entry
   int *exC_ = nullptr, *exG_ = nullptr, *fy_ = nullptr;
   long long products_ = 0;
@@ -197,7 +201,10 @@ class BRunner {
   // gets its row planes from its own epilogue.
   // it0 = 1: the first step is done (b_pairs_shared, b_pair_first) and
   // mask_e holds the matrices that go on.
-  void correct(int dmax, int nb, int it0 = 0) {
+  // ushared != 0: C = ushared B^2 (a shared system), and the residual's
+  // product is ushared (B^2 Y) from B^2's own row planes (pxB2_) instead of
+  // C Y from planes of C (the same product up to the rounding of C).
+  void correct(int dmax, int nb, int it0 = 0, double ushared = 0.0) {
     const int batch = j_.batch;
     if (it0 == 0)
       api(cudaMemcpyAsync(mask_e_, alive_, (size_t)batch * 4, cudaMemcpyDeviceToDevice, st_),
@@ -209,7 +216,12 @@ class BRunner {
       e1.b1r = 1.0;
       e1.Z2 = Y_;
       e1.b2r = -1.0;
-      prod(C_, pxC_, exC_, it == it0, Y_, e1, E_, mask_e_, emax_, 8, pxG_, exG_);
+      if (ushared != 0.0) {
+        e1.ar = ushared;
+        prod(B2_, pxB2_, exB2_, false, Y_, e1, E_, mask_e_, emax_, 8, pxG_, exG_);
+      } else {
+        prod(C_, pxC_, exC_, it == it0, Y_, e1, E_, mask_e_, emax_, 8, pxG_, exG_);
+      }
       grid::b_flags<<<nb, 256, 0, st_>>>(batch, mats_, emax_, prev_, it, j_.max_iters, mask_e_,
                                          mask_u_, j_.info_dev, &ctr_->active, &ctr_->corrections,
                                          &ctr_->emax);
@@ -349,6 +361,8 @@ int BRunner<T>::run() {
   py_ = (unsigned char*)(base_ + L_.py);
   pyB_ = (unsigned char*)(base_ + L_.pyB);
   fyB_ = (int*)(base_ + L_.fyB);
+  pxB2_ = (unsigned char*)(base_ + L_.pxB2);
+  exB2_ = (int*)(base_ + L_.exB2);
   acc_ = (long long*)(base_ + L_.acc);
   exC_ = (int*)(base_ + L_.exC);
   exG_ = (int*)(base_ + L_.exG);
@@ -383,6 +397,7 @@ int BRunner<T>::run() {
   api(cudaMemsetAsync(pxG_, 0, (size_t)g_.pxb, st_), "plane reset");
   api(cudaMemsetAsync(py_, 0, (size_t)g_.pyb, st_), "plane reset");
   api(cudaMemsetAsync(pyB_, 0, (size_t)g_.pyb, st_), "plane reset");
+  api(cudaMemsetAsync(pxB2_, 0, (size_t)g_.pxb, st_), "plane reset");
 
   // a1/a2
   grid::b_prologue<T><<<batch, NT, 0, st_>>>(mats_, (const T*)j.A, j.t_dev, B_, j.anorm, cf.theta,
@@ -469,7 +484,7 @@ int BRunner<T>::run() {
   int act_host[kMaxTerms] = {};
   if (pf.nq > 0) {
     grid::Epi e;
-    prod(B2_, pxG_, exG_, true, B2_, e, B4_, alive_, emax4_, 8, pxG_, exG_);
+    prod(B2_, pxB2_, exB2_, true, B2_, e, B4_, alive_, emax4_, 8, pxG_, exG_);
     // B^6 enters only as u^3 B^6 beside u B^2: it needs the absolute accuracy
     // u max|B^2| 2^-53 / u^3, and the digit products' error at level cap L is
     // about 2^(14 - 8L) 8 sqrt(d) max|B^4| max|B^2|.  With s from ||tA||_1,
@@ -521,7 +536,7 @@ int BRunner<T>::run() {
       grid::b_pair_first<T><<<gE_, NT, 0, st_>>>(mats_, cq, cq, u, pf.u2[i], pf.u3[i], B2_, B4_,
                                                  B6_, C_, Y_);
       check("first correction");
-      correct(dmax, nb, 1);  // Y = (I - C)^-1 C
+      correct(dmax, nb, 1, u);  // Y = (I - C)^-1 C
       if (err_ != cudaSuccess) break;
       for (int f = 0; f < nf; ++f) {
         grid::b_pair_acc<T><<<gE_, NT, 0, st_>>>(mats_, cq, S.yr[f], S.yi[f], S.xr[f], S.xi[f],

@@ -155,3 +155,37 @@ def test_bgrid_phi1_and_action(fm):
         W_ref, _, _ = oracle.phi1mv(M, Vb, t, ce, cp)
         assert relerr(W[o:o + d * m].reshape(d, m), W_ref) <= TOL_FP64
         o += d * m
+
+
+def spread(A, cs, form, F_ref):
+    """Relative difference of two correct double evaluations (the oracle on
+    P A P^T mapped back against the oracle on A): sets whose weights cancel
+    (R10*: sum |b_i c_i| = 1.3e6) and the plain form of Eq. rat1 amplify the
+    rounding of each system by their weights (Sec. 4.3)."""
+    d = A.shape[0]
+    p = np.random.default_rng(5).permutation(d)
+    F2, _, _ = oracle.expm(A[np.ix_(p, p)], 1.0, cs, form)
+    q = np.argsort(p)
+    return relerr(F2[np.ix_(q, q)], F_ref)
+
+
+@pytest.mark.parametrize("name,form", [("R10", "roundoff"), ("R10star", "roundoff"),
+                                       ("R8", "plain"), ("R4", "plain")])
+def test_bgrid_hybrid_and_plain(fm, name, form):
+    """Sets with the hybrid terms d1 B + d2 B^2 (F starts from the multiple of
+    I and those terms before the shifted systems add to it) and the plain
+    form (no pair fusion: one system per node, b (I + Y) added), on ragged
+    orders; the combination ends in the deviation F - I that the squarings
+    take.  Bar: max(1e-12, twice the spread of two correct double
+    evaluations)."""
+    cs = oracle_set(name)
+    fo = oracle.ROUNDOFF if form == "roundoff" else oracle.PLAIN
+    mats = [wl.dense_scaled(d, 2.0 + 0.5 * i, 700 + d) for i, d in enumerate((17, 64, 130))]
+    P = fm.Packed([T(m) for m in mats])
+    F, info, s = fm.expm_batched(P, 1.0, fm.Coeffs(cs), path="grid", form=form)
+    F, info, s = F.cpu().numpy(), info.cpu().numpy(), s.cpu().numpy()
+    for b, M in enumerate(mats):
+        ref, s_ref, _ = oracle.expm(M, 1.0, cs, fo)
+        assert info[b] == 0 and s[b] == s_ref
+        bar = max(TOL_FP64, 2.0 * spread(M, cs, fo, ref))
+        assert relerr(P.get(F, b), ref) <= bar, (b, relerr(P.get(F, b), ref), bar)
