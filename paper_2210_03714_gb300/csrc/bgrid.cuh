@@ -31,6 +31,29 @@ __device__ __forceinline__ double block_max(double m, double* red) {
   return r;
 }
 
+// Finiteness, |v| and v 2^-s of an entry.  For real entries they are integer
+// operations on the bit pattern (the FP64 pipe, the limit of the elementwise
+// passes on GB300, is left to the sums): v 2^-s by subtracting s from the
+// exponent field when the result stays normal (exactly the product), by the
+// multiplication otherwise (zero, subnormal results, inf, NaN).
+template <class T> __device__ __forceinline__ bool entry_finite(T a) { return Tr<T>::finite(a); }
+template <> __device__ __forceinline__ bool entry_finite<double>(double a) {
+  return ((__double_as_longlong(a) >> 52) & 0x7FF) != 0x7FF;
+}
+template <class T> __device__ __forceinline__ double entry_mag(T a) { return Tr<T>::mag(a); }
+template <> __device__ __forceinline__ double entry_mag<double>(double a) {
+  return __longlong_as_double(__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFLL);
+}
+template <class T> __device__ __forceinline__ T entry_pow2(T a, int s, double p2) {
+  return Tr<T>::rscale(a, p2);
+}
+template <> __device__ __forceinline__ double entry_pow2<double>(double a, int s, double p2) {
+  const long long bits = __double_as_longlong(a);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  return (E > s && E != 0x7FF) ? __longlong_as_double(bits - ((long long)s << 52))
+                               : __dmul_rn(a, p2);
+}
+
 // a1/a2, one block per matrix: B = t A (one rounding), eta = ||tA||_1 (column
 // sums, rows ascending, as the one-CTA kernels), s, B <- B / 2^s; info -2 for
 // a non-finite entry or t.  alive[b] = 1 unless info = -2.
@@ -62,10 +85,10 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
 #pragma unroll 8
     for (int r = 0; r < n; ++r) {
       const T a = Ab[(size_t)r * n + c];
-      bad |= !Tr<T>::finite(a);
+      bad |= !entry_finite<T>(a);
       const T v = tb == 1.0 ? a : Tr<T>::rscale(a, tb);  // t = 1: fl(t a) = a
       Bb[(size_t)r * n + c] = v;
-      sc += Tr<T>::mag(v);
+      sc += entry_mag<T>(v);
     }
     cmax = (sc > cmax || isnan(sc)) ? sc : cmax;
   }
@@ -84,7 +107,7 @@ __global__ void b_prologue(const BMat* mats, const T* A, const double* t, T* B, 
   // column loop's stores before these loads
   if (s > 0) {
     const double p2 = ldexp(1.0, -s);
-    for (int e = tid; e < n * n; e += blockDim.x) Bb[e] = Tr<T>::rscale(Bb[e], p2);
+    for (int e = tid; e < n * n; e += blockDim.x) Bb[e] = entry_pow2<T>(Bb[e], s, p2);
   }
   if (tid == 0) {
     if (s_out) s_out[blockIdx.x] = s;
