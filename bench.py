@@ -195,9 +195,8 @@ def pipe_peaks(peaks):
                             else (1900.0, "fallback"))}
 
 
-def survey_flops(dims, s, k=8):
-    """The algorithmic count of the method per matrix, as the scope table states
-    it: k shifted systems (the R8 nodes), each an inverse of 8/3 d^3 flops (Sec. 1:
+def counted_flops(dims, s, k=8):
+    """The method's algorithmic count per matrix: k shifted systems (the R8 nodes), each an inverse of 8/3 d^3 flops (Sec. 1:
     LU and d triangular solves), and s squarings of 2 d^3: (8/3 k + 2 s) d^3,
     summed over the batch.  (The fused +-c pairs do less work than this count.)"""
     import numpy as np
@@ -334,7 +333,7 @@ def run_single(args, emit=True):
     ms = sum(per) / len(per)
     peaks = load_peaks()
     pk = pipe_peaks(peaks)
-    # the method's algorithmic flops per call (the scope table's count; complex
+    # the method's algorithmic flops per call (8/3 d^3 per inverse, 2 d^3 per product; complex
     # arithmetic as 4 real flops per multiply-add)
     if args.workload == "diffusion":
         _, _, _, s_d = fm.phi1_batched(Pd, td, cs, cp, precision=args.precision)
@@ -1000,7 +999,7 @@ def main():
         tile_s = st["tile_ms"] / 1000.0
         # with a tuned split the tile kernel sees only the orders from d*
         gmask = np.asarray(dims) >= (tune["dstar"] if tune else 1)
-        alg = survey_flops(np.asarray(dims)[gmask], np.asarray(s_host)[gmask])
+        alg = counted_flops(np.asarray(dims)[gmask], np.asarray(s_host)[gmask])
         ach = alg / tile_s / 1e12 if tile_s > 0 else 0.0
         busy = st["digit_flops"] / tile_s / 1e12 if tile_s > 0 else 0.0
         step_ach = alg / (ms / 1000.0) / 1e12
